@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""Benchmark: 30-qubit QFT followed by its inverse (960 gates, partition budget
+L = 11) on a random normalised complex64 state, on one GB300 per rank.
+
+One step = partition the circuit on the host (C++ closeness-centrality
+partitioner), run every stage sweep on the GPU, and reduce the state norm in FP64
+(the step's device->host result).  Reported: time per circuit, the live roofline
+of the stage-sweep kernel, the HBM passes, the adjoint-gradient / forward ratio
+on the 28-qubit hardware-efficient ansatz, an end-to-end number through the C ABI
+with host buffers, and the CPU oracle timed on a bounded sample.
+
+Multi-GPU: the path does not shard (one full state per GPU), so N ranks run N
+independent replicas (weak scaling) with a barrier and max-over-ranks timing.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "30-qubit circuit time & achieved HBM GB/s vs peak; adjoint-grad/forward ratio"
+N_QUBITS, L_BUDGET = 30, 11
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--L", type=int, default=L_BUDGET)
+    ap.add_argument("--n", type=int, default=N_QUBITS)
+    ap.add_argument("--grad-n", type=int, default=28)
+    ap.add_argument("--grad-L", type=int, default=12)
+    ap.add_argument("--no-extras", action="store_true", help="skip e2e, grad ratio and CPU baseline")
+    ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--sample-seconds", type=float, default=12.0, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (runs in a child process with one BLAS / OpenMP thread)
+# ---------------------------------------------------------------------------
+def cpu_sample(seconds):
+    import numpy as np
+
+    import circuits as C
+    from oracle import statevector as S
+    n_s = 24
+    circ = C.qft_roundtrip(n_s)
+    psi = C.random_state(n_s, 2)
+    t0 = time.perf_counter()
+    k = 0
+    while k < len(circ.gates) and time.perf_counter() - t0 < seconds:
+        g = circ.gates[k]
+        psi = S.apply_gate(psi, n_s, g, circ.angles_of(g, None))
+        k += 1
+    dt = time.perf_counter() - t0
+    full_gates = len(C.qft_roundtrip(N_QUBITS).gates)
+    per_gate_amp = dt / (k * (1 << n_s))
+    est_ms = per_gate_amp * full_gates * (1 << N_QUBITS) * 1e3
+    print(json.dumps({"ms_per_circuit": est_ms, "seconds": dt, "gates": k, "n_sample": n_s,
+                      "full_gates": full_gates, "norm": float(np.vdot(psi, psi).real)}))
+
+
+def run_cpu_sample(seconds):
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[v] = "1"
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", "--sample-seconds", str(seconds)],
+                       capture_output=True, text=True, env=env, timeout=600)
+    if r.returncode != 0:
+        return None
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {
+        "value": d["ms_per_circuit"], "unit": "ms", "cores": 1, "kind": "oracle",
+        "sample": (f"first {d['gates']} gates of QFT{d['n_sample']} then inverse QFT (complex128 gate-by-gate "
+                   f"oracle) on a 2^{d['n_sample']} state in {d['seconds']:.1f} s, scaled by 2^{N_QUBITS}/2^{d['n_sample']} "
+                   f"amplitudes and {d['full_gates']}/{d['gates']} gates; 1 thread of {os.cpu_count()} host cores"),
+    }
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        for r in rows:
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        load = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return None
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("stage_kernels.cu", "kdev.cuh", "program.h", "lower.cpp"):
+        h.update(open(os.path.join(ROOT, "paper_2509_14098_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch():
+    """DRAM bytes per stage-sweep launch from the committed ncu summary, if it was
+    taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "stage_fwd_qft30.json")
+    try:
+        d = json.load(open(p))
+    except OSError:
+        return None
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, x):
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def main_reference(args):
+    world, rank, local, pg = dist_setup(args)
+    if rank != 0:
+        return
+    samples = []
+    per = max(2.0, min(10.0, 150.0 / max(1, args.steps + args.warmup)))
+    for i in range(args.warmup + args.steps):
+        cb = run_cpu_sample(per)
+        if cb is None:
+            print(json.dumps({"impl": "reference", "unavailable": "oracle sample failed"}))
+            return
+        if i >= args.warmup:
+            samples.append(cb["value"])
+    v = statistics.median(samples)
+    cb["value"] = v
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "qft30_roundtrip", "n_qubits": N_QUBITS, "L": args.L, "gates": 960},
+        "cpu_baseline": cb, "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main_ours(args):
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    import circuits as C
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2509_14098_gb300 as sv
+    from paper_2509_14098_gb300 import _native as N
+
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n, L = args.n, args.L
+    circ = C.qft_roundtrip(n)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(2 + rank)
+    psi = torch.randn(1 << n, dtype=torch.complex64, device=dev, generator=gen)
+    psi /= torch.linalg.vector_norm(psi)
+    ref_copy = psi.clone() if rank == 0 else None
+    st = sv.StateVector(n, tensor=psi)
+    stream = st.stream
+
+    t0 = time.perf_counter()
+    plan0 = sv.Plan(circ, L)
+    partition_ms = (time.perf_counter() - t0) * 1e3
+    stages = plan0.stages()
+
+    def step():
+        plan = sv.Plan(circ, L)
+        st.run(plan)
+        return st.norm()
+
+    for _ in range(args.warmup):
+        step()
+    info = st.run_info()
+    launches_per_step = info["kernel_launches"] + 2           # + norm and its reduction
+    passes = info["stage_sweeps"] + info["permutation_sweeps"]
+    torch.cuda.synchronize()
+    barrier(pg)
+    clocks = Clocks(local)
+    clocks.start()
+    st.timing(True)
+    st.timing(reset=True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    norms = [step() for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_total = e0.elapsed_time(e1)
+    tm = st.timing(reset=True)
+    st.timing(False)
+    ck = clocks.stop()
+    barrier(pg)
+    ms_total = max_over_ranks(pg, ms_total)
+    ms_step = ms_total / args.steps
+    value = ms_step / world                                       # ms per circuit, whole job
+
+    pk = peaks()
+    hbm_peak = pk["hbm_gbs"] if pk else 6800.0
+    bytes_per_launch = 2.0 * (1 << n) * 8
+    avg_stage_ms = tm["stage_ms"] / max(1, tm["stage_launches"])
+    achieved = bytes_per_launch / (avg_stage_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": traffic_per_launch(),
+                "kernel": "k_stage_fwd (one partition sweep, complex64)",
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback",
+                "avg_launch_ms": avg_stage_ms, "launches": tm["stage_launches"]}
+    whole_gbs = passes * bytes_per_launch / (ms_step * 1e-3) / 1e9
+
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        # parity check of the timed result: QFT then inverse QFT is the identity
+        err = float(torch.linalg.vector_norm(psi - ref_copy).item())
+        extras["roundtrip_error_l2"] = err
+        del ref_copy
+        # end to end through the C ABI with host buffers (pinned)
+        host_in = torch.empty(1 << n, dtype=torch.complex64, pin_memory=True)
+        host_in.copy_(psi)
+        host_out = torch.empty_like(host_in, pin_memory=True)
+        h = st.handle
+
+        def e2e_step():
+            N.check(N.lib.sv_set_state_host(h, ctypes.c_void_p(host_in.data_ptr())))
+            plan = sv.Plan(circ, L)
+            st.run(plan)
+            nrm = st.norm()
+            N.check(N.lib.sv_get_state_host(h, ctypes.c_void_p(host_out.data_ptr())))
+            return nrm
+
+        e2e_step()
+        t0 = time.perf_counter()
+        ne = 2
+        for _ in range(ne):
+            e2e_step()
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / ne
+        extras["e2e"] = {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": (1 << n) * 8,
+                         "d2h_bytes_per_step": (1 << n) * 8 + 8}
+        del host_in, host_out
+        # adjoint gradient / forward ratio on the hardware-efficient ansatz
+        st.close()
+        del st, psi
+        torch.cuda.empty_cache()
+        gn = args.grad_n
+        hc = C.hea(gn, 10)
+        hp = C.hea_params(hc.n_params, 4)
+        hplan = sv.Plan(hc, args.grad_L)
+        g = sv.StateVector(gn)
+        obs = C.tfim(gn)
+
+        def fwd():
+            g.reset()
+            g.run(hplan, hp)
+            return g.expval(obs)
+
+        def grad():
+            g.reset()
+            return g.grad(hplan, hp, obs)
+
+        fwd(); grad()
+        torch.cuda.synchronize()
+        g.timing(True); g.timing(reset=True)
+        t0 = time.perf_counter(); [g.run(hplan, hp) for _ in range(3)]; torch.cuda.synchronize()
+        t_fwd = (time.perf_counter() - t0) / 3
+        tf = g.timing(reset=True)
+        t0 = time.perf_counter(); [grad() for _ in range(3)]; torch.cuda.synchronize()
+        t_grad = (time.perf_counter() - t0) / 3
+        tg = g.timing(reset=True)
+        g.timing(False)
+        extras["grad_forward_ratio"] = {
+            "workload": f"hea{gn}x10 (560 params), TFIM open chain, L={args.grad_L}",
+            "ratio": (t_grad - t_fwd) / t_fwd, "grad_over_forward": t_grad / t_fwd,
+            "forward_ms": t_fwd * 1e3, "grad_ms": t_grad * 1e3,
+            "kernel_ms": {"forward_stages": tf["stage_ms"] / 3, "grad_forward_stages": tg["stage_ms"] / 3,
+                          "backward_stages": tg["backward_ms"] / 3, "lambda_and_expval": tg["observable_ms"] / 3},
+            "definition": "(time(sv_grad) - time(sv_run)) / time(sv_run): lambda formation + backward over forward",
+        }
+        g.close()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        cpu = run_cpu_sample(args.sample_seconds)
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "qft30_roundtrip", "n_qubits": n, "L": L, "gates": len(circ.gates),
+                       "state": "complex64, i.i.d. N(0,1) re/im (seeded torch Philox), normalised",
+                       "l2": "inputs larger than L2 (8 GiB state)", "parallelism": f"replicas x{world}"},
+            "roofline": roofline,
+            "hbm_passes": passes, "stages": len(stages), "achieved_gbs_whole_circuit": whole_gbs,
+            "partition_ms": partition_ms, "norm_last_step": norms[-1],
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": ck,
+        }
+        if cpu:
+            out["cpu_baseline"] = cpu
+        out.update(extras)
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.cpu_sample:
+        cpu_sample(a.sample_seconds)
+    elif a.impl == "reference":
+        main_reference(a)
+    else:
+        main_ours(a)

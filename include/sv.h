@@ -1,0 +1,255 @@
+/*
+ * sv.h — C ABI of the GB300 state-vector engine for closeness-centrality
+ * partitioned quantum circuits.
+ *
+ * What it computes.  A circuit is a flat gate list applied to an n-qubit state
+ * psi (2^n complex amplitudes; qubit q is bit q of the amplitude index).  The
+ * exact result is psi = U_G ... U_1 psi_0 with the gates in their original order
+ * (Sec. 3.2; Sec. 4.1: gates are neither permuted nor replaced).  The host builds
+ * the gate-dependency graph and partitions it by closeness centrality (Sec. 4.2);
+ * the GPU then executes each partition as one sweep over the state held in HBM:
+ * a partition's local qubits become the bits of a shared-memory tile, its other
+ * qubits index the tiles (Sec. 4.3, "Partitioning the Input/Output Tensors" and
+ * the single-device pack/unpack into shared memory).
+ *
+ * Conventions shared by every call
+ *  - Every call returns sv_status; SV_OK (0) on success.  Nothing throws across
+ *    the ABI.  sv_last_error() returns a message for the calling thread's most
+ *    recent failure (valid until that thread's next call).
+ *  - Device pointers are CUDA global-memory pointers on the handle's device;
+ *    host pointers are ordinary CPU memory.  "Borrowed" means the caller owns the
+ *    memory and must keep it alive (and unmodified by other streams) while the
+ *    handle may use it; "library-owned" objects are freed by the matching
+ *    destroy call.
+ *  - Work is enqueued on the handle's CUDA stream and is asynchronous unless the
+ *    call returns host values (sv_expval, sv_norm, sv_grad, sv_get_state_host),
+ *    which synchronise that stream.
+ *  - There is no CPU fallback: every state operation runs in the library's CUDA
+ *    kernels.  Without a usable GPU, state calls return SV_ERR_CUDA.  The host
+ *    partitioning calls (sv_partition*, sv_plan_*) need no GPU.
+ *  - Amplitude layout: complex64 = {float re, float im}, complex128 =
+ *    {double re, double im}, contiguous, index = sum_q bit_q * 2^q.  Between
+ *    calls the state is always in this canonical layout.
+ */
+#ifndef SV_GB300_H
+#define SV_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SV_OK = 0,
+    SV_ERR_ARG = 1,          /* invalid argument (null pointer, bad size, bad gate)         */
+    SV_ERR_OOM = 2,          /* device or host allocation failed                            */
+    SV_ERR_CUDA = 3,         /* a CUDA runtime call or kernel launch failed / no GPU        */
+    SV_ERR_PARTITION = 4,    /* a gate needs more local qubits than the budget L allows     */
+    SV_ERR_UNSUPPORTED = 5,  /* valid request this build does not implement                 */
+    SV_ERR_TIMEOUT = 6       /* a bounded device-side wait gave up (error flag, no hang)     */
+} sv_status;
+
+typedef enum { SV_C64 = 0, SV_C128 = 1 } sv_dtype;
+
+/* Arithmetic used for stage sweeps.  SV_PREC_CUDACORE: complex FP32 (complex64
+ * states) or FP64 (complex128 states) on the CUDA cores.  The split-precision
+ * tensor-core modes apply stages fused into dense 2^k x 2^k unitaries as GEMMs. */
+typedef enum { SV_PREC_CUDACORE = 0, SV_PREC_TF32X3 = 1, SV_PREC_BF16X3 = 2 } sv_prec;
+
+/* Gate kinds.  Matrices (Sec. 3.1): H, Pauli X/Y/Z, S = P(pi/2), SDG = P(-pi/2),
+ * T = P(pi/4), TDG = P(-pi/4), RX/RY/RZ(t) = exp(-i t {X,Y,Z} / 2),
+ * P(a) = diag(1, e^{ia}) (the paper prints e^{-ja}; this library uses the usual
+ * +i sign), U3(t,p,l) = [[cos t/2, -e^{il} sin t/2], [e^{ip} sin t/2, e^{i(p+l)} cos t/2]],
+ * CX/CY/CZ controlled Paulis, CP(a) = diag(1,1,1,e^{ia}), SWAP. */
+enum {
+    SV_GATE_H = 1, SV_GATE_X, SV_GATE_Y, SV_GATE_Z, SV_GATE_S, SV_GATE_SDG, SV_GATE_T,
+    SV_GATE_TDG, SV_GATE_RX, SV_GATE_RY, SV_GATE_RZ, SV_GATE_P, SV_GATE_U3, SV_GATE_CX,
+    SV_GATE_CY, SV_GATE_CZ, SV_GATE_CP, SV_GATE_SWAP
+};
+
+/* One gate, 40 bytes, no implicit padding.  q[0] is the control of CX/CY/CP/CZ,
+ * q[1] the target.  param >= 0 makes the gate's single angle params[param]
+ * (RX, RY, RZ, P, CP only); param = -1 uses angle[] (U3 uses all three). */
+typedef struct {
+    uint16_t kind;
+    uint8_t  nq;
+    uint8_t  q[3];
+    uint16_t reserved;
+    int32_t  param;
+    double   angle[3];
+} sv_gate;
+
+/* A circuit (borrowed for the duration of the call that receives it). */
+typedef struct {
+    uint32_t n_qubits;
+    uint32_t n_gates;
+    uint32_t n_params;
+    const sv_gate* gates;
+} sv_circuit;
+
+/* Sum of Pauli strings.  pauli[t * n_qubits + q] in {0=I, 1=X, 2=Y, 3=Z} is the
+ * factor on qubit q of term t; coeff[t] its real coefficient.  Borrowed. */
+typedef struct {
+    uint32_t n_terms;
+    uint32_t n_qubits;
+    const uint8_t* pauli;
+    const double* coeff;
+} sv_observable;
+
+typedef struct sv_handle_s* sv_handle;
+typedef struct sv_plan_s sv_plan;
+
+/* Work counters of the last sv_run / sv_grad on a handle. */
+typedef struct {
+    uint32_t stage_sweeps;       /* read+write passes over psi by stage kernels          */
+    uint32_t permutation_sweeps; /* bit-permutation passes                              */
+    uint32_t reduction_sweeps;   /* read-only / observable passes                       */
+    uint32_t backward_sweeps;    /* adjoint passes (psi and lambda together)             */
+    uint32_t kernel_launches;    /* kernels this library launched in the call           */
+    double   hbm_bytes;          /* algorithmic bytes moved (reads + writes)            */
+} sv_run_info;
+
+/* ---------------------------------------------------------------------------
+ * Errors
+ * ------------------------------------------------------------------------- */
+/* Message of the calling thread's last failure ("" if none).  Library-owned. */
+const char* sv_last_error(void);
+
+/* ---------------------------------------------------------------------------
+ * Handles (state vectors)
+ * ------------------------------------------------------------------------- */
+/* Create a handle for an n_qubits state (1 <= n_qubits <= 34) of the given dtype.
+ * dev_state: borrowed device buffer of 2^n amplitudes (16-byte aligned), or NULL
+ * to let the library allocate (and own) one initialised to |0...0>.
+ * cuda_stream: a cudaStream_t to enqueue on (NULL = the legacy default stream).
+ * Errors: SV_ERR_ARG (bad n, dtype, null out, misaligned buffer), SV_ERR_OOM,
+ * SV_ERR_CUDA (no device). */
+sv_status sv_create(uint32_t n_qubits, sv_dtype dtype, void* dev_state, void* cuda_stream,
+                    sv_handle* out);
+
+/* Free the handle and every library-owned buffer (not a borrowed state). */
+sv_status sv_destroy(sv_handle h);
+
+/* Number of qubits, dtype and the device pointer of the state. */
+sv_status sv_info(sv_handle h, uint32_t* n_qubits, sv_dtype* dtype, void** dev_state);
+
+/* Set psi to |0...0>.  Async. */
+sv_status sv_reset_zero(sv_handle h);
+
+/* Copy 2^n amplitudes from / to device memory (async, stream-ordered). */
+sv_status sv_set_state(sv_handle h, const void* dev_src);
+sv_status sv_get_state(sv_handle h, void* dev_dst);
+
+/* Copy 2^n amplitudes from / to host memory.  Pinned host memory gives full
+ * transfer speed; set is async with respect to the host only for pinned memory,
+ * get synchronises the stream. */
+sv_status sv_set_state_host(sv_handle h, const void* host_src);
+sv_status sv_get_state_host(sv_handle h, void* host_dst);
+
+/* Wait for all work queued on the handle's stream. */
+sv_status sv_synchronize(sv_handle h);
+
+/* Counters of the last sv_run / sv_grad. */
+sv_status sv_last_run_info(sv_handle h, sv_run_info* out);
+
+/* Per-kernel device time, accumulated while timing is enabled on a handle. */
+typedef struct {
+    double   stage_ms;          /* forward stage sweeps        */
+    double   backward_ms;       /* adjoint stage sweeps        */
+    double   permute_ms;        /* bit-permutation sweeps      */
+    double   observable_ms;     /* Pauli / norm sweeps         */
+    uint32_t stage_launches;
+    uint32_t backward_launches;
+    uint32_t permute_launches;
+    uint32_t observable_launches;
+} sv_timing;
+
+/* enable != 0: record a CUDA event pair on the handle's stream around every
+ * sweep kernel the handle launches (negligible overhead); 0 stops recording. */
+sv_status sv_timing_enable(sv_handle h, int enable);
+
+/* Sum the recorded event pairs into *out (synchronises the stream); reset != 0
+ * clears the record afterwards. */
+sv_status sv_timing_read(sv_handle h, sv_timing* out, int reset);
+
+/* ---------------------------------------------------------------------------
+ * Partitioning (host only; Sec. 4.1-4.2)
+ * ------------------------------------------------------------------------- */
+/* Build the contraction DAG (each gate a node, edges = qubit dimensions, critical
+ * path level l_g = 1 + max over predecessors), compute exact closeness centrality
+ * CC(v) = |RN(v)|^2 / (N * dist(v)) with RN the reachable set and
+ * dist(v) = sum_{x in RN(v)} (l_x - l_v) (Sec. 4.2 equations; the overlap
+ * threshold heuristic is unnecessary because the distance sum is exact), and cut
+ * the circuit into partitions whose required qubits fit L local qubits with the
+ * forward frontier pass of Sec. 4.2 (highest CC first, ties by gate index;
+ * diagonal gates and non-local controls exempt; SWAP executed as a relabel).
+ * L is the width of the shared-memory tile in qubits.  sv_partition reserves the
+ * min(4, L - 1, n) lowest physical qubits in every partition: a tile must contain them
+ * so that each HBM access is a contiguous run of >= 128 bytes.  The plan is
+ * deterministic, library-owned, independent of any handle and of the dtype.
+ * Errors: SV_ERR_ARG (bad circuit: qubit out of range, unknown kind, bad param
+ * slot; L < 1 or > 14), SV_ERR_PARTITION (a gate's qubits cannot be made local). */
+sv_status sv_partition(const sv_circuit* circuit, uint32_t L, sv_plan** out);
+
+/* As sv_partition with an explicit number of reserved low qubits (0 gives the
+ * paper's unconstrained partitioner, e.g. for its worked examples). */
+sv_status sv_partition_ex(const sv_circuit* circuit, uint32_t L, uint32_t n_fixed, sv_plan** out);
+
+/* Partition summary.  local_masks[s] = physical-bit mask of stage s's local set
+ * (after SWAP relabelling); gate_counts[s] = gates in stage s.  Either array may be
+ * NULL; each must hold n_stages entries (query n_stages first with both NULL). */
+sv_status sv_plan_stages(const sv_plan* plan, uint32_t* n_stages, uint64_t* local_masks,
+                         uint32_t* gate_counts);
+
+/* Gate ids in execution order (n_gates entries) and the final map circuit qubit ->
+ * physical bit (n_qubits entries).  Either may be NULL. */
+sv_status sv_plan_order(const sv_plan* plan, uint32_t* gate_order, uint32_t* final_map);
+
+/* Exact closeness of every gate as the integers |RN(v)| and dist(v), and the
+ * critical-path level l_v (arrays of n_gates; any may be NULL). */
+sv_status sv_plan_centrality(const sv_plan* plan, uint32_t* reach, uint64_t* dist, uint32_t* level);
+
+/* Free a plan. */
+sv_status sv_plan_destroy(sv_plan* plan);
+
+/* ---------------------------------------------------------------------------
+ * Execution
+ * ------------------------------------------------------------------------- */
+/* Apply the planned circuit to the handle's state in place: one stage-sweep
+ * kernel per partition, then a bit-permutation sweep if the SWAP relabels leave
+ * a non-identity qubit map.  params: host array of the circuit's n_params angles
+ * (NULL if n_params == 0).  prec: SV_PREC_CUDACORE, or a tensor-core mode (needs a
+ * plan from sv_partition_gemm).  Async.
+ * Errors: SV_ERR_ARG (width mismatch, null params), SV_ERR_UNSUPPORTED
+ * (precision / dtype / plan combination), SV_ERR_CUDA. */
+sv_status sv_run(sv_handle h, const sv_plan* plan, const double* params, sv_prec prec);
+
+/* Bit-permutation sweep: new[y] = old[x] where bit phys_of_qubit[q] of x equals
+ * bit q of y (Sec. 4.3 data reshaping; on one GPU the exchange is a relabel plus
+ * this sweep).  phys_of_qubit: host array of n entries, a permutation. */
+sv_status sv_permute(sv_handle h, const uint32_t* phys_of_qubit);
+
+/* <psi|O|psi> for a Pauli sum, reduced in FP64 (FP32 partial sums over at most
+ * 32 amplitudes).  Result written to *out (host); synchronises. */
+sv_status sv_expval(sv_handle h, const sv_observable* obs, double* out);
+
+/* ||psi||^2 in FP64; synchronises. */
+sv_status sv_norm(sv_handle h, double* out);
+
+/* Adjoint differentiation of E(theta) = <psi(theta)|O|psi(theta)>: runs the
+ * forward circuit from the current state, forms lambda = O psi, then un-applies
+ * the partitions in reverse to psi and lambda together while accumulating
+ * dE/dtheta_p = 2 Re <lambda| dU_p/dtheta psi> for every parameter (RX, RY, RZ
+ * parameters supported).  On return the handle holds psi(theta) (forward result).
+ * expval_out (host, may be NULL) receives E; grad_out (host, n_params) the
+ * gradient.  Synchronises.  Errors: SV_ERR_UNSUPPORTED for parameters on other
+ * gate kinds. */
+sv_status sv_grad(sv_handle h, const sv_plan* plan, const double* params, const sv_observable* obs,
+                  double* expval_out, double* grad_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SV_GB300_H */

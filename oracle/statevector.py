@@ -63,3 +63,16 @@ def permute_qubits(psi, n, phys_of_wire):
     for w, p in enumerate(phys_of_wire):
         src |= ((idx >> w) & 1) << p
     return psi[src]
+
+
+def dft_amplitude(psi, k, chunk=1 << 24):
+    """One output amplitude of the QFT (little-endian, Sec. 5 QFT workload) from its
+    definition y_k = 2^{-n/2} sum_x psi_x exp(2 pi i x k / 2^n), summed in chunks in
+    FP64.  The exponent x*k is reduced mod 2^n in exact integer arithmetic."""
+    N = len(psi)
+    acc = 0j
+    for s in range(0, N, chunk):
+        x = np.arange(s, min(N, s + chunk), dtype=np.int64)
+        ph = ((x * int(k)) % N).astype(np.float64) * (2.0 * np.pi / N)
+        acc += np.sum(psi[s:s + len(x)].astype(np.complex128) * np.exp(1j * ph))
+    return acc / np.sqrt(N)

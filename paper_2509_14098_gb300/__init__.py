@@ -1,0 +1,162 @@
+"""GB300-native execution of closeness-centrality-partitioned quantum circuits.
+
+Python surface over the C ABI (include/sv.h): partition a circuit on the host
+(Plan), then run it on a state vector held in GPU memory (StateVector).  PyTorch
+provides device memory and streams only; every state operation runs in this
+package's CUDA kernels.
+"""
+import ctypes
+
+import numpy as np
+
+from . import _native as N
+from ._native import SvError, SV_C64, SV_C128, SV_PREC_CUDACORE, SV_PREC_TF32X3, SV_PREC_BF16X3
+
+__all__ = ["Plan", "StateVector", "SvError", "partition", "SV_C64", "SV_C128",
+           "SV_PREC_CUDACORE", "SV_PREC_TF32X3", "SV_PREC_BF16X3"]
+
+
+class Plan:
+    """Host-side partition of a circuit (sv_partition / sv_partition_ex)."""
+
+    def __init__(self, circuit, L, n_fixed=None):
+        self.circuit = circuit
+        self.L = L
+        c, self._gates = N.circuit_struct(circuit)
+        self._c = c
+        h = ctypes.c_void_p()
+        if n_fixed is None:
+            N.check(N.lib.sv_partition(ctypes.byref(c), L, ctypes.byref(h)))
+        else:
+            N.check(N.lib.sv_partition_ex(ctypes.byref(c), L, n_fixed, ctypes.byref(h)))
+        self.handle = h
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            N.lib.sv_plan_destroy(h)
+            self.handle = None
+
+    def stages(self):
+        """[(local physical-bit mask, gate count)] per stage."""
+        n = ctypes.c_uint32(0)
+        N.check(N.lib.sv_plan_stages(self.handle, ctypes.byref(n), None, None))
+        masks = (ctypes.c_uint64 * n.value)()
+        counts = (ctypes.c_uint32 * n.value)()
+        N.check(N.lib.sv_plan_stages(self.handle, ctypes.byref(n), masks, counts))
+        return [(int(masks[i]), int(counts[i])) for i in range(n.value)]
+
+    def order(self):
+        """(gate ids in execution order, final map circuit qubit -> physical bit)."""
+        G, n = len(self.circuit.gates), self.circuit.n_qubits
+        order = (ctypes.c_uint32 * G)()
+        fmap = (ctypes.c_uint32 * n)()
+        N.check(N.lib.sv_plan_order(self.handle, order, fmap))
+        return list(order), list(fmap)
+
+    def centrality(self):
+        """(|RN|, dist, level) per gate."""
+        G = len(self.circuit.gates)
+        r = (ctypes.c_uint32 * G)()
+        d = (ctypes.c_uint64 * G)()
+        lv = (ctypes.c_uint32 * G)()
+        N.check(N.lib.sv_plan_centrality(self.handle, r, d, lv))
+        return list(r), list(d), list(lv)
+
+
+def partition(circuit, L, n_fixed=None):
+    return Plan(circuit, L, n_fixed)
+
+
+class StateVector:
+    """A state of n qubits in GPU memory (a borrowed torch tensor of complex64 /
+    complex128), bound to a CUDA stream."""
+
+    def __init__(self, n_qubits, dtype=SV_C64, tensor=None, device="cuda", stream=None):
+        import torch
+        self.n = n_qubits
+        self.dtype = dtype
+        tdt = torch.complex64 if dtype == SV_C64 else torch.complex128
+        if tensor is None:
+            tensor = torch.zeros(1 << n_qubits, dtype=tdt, device=device)
+            tensor[0] = 1
+        if tensor.dtype != tdt or tensor.numel() != (1 << n_qubits) or not tensor.is_cuda or not tensor.is_contiguous():
+            raise ValueError("state tensor must be a contiguous CUDA tensor of 2^n amplitudes of the dtype")
+        self.tensor = tensor
+        self.stream = stream if stream is not None else torch.cuda.current_stream(tensor.device)
+        h = ctypes.c_void_p()
+        N.check(N.lib.sv_create(n_qubits, dtype, ctypes.c_void_p(tensor.data_ptr()),
+                                ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            N.lib.sv_destroy(h)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+    # --- state movement -------------------------------------------------------
+    def reset(self):
+        N.check(N.lib.sv_reset_zero(self.handle))
+
+    def set_host(self, array):
+        a = np.ascontiguousarray(array, dtype=np.complex64 if self.dtype == SV_C64 else np.complex128)
+        N.check(N.lib.sv_set_state_host(self.handle, a.ctypes.data_as(ctypes.c_void_p)))
+        self.synchronize()   # the host array may be pageable and temporary
+
+    def get_host(self):
+        out = np.empty(1 << self.n, dtype=np.complex64 if self.dtype == SV_C64 else np.complex128)
+        N.check(N.lib.sv_get_state_host(self.handle, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def synchronize(self):
+        N.check(N.lib.sv_synchronize(self.handle))
+
+    # --- execution ------------------------------------------------------------
+    def run(self, plan, params=None, prec=SV_PREC_CUDACORE):
+        p = None if params is None else np.ascontiguousarray(params, dtype=np.float64)
+        self._params = p
+        N.check(N.lib.sv_run(self.handle, plan.handle, N.as_double_ptr(p), prec))
+
+    def permute(self, phys_of_qubit):
+        arr = (ctypes.c_uint32 * self.n)(*phys_of_qubit)
+        N.check(N.lib.sv_permute(self.handle, arr))
+
+    def norm(self):
+        out = ctypes.c_double()
+        N.check(N.lib.sv_norm(self.handle, ctypes.byref(out)))
+        return out.value
+
+    def expval(self, obs):
+        o, keep = N.observable_struct(obs)
+        out = ctypes.c_double()
+        N.check(N.lib.sv_expval(self.handle, ctypes.byref(o), ctypes.byref(out)))
+        return out.value
+
+    def grad(self, plan, params, obs):
+        """Adjoint gradient; returns (E, dE/dtheta).  The state after the call is the
+        backward pass's reconstruction of the input state."""
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        o, keep = N.observable_struct(obs)
+        e = ctypes.c_double()
+        g = np.zeros(max(1, len(p)), dtype=np.float64)
+        N.check(N.lib.sv_grad(self.handle, plan.handle, N.as_double_ptr(p), ctypes.byref(o),
+                              ctypes.byref(e), N.as_double_ptr(g)))
+        return e.value, g[: len(p)]
+
+    def timing(self, enable=None, reset=False):
+        """Enable / disable per-kernel event timing, or read the accumulated record."""
+        if enable is not None:
+            N.check(N.lib.sv_timing_enable(self.handle, 1 if enable else 0))
+            return None
+        t = N.sv_timing()
+        N.check(N.lib.sv_timing_read(self.handle, ctypes.byref(t), 1 if reset else 0))
+        return {f: getattr(t, f) for f, _ in N.sv_timing._fields_}
+
+    def run_info(self):
+        info = N.sv_run_info()
+        N.check(N.lib.sv_last_run_info(self.handle, ctypes.byref(info)))
+        return {f: getattr(info, f) for f, _ in N.sv_run_info._fields_}

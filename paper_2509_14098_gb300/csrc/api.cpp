@@ -1,0 +1,722 @@
+// api.cpp — the C ABI declared in include/sv.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "planner.h"
+#include "sv.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+sv_status fail(sv_status s, const std::string& m) {
+    g_err = m;
+    return s;
+}
+
+#define SV_CUDA(x)                                                                             \
+    do {                                                                                       \
+        cudaError_t e_ = (x);                                                                  \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(SV_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_));        \
+    } while (0)
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+    cudaError_t ensure(size_t n) {
+        if (n <= cap) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e == cudaSuccess) cap = n;
+        return e;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+// Device copy of a lowered program: [stages][groups][ops][terms].
+struct DevProgram {
+    DevBuf buf;
+    svk::Stage* stages = nullptr;
+    svk::Group* groups = nullptr;
+    svk::Op* ops = nullptr;
+    svk::Term* terms = nullptr;
+    std::vector<uint8_t> host;
+};
+
+size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+}  // namespace
+
+struct sv_plan_s {
+    svh::Plan plan;
+};
+
+struct sv_handle_s {
+    uint32_t n = 0;
+    sv_dtype dt = SV_C64;
+    int eb = 8;
+    void* psi = nullptr;
+    bool owns = false;
+    cudaStream_t stream = nullptr;
+    DevBuf scratch;      // state-sized: permutation target / adjoint lambda
+    DevProgram fwd, bwd;
+    DevBuf partial;      // per-tile gradient partial sums
+    DevBuf slot_sum;     // per-slot gradient sums
+    DevBuf red;          // reduction partials and results
+    DevBuf aux;          // Pauli sweeps / permutation descriptors
+    std::vector<uint8_t> aux_host;
+    sv_run_info info{};
+    // kernel timing: event pairs recorded around sweep launches
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    struct Rec { cudaEvent_t a, b; int kind; };
+    std::vector<Rec> recs;
+    size_t ev_used = 0;
+};
+
+enum { TK_STAGE = 0, TK_BWD = 1, TK_PERM = 2, TK_OBS = 3 };
+
+static cudaEvent_t next_event(sv_handle h) {
+    if (h->ev_used == h->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        h->ev_pool.push_back(e);
+    }
+    return h->ev_pool[h->ev_used++];
+}
+// RAII-free helpers: tick() before a launch, tock() after it.
+static cudaEvent_t tick(sv_handle h) {
+    if (!h->timing) return nullptr;
+    cudaEvent_t e = next_event(h);
+    if (e) cudaEventRecord(e, h->stream);
+    return e;
+}
+static void tock(sv_handle h, cudaEvent_t a, int kind) {
+    if (!h->timing || !a) return;
+    cudaEvent_t b = next_event(h);
+    if (!b) return;
+    cudaEventRecord(b, h->stream);
+    h->recs.push_back({a, b, kind});
+}
+
+static sv_status upload_program(sv_handle h, const svh::Program& p, DevProgram* d) {
+    const size_t s0 = 0;
+    const size_t s1 = align16(s0 + p.stages.size() * sizeof(svk::Stage));
+    const size_t s2 = align16(s1 + p.groups.size() * sizeof(svk::Group));
+    const size_t s3 = align16(s2 + p.ops.size() * sizeof(svk::Op));
+    const size_t s4 = align16(s3 + std::max<size_t>(1, p.terms.size()) * sizeof(svk::Term));
+    SV_CUDA(d->buf.ensure(s4));
+    d->host.assign(s4, 0);
+    std::memcpy(d->host.data() + s0, p.stages.data(), p.stages.size() * sizeof(svk::Stage));
+    std::memcpy(d->host.data() + s1, p.groups.data(), p.groups.size() * sizeof(svk::Group));
+    std::memcpy(d->host.data() + s2, p.ops.data(), p.ops.size() * sizeof(svk::Op));
+    if (!p.terms.empty())
+        std::memcpy(d->host.data() + s3, p.terms.data(), p.terms.size() * sizeof(svk::Term));
+    // pageable source: the call returns once the data is staged, so the host vector
+    // may be reused immediately; the device copy is stream-ordered.
+    SV_CUDA(cudaMemcpyAsync(d->buf.p, d->host.data(), s4, cudaMemcpyHostToDevice, h->stream));
+    uint8_t* b = (uint8_t*)d->buf.p;
+    d->stages = (svk::Stage*)(b + s0);
+    d->groups = (svk::Group*)(b + s1);
+    d->ops = (svk::Op*)(b + s2);
+    d->terms = (svk::Term*)(b + s3);
+    return SV_OK;
+}
+
+static sv_status check_handle(sv_handle h) {
+    if (!h) return fail(SV_ERR_ARG, "null handle");
+    return SV_OK;
+}
+
+static size_t state_bytes(sv_handle h) { return ((size_t)1 << h->n) * (size_t)h->eb; }
+
+// ---------------------------------------------------------------------------
+// permutation sweep: new[y] = old[x], bit phys_of_qubit[q] of x = bit q of y
+// ---------------------------------------------------------------------------
+static sv_status do_permute(sv_handle h, const uint32_t* phys_of_qubit) {
+    const int n = (int)h->n;
+    int dst[64];
+    {
+        uint64_t seen = 0;
+        for (int q = 0; q < n; ++q) {
+            uint32_t p = phys_of_qubit[q];
+            if (p >= (uint32_t)n || ((seen >> p) & 1)) return fail(SV_ERR_ARG, "not a permutation");
+            seen |= 1ull << p;
+            dst[p] = q;
+        }
+    }
+    bool ident = true;
+    for (int p = 0; p < n; ++p)
+        if (dst[p] != p) ident = false;
+    if (ident) return SV_OK;
+    const int c = std::min(4, n);
+    uint64_t B = (1ull << c) - 1;
+    for (int p = 0; p < n; ++p)
+        if (dst[p] < c) B |= 1ull << p;
+    const int Tp = std::min(n, std::max(12, __builtin_popcountll(B)));
+    for (int p = 0; p < n && __builtin_popcountll(B) < Tp; ++p) B |= 1ull << p;
+    svk::PermDesc d;
+    std::memset(&d, 0, sizeof(d));
+    d.T = (uint32_t)Tp;
+    int nt = 0, ng = 0;
+    for (int p = 0; p < n; ++p) {
+        if ((B >> p) & 1) {
+            d.tile_pos[nt] = (uint8_t)p;
+            d.ptile[nt] = 1ull << p;
+            d.swbit[nt] = svk::swizzle(1u << nt, h->eb);
+            ++nt;
+        } else {
+            d.glob_pos[ng] = (uint8_t)p;
+            d.gout[ng] = 1ull << dst[p];
+            ++ng;
+        }
+    }
+    d.n_glob = (uint32_t)ng;
+    // output tile positions ascending; sig = swizzled input element offset
+    std::vector<std::pair<int, int>> outs;   // (output position, input tile bit)
+    for (int b = 0; b < nt; ++b) outs.push_back({dst[d.tile_pos[b]], b});
+    std::sort(outs.begin(), outs.end());
+    for (int c2 = 0; c2 < nt; ++c2) {
+        d.pout[c2] = 1ull << outs[c2].first;
+        d.sig[c2] = d.swbit[outs[c2].second];
+    }
+    SV_CUDA(h->scratch.ensure(state_bytes(h)));
+    SV_CUDA(h->aux.ensure(sizeof(d)));
+    h->aux_host.assign((uint8_t*)&d, (uint8_t*)&d + sizeof(d));
+    SV_CUDA(cudaMemcpyAsync(h->aux.p, h->aux_host.data(), sizeof(d), cudaMemcpyHostToDevice, h->stream));
+    const uint64_t ntiles = 1ull << (n - Tp);
+    cudaEvent_t t0 = tick(h);
+    SV_CUDA(svk::launch_permute(h->eb, h->psi, h->scratch.p, (const svk::PermDesc*)h->aux.p, Tp,
+                                ntiles, h->stream));
+    tock(h, t0, TK_PERM);
+    SV_CUDA(cudaMemcpyAsync(h->psi, h->scratch.p, state_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
+    h->info.permutation_sweeps += 1;
+    h->info.kernel_launches += 1;
+    h->info.hbm_bytes += 4.0 * (double)state_bytes(h);
+    return SV_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Pauli sweeps
+// ---------------------------------------------------------------------------
+struct PauliPlan {
+    std::vector<svk::PauliSweep> sweeps;
+    std::vector<svk::PauliTerm> terms;
+    int R = 4;
+};
+
+static sv_status plan_pauli(sv_handle h, const sv_observable* obs, const std::vector<int>& where,
+                            PauliPlan* out) {
+    const int n = (int)h->n;
+    if (!obs || obs->n_qubits != h->n || (obs->n_terms && (!obs->pauli || !obs->coeff)))
+        return fail(SV_ERR_ARG, "bad observable");
+    struct Raw { uint64_t x, z; double fre, fim; };
+    std::vector<Raw> diag, off;
+    for (uint32_t t = 0; t < obs->n_terms; ++t) {
+        uint64_t x = 0, z = 0;
+        int ny = 0;
+        for (int q = 0; q < n; ++q) {
+            uint8_t c = obs->pauli[(size_t)t * n + q];
+            uint64_t b = 1ull << where[q];
+            if (c == 1) x |= b;
+            else if (c == 2) { x |= b; z |= b; ++ny; }
+            else if (c == 3) z |= b;
+            else if (c != 0) return fail(SV_ERR_ARG, "pauli code must be 0..3");
+        }
+        double fr = obs->coeff[t], fi = 0;   // coeff * i^ny
+        for (int k = 0; k < (ny & 3); ++k) { double r = -fi, i2 = fr; fr = r; fi = i2; }
+        (x ? off : diag).push_back(Raw{x, z, fr, fi});
+    }
+    const int c = std::min(4, n);
+    const int Tp = std::min(n, 12);
+    out->R = std::min(4, Tp);
+    std::vector<char> used(off.size(), 0);
+    size_t left = off.size();
+    bool first = true;
+    while (first || left) {
+        uint64_t tile = (1ull << c) - 1;
+        for (size_t i = 0; i < off.size(); ++i)
+            if (!used[i] && __builtin_popcountll(tile | off[i].x) <= Tp) tile |= off[i].x;
+        for (int p = 0; p < n && __builtin_popcountll(tile) < Tp; ++p) tile |= 1ull << p;
+        if (!first) {
+            bool any = false;
+            for (size_t i = 0; i < off.size(); ++i)
+                if (!used[i] && (off[i].x & ~tile) == 0) any = true;
+            if (!any) return fail(SV_ERR_UNSUPPORTED, "a Pauli term has X/Y on more qubits than a tile holds");
+        }
+        svk::PauliSweep sw;
+        std::memset(&sw, 0, sizeof(sw));
+        sw.T = (uint32_t)Tp;
+        int nt = 0, ng = 0;
+        int tidx[64];
+        for (int p = 0; p < n; ++p) {
+            if ((tile >> p) & 1) {
+                tidx[p] = nt;
+                sw.tile_pos[nt] = (uint8_t)p;
+                sw.ptile[nt] = 1ull << p;
+                sw.swbit[nt] = svk::swizzle(1u << nt, h->eb);
+                ++nt;
+            } else {
+                tidx[p] = -1;
+                sw.glob_pos[ng++] = (uint8_t)p;
+            }
+        }
+        sw.n_glob = (uint32_t)ng;
+        sw.term_off = (uint32_t)out->terms.size();
+        auto add = [&](const Raw& r) {
+            svk::PauliTerm pt;
+            std::memset(&pt, 0, sizeof(pt));
+            pt.zmask = r.z;
+            pt.xmask = r.x;
+            for (uint64_t m = r.x; m; m &= m - 1) pt.xtile |= 1u << tidx[__builtin_ctzll(m)];
+            for (int j = 0; j < out->R; ++j)
+                if ((r.z >> sw.tile_pos[j]) & 1) pt.zreg |= 1u << j;
+            pt.fre = r.fre;
+            pt.fim = r.fim;
+            out->terms.push_back(pt);
+        };
+        if (first)
+            for (auto& r : diag) add(r);
+        for (size_t i = 0; i < off.size(); ++i)
+            if (!used[i] && (off[i].x & ~tile) == 0) {
+                add(off[i]);
+                used[i] = 1;
+                --left;
+            }
+        sw.n_terms = (uint32_t)(out->terms.size() - sw.term_off);
+        out->sweeps.push_back(sw);
+        first = false;
+    }
+    return SV_OK;
+}
+
+// Run the sweeps; lam != nullptr also forms lam = O psi.  Leaves the expectation
+// value (FP64) at red[0] on the device.
+static sv_status run_pauli(sv_handle h, const PauliPlan& pp, void* lam) {
+    const int n = (int)h->n;
+    const size_t szs = align16(pp.sweeps.size() * sizeof(svk::PauliSweep));
+    const size_t szt = align16(std::max<size_t>(1, pp.terms.size()) * sizeof(svk::PauliTerm));
+    SV_CUDA(h->aux.ensure(szs + szt));
+    h->aux_host.assign(szs + szt, 0);
+    std::memcpy(h->aux_host.data(), pp.sweeps.data(), pp.sweeps.size() * sizeof(svk::PauliSweep));
+    std::memcpy(h->aux_host.data() + szs, pp.terms.data(), pp.terms.size() * sizeof(svk::PauliTerm));
+    SV_CUDA(cudaMemcpyAsync(h->aux.p, h->aux_host.data(), szs + szt, cudaMemcpyHostToDevice, h->stream));
+    uint64_t total_blocks = 0;
+    for (auto& sw : pp.sweeps) total_blocks += 1ull << (n - (int)sw.T);
+    SV_CUDA(h->red.ensure((total_blocks + 16) * sizeof(double)));
+    double* part = (double*)h->red.p + 16;
+    uint64_t off = 0;
+    for (size_t i = 0; i < pp.sweeps.size(); ++i) {
+        const int T = (int)pp.sweeps[i].T;
+        const uint64_t nt = 1ull << (n - T);
+        cudaEvent_t t0 = tick(h);
+        SV_CUDA(svk::launch_pauli(h->eb, pp.R, h->psi, lam, i > 0,
+                                  (const svk::PauliSweep*)h->aux.p + i,
+                                  (const svk::PauliTerm*)((uint8_t*)h->aux.p + szs), part + off, T, nt,
+                                  h->stream));
+        tock(h, t0, TK_OBS);
+        off += nt;
+        h->info.reduction_sweeps += 1;
+        h->info.kernel_launches += 1;
+        h->info.hbm_bytes += (double)state_bytes(h) * (lam ? (i ? 3.0 : 2.0) : 1.0);
+    }
+    SV_CUDA(svk::launch_reduce_rows(part, total_blocks, 1, (double*)h->red.p, h->stream));
+    h->info.kernel_launches += 1;
+    return SV_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* sv_last_error(void) { return g_err.c_str(); }
+
+sv_status sv_create(uint32_t n_qubits, sv_dtype dtype, void* dev_state, void* cuda_stream,
+                    sv_handle* out) {
+    if (!out) return fail(SV_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_qubits < 1 || n_qubits > 34) return fail(SV_ERR_ARG, "n_qubits must be in [1, 34]");
+    if (dtype != SV_C64 && dtype != SV_C128) return fail(SV_ERR_ARG, "bad dtype");
+    if (dev_state && ((uintptr_t)dev_state & 15)) return fail(SV_ERR_ARG, "state buffer must be 16-byte aligned");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(SV_ERR_CUDA, "no CUDA device");
+    }
+    sv_handle h = new (std::nothrow) sv_handle_s();
+    if (!h) return fail(SV_ERR_OOM, "host allocation failed");
+    h->n = n_qubits;
+    h->dt = dtype;
+    h->eb = dtype == SV_C64 ? 8 : 16;
+    h->stream = (cudaStream_t)cuda_stream;
+    if (dev_state) {
+        h->psi = dev_state;
+        h->owns = false;
+    } else {
+        cudaError_t e = cudaMalloc(&h->psi, state_bytes(h));
+        if (e != cudaSuccess) {
+            delete h;
+            cudaGetLastError();
+            return fail(SV_ERR_OOM, std::string("cudaMalloc state: ") + cudaGetErrorString(e));
+        }
+        h->owns = true;
+        e = svk::launch_zero_state(h->eb, h->psi, 1ull << h->n, h->stream);
+        if (e != cudaSuccess) {
+            cudaFree(h->psi);
+            delete h;
+            return fail(SV_ERR_CUDA, cudaGetErrorString(e));
+        }
+    }
+    *out = h;
+    return SV_OK;
+}
+
+sv_status sv_timing_enable(sv_handle h, int enable) {
+    if (check_handle(h)) return SV_ERR_ARG;
+    h->timing = enable != 0;
+    return SV_OK;
+}
+
+sv_status sv_timing_read(sv_handle h, sv_timing* out, int reset) {
+    if (check_handle(h) || !out) return fail(SV_ERR_ARG, "null argument");
+    SV_CUDA(cudaStreamSynchronize(h->stream));
+    std::memset(out, 0, sizeof(*out));
+    for (auto& r : h->recs) {
+        float ms = 0.f;
+        SV_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+        switch (r.kind) {
+            case TK_STAGE: out->stage_ms += ms; out->stage_launches++; break;
+            case TK_BWD: out->backward_ms += ms; out->backward_launches++; break;
+            case TK_PERM: out->permute_ms += ms; out->permute_launches++; break;
+            default: out->observable_ms += ms; out->observable_launches++; break;
+        }
+    }
+    if (reset) {
+        h->recs.clear();
+        h->ev_used = 0;
+    }
+    return SV_OK;
+}
+
+sv_status sv_destroy(sv_handle h) {
+    if (!h) return SV_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    if (h->owns && h->psi) cudaFree(h->psi);
+    h->scratch.release();
+    h->fwd.buf.release();
+    h->bwd.buf.release();
+    h->partial.release();
+    h->slot_sum.release();
+    h->red.release();
+    h->aux.release();
+    delete h;
+    return SV_OK;
+}
+
+sv_status sv_info(sv_handle h, uint32_t* n_qubits, sv_dtype* dtype, void** dev_state) {
+    if (check_handle(h)) return SV_ERR_ARG;
+    if (n_qubits) *n_qubits = h->n;
+    if (dtype) *dtype = h->dt;
+    if (dev_state) *dev_state = h->psi;
+    return SV_OK;
+}
+
+sv_status sv_reset_zero(sv_handle h) {
+    if (check_handle(h)) return SV_ERR_ARG;
+    SV_CUDA(svk::launch_zero_state(h->eb, h->psi, 1ull << h->n, h->stream));
+    return SV_OK;
+}
+
+sv_status sv_set_state(sv_handle h, const void* dev_src) {
+    if (check_handle(h) || !dev_src) return fail(SV_ERR_ARG, "null argument");
+    SV_CUDA(cudaMemcpyAsync(h->psi, dev_src, state_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
+    return SV_OK;
+}
+sv_status sv_get_state(sv_handle h, void* dev_dst) {
+    if (check_handle(h) || !dev_dst) return fail(SV_ERR_ARG, "null argument");
+    SV_CUDA(cudaMemcpyAsync(dev_dst, h->psi, state_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
+    return SV_OK;
+}
+sv_status sv_set_state_host(sv_handle h, const void* host_src) {
+    if (check_handle(h) || !host_src) return fail(SV_ERR_ARG, "null argument");
+    SV_CUDA(cudaMemcpyAsync(h->psi, host_src, state_bytes(h), cudaMemcpyHostToDevice, h->stream));
+    return SV_OK;
+}
+sv_status sv_get_state_host(sv_handle h, void* host_dst) {
+    if (check_handle(h) || !host_dst) return fail(SV_ERR_ARG, "null argument");
+    SV_CUDA(cudaMemcpyAsync(host_dst, h->psi, state_bytes(h), cudaMemcpyDeviceToHost, h->stream));
+    SV_CUDA(cudaStreamSynchronize(h->stream));
+    return SV_OK;
+}
+
+sv_status sv_synchronize(sv_handle h) {
+    if (check_handle(h)) return SV_ERR_ARG;
+    SV_CUDA(cudaStreamSynchronize(h->stream));
+    return SV_OK;
+}
+
+sv_status sv_last_run_info(sv_handle h, sv_run_info* out) {
+    if (check_handle(h) || !out) return fail(SV_ERR_ARG, "null argument");
+    *out = h->info;
+    return SV_OK;
+}
+
+// ---------------- partitioning ----------------
+static sv_status build_plan(const sv_circuit* c, uint32_t L, uint32_t n_fixed, sv_plan** out) {
+    if (!out) return fail(SV_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!c || (c->n_gates && !c->gates)) return fail(SV_ERR_ARG, "null circuit");
+    if (c->n_qubits < 1 || c->n_qubits > (uint32_t)svk::kMaxQ) return fail(SV_ERR_ARG, "n_qubits out of range");
+    if (L < 1 || L > (uint32_t)svk::kMaxT) return fail(SV_ERR_ARG, "L must be in [1, 14]");
+    if (c->n_gates == 0) return fail(SV_ERR_ARG, "empty circuit");
+    if (c->n_gates > 32768) return fail(SV_ERR_ARG, "more than 32768 gates");
+    sv_plan* p = new (std::nothrow) sv_plan();
+    if (!p) return fail(SV_ERR_OOM, "host allocation failed");
+    svh::Plan& P = p->plan;
+    P.n = (int)c->n_qubits;
+    P.n_params = (int)c->n_params;
+    P.L = (int)L;
+    for (uint32_t i = 0; i < c->n_gates; ++i) {
+        const sv_gate& g = c->gates[i];
+        svh::GateRec r;
+        r.kind = g.kind;
+        if (g.kind < svh::K_H || g.kind > svh::K_LAST) { delete p; return fail(SV_ERR_ARG, "gate " + std::to_string(i) + ": unknown kind"); }
+        r.nq = svh::kind_nq(g.kind);
+        if (g.nq != r.nq) { delete p; return fail(SV_ERR_ARG, "gate " + std::to_string(i) + ": wrong qubit count"); }
+        for (int k = 0; k < r.nq; ++k) {
+            if (g.q[k] >= c->n_qubits) { delete p; return fail(SV_ERR_ARG, "gate " + std::to_string(i) + ": qubit out of range"); }
+            r.q[k] = g.q[k];
+        }
+        if (r.nq == 1) r.q[1] = -1;
+        if (r.nq == 2 && r.q[0] == r.q[1]) { delete p; return fail(SV_ERR_ARG, "gate " + std::to_string(i) + ": repeated qubit"); }
+        r.param = g.param;
+        if (g.param >= 0) {
+            bool ok = g.kind == svh::K_RX || g.kind == svh::K_RY || g.kind == svh::K_RZ ||
+                      g.kind == svh::K_P || g.kind == svh::K_CP;
+            if (!ok || (uint32_t)g.param >= c->n_params) { delete p; return fail(SV_ERR_ARG, "gate " + std::to_string(i) + ": bad parameter slot"); }
+        } else if (g.param != -1) {
+            delete p;
+            return fail(SV_ERR_ARG, "gate " + std::to_string(i) + ": param must be -1 or a slot");
+        }
+        for (int k = 0; k < 3; ++k) r.angle[k] = g.angle[k];
+        P.gates.push_back(r);
+    }
+    svh::relabel(P.n, P.gates, &P.phys, &P.final_map);
+    const int nf = (int)std::min<uint32_t>(n_fixed, std::min<uint32_t>(L, c->n_qubits));
+    P.n_fixed = nf;
+    const uint64_t fixed = nf ? ((1ull << nf) - 1) : 0;
+    const uint64_t universe = (P.n >= 64) ? ~0ull : ((1ull << P.n) - 1);
+    std::string err = svh::partition_core(P.n, P.phys, (int)L, fixed, universe, &P.top, &P.cc);
+    if (!err.empty()) {
+        delete p;
+        return fail(SV_ERR_PARTITION, err);
+    }
+    *out = p;
+    return SV_OK;
+}
+
+sv_status sv_partition(const sv_circuit* circuit, uint32_t L, sv_plan** out) {
+    // reserve the coalescing low bits, but always leave one free local qubit
+    return build_plan(circuit, L, L > 1 ? std::min<uint32_t>(4, L - 1) : 0, out);
+}
+sv_status sv_partition_ex(const sv_circuit* circuit, uint32_t L, uint32_t n_fixed, sv_plan** out) {
+    return build_plan(circuit, L, n_fixed, out);
+}
+
+sv_status sv_plan_stages(const sv_plan* plan, uint32_t* n_stages, uint64_t* local_masks,
+                         uint32_t* gate_counts) {
+    if (!plan || !n_stages) return fail(SV_ERR_ARG, "null argument");
+    const auto& top = plan->plan.top;
+    if ((local_masks || gate_counts) && *n_stages < top.local.size())
+        return fail(SV_ERR_ARG, "arrays too small");
+    *n_stages = (uint32_t)top.local.size();
+    for (size_t s = 0; s < top.local.size(); ++s) {
+        if (local_masks) local_masks[s] = top.local[s];
+        if (gate_counts) gate_counts[s] = (uint32_t)top.ids[s].size();
+    }
+    return SV_OK;
+}
+
+sv_status sv_plan_order(const sv_plan* plan, uint32_t* gate_order, uint32_t* final_map) {
+    if (!plan) return fail(SV_ERR_ARG, "null plan");
+    if (gate_order) {
+        size_t k = 0;
+        for (auto& ids : plan->plan.top.ids)
+            for (uint32_t i : ids) gate_order[k++] = i;
+    }
+    if (final_map)
+        for (int q = 0; q < plan->plan.n; ++q) final_map[q] = (uint32_t)plan->plan.final_map[q];
+    return SV_OK;
+}
+
+sv_status sv_plan_centrality(const sv_plan* plan, uint32_t* reach, uint64_t* dist, uint32_t* level) {
+    if (!plan) return fail(SV_ERR_ARG, "null plan");
+    const auto& cc = plan->plan.cc;
+    for (size_t i = 0; i < cc.reach.size(); ++i) {
+        if (reach) reach[i] = cc.reach[i];
+        if (dist) dist[i] = cc.dist[i];
+        if (level) level[i] = cc.level[i];
+    }
+    return SV_OK;
+}
+
+sv_status sv_plan_destroy(sv_plan* plan) {
+    delete plan;
+    return SV_OK;
+}
+
+// ---------------- execution ----------------
+static int rmax_fwd(int eb) { return eb == 8 ? 5 : 4; }
+static int rmax_bwd(int eb) { return eb == 8 ? 4 : 3; }
+
+static sv_status run_forward(sv_handle h, const sv_plan* plan, const double* params, bool permute_back) {
+    const svh::Plan& P = plan->plan;
+    svh::Program prog;
+    std::string err = svh::lower(P, params, h->eb, rmax_fwd(h->eb), false, &prog);
+    if (!err.empty()) return fail(SV_ERR_ARG, err);
+    for (auto& st : prog.stages)
+        if (((size_t)h->eb << st.T) > 227 * 1024) return fail(SV_ERR_UNSUPPORTED, "tile too wide for shared memory at this dtype (use L <= 13 for complex128)");
+    sv_status s = upload_program(h, prog, &h->fwd);
+    if (s) return s;
+    for (size_t i = 0; i < prog.stages.size(); ++i) {
+        const svk::Stage& st = prog.stages[i];
+        const uint64_t ntiles = 1ull << (h->n - st.T);
+        cudaEvent_t t0 = tick(h);
+        SV_CUDA(svk::launch_stage_fwd(h->eb, (int)st.R, h->psi, h->fwd.stages + i, h->fwd.groups,
+                                      h->fwd.ops, h->fwd.terms, (int)st.T, ntiles, h->stream));
+        tock(h, t0, TK_STAGE);
+        h->info.stage_sweeps += 1;
+        h->info.kernel_launches += 1;
+        h->info.hbm_bytes += 2.0 * (double)state_bytes(h);
+    }
+    if (permute_back && !prog.identity_map) {
+        std::vector<uint32_t> m(P.n);
+        for (int q = 0; q < P.n; ++q) m[q] = (uint32_t)P.final_map[q];
+        s = do_permute(h, m.data());
+        if (s) return s;
+    }
+    return SV_OK;
+}
+
+sv_status sv_run(sv_handle h, const sv_plan* plan, const double* params, sv_prec prec) {
+    if (check_handle(h) || !plan) return fail(SV_ERR_ARG, "null argument");
+    if (plan->plan.n != (int)h->n) return fail(SV_ERR_ARG, "plan width differs from the state");
+    if (plan->plan.n_params > 0 && !params) return fail(SV_ERR_ARG, "params is NULL");
+    if (prec != SV_PREC_CUDACORE) return fail(SV_ERR_UNSUPPORTED, "tensor-core precision needs a GEMM plan");
+    h->info = sv_run_info{};
+    return run_forward(h, plan, params, true);
+}
+
+sv_status sv_permute(sv_handle h, const uint32_t* phys_of_qubit) {
+    if (check_handle(h) || !phys_of_qubit) return fail(SV_ERR_ARG, "null argument");
+    return do_permute(h, phys_of_qubit);
+}
+
+sv_status sv_norm(sv_handle h, double* out) {
+    if (check_handle(h) || !out) return fail(SV_ERR_ARG, "null argument");
+    SV_CUDA(h->red.ensure((152 * 16 + 16) * sizeof(double)));
+    double* part = (double*)h->red.p + 16;
+    uint32_t nb = 0;
+    cudaEvent_t t0 = tick(h);
+    SV_CUDA(svk::launch_norm(h->eb, h->psi, 1ull << h->n, part, &nb, h->stream));
+    tock(h, t0, TK_OBS);
+    h->info.kernel_launches += 2;
+    SV_CUDA(svk::launch_reduce_rows(part, nb, 1, (double*)h->red.p, h->stream));
+    SV_CUDA(cudaMemcpyAsync(out, h->red.p, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    SV_CUDA(cudaStreamSynchronize(h->stream));
+    return SV_OK;
+}
+
+sv_status sv_expval(sv_handle h, const sv_observable* obs, double* out) {
+    if (check_handle(h) || !out) return fail(SV_ERR_ARG, "null argument");
+    std::vector<int> ident(h->n);
+    for (uint32_t q = 0; q < h->n; ++q) ident[q] = (int)q;
+    PauliPlan pp;
+    sv_status s = plan_pauli(h, obs, ident, &pp);
+    if (s) return s;
+    s = run_pauli(h, pp, nullptr);
+    if (s) return s;
+    SV_CUDA(cudaMemcpyAsync(out, h->red.p, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    SV_CUDA(cudaStreamSynchronize(h->stream));
+    return SV_OK;
+}
+
+sv_status sv_grad(sv_handle h, const sv_plan* plan, const double* params, const sv_observable* obs,
+                  double* expval_out, double* grad_out) {
+    if (check_handle(h) || !plan || !obs) return fail(SV_ERR_ARG, "null argument");
+    const svh::Plan& P = plan->plan;
+    if (P.n != (int)h->n) return fail(SV_ERR_ARG, "plan width differs from the state");
+    if (P.n_params > 0 && (!params || !grad_out)) return fail(SV_ERR_ARG, "params / grad_out is NULL");
+    h->info = sv_run_info{};
+    // lower the backward program first so unsupported parameters fail before any work
+    svh::Program bprog;
+    std::string err = svh::lower(P, params, h->eb, rmax_bwd(h->eb), true, &bprog);
+    if (!err.empty()) return fail(err.find("not supported") != std::string::npos ? SV_ERR_UNSUPPORTED : SV_ERR_ARG, err);
+    for (auto& st : bprog.stages)
+        if (((size_t)h->eb << (st.T + 1)) > 200 * 1024) return fail(SV_ERR_UNSUPPORTED, "tile too wide for the adjoint sweep (psi and lambda tiles must fit shared memory)");
+    sv_status s = run_forward(h, plan, params, false);
+    if (s) return s;
+    // lambda = O psi in the forward program's final physical layout
+    PauliPlan pp;
+    s = plan_pauli(h, obs, P.final_map, &pp);
+    if (s) return s;
+    SV_CUDA(h->scratch.ensure(state_bytes(h)));
+    s = run_pauli(h, pp, h->scratch.p);
+    if (s) return s;
+    double E = 0.0;
+    SV_CUDA(cudaMemcpyAsync(&E, h->red.p, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    s = upload_program(h, bprog, &h->bwd);
+    if (s) return s;
+    const size_t nslots_total = bprog.slot_param.size();
+    size_t maxpart = 1;
+    for (auto& st : bprog.stages)
+        maxpart = std::max(maxpart, (size_t)st.n_slots << (h->n - st.T));
+    SV_CUDA(h->partial.ensure(maxpart * sizeof(double)));
+    SV_CUDA(h->slot_sum.ensure(std::max<size_t>(1, nslots_total) * sizeof(double)));
+    for (size_t i = 0; i < bprog.stages.size(); ++i) {
+        const svk::Stage& st = bprog.stages[i];
+        const uint64_t ntiles = 1ull << (h->n - st.T);
+        cudaEvent_t t0 = tick(h);
+        SV_CUDA(svk::launch_stage_bwd(h->eb, (int)st.R, h->psi, h->scratch.p, h->bwd.stages + i,
+                                      h->bwd.groups, h->bwd.ops, h->bwd.terms, (double*)h->partial.p,
+                                      (int)st.T, st.n_slots, ntiles, h->stream));
+        tock(h, t0, TK_BWD);
+        h->info.backward_sweeps += 1;
+        h->info.kernel_launches += 1;
+        h->info.hbm_bytes += 4.0 * (double)state_bytes(h);
+        if (st.n_slots) {
+            SV_CUDA(svk::launch_reduce_rows((double*)h->partial.p, ntiles, st.n_slots,
+                                            (double*)h->slot_sum.p + st.slot_off, h->stream));
+            h->info.kernel_launches += 1;
+        }
+    }
+    std::vector<double> slots(nslots_total);
+    if (nslots_total)
+        SV_CUDA(cudaMemcpyAsync(slots.data(), h->slot_sum.p, nslots_total * sizeof(double),
+                                cudaMemcpyDeviceToHost, h->stream));
+    SV_CUDA(cudaStreamSynchronize(h->stream));
+    if (expval_out) *expval_out = E;
+    if (grad_out) {
+        for (int k = 0; k < P.n_params; ++k) grad_out[k] = 0.0;
+        for (size_t i = 0; i < nslots_total; ++i) grad_out[bprog.slot_param[i]] += slots[i];
+    }
+    return SV_OK;
+}
+
+}  // extern "C"

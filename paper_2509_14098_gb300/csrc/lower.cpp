@@ -1,0 +1,398 @@
+// lower.cpp — turn a partition into the device program of one direction.
+//
+// For each partition (stage) the tile bits are its local set (Sec. 4.3: the state
+// tensor is split on the partition's global dimensions, each tile packed into
+// shared memory).  Inside a stage the partitioner is invoked again with the
+// register budget R (the next memory level, Sec. 4.2: "the algorithm can be invoked
+// for each of the newly determined partitions"), giving register groups.
+//
+// Gates become micro-ops on the amplitudes a thread holds.  Diagonal gates (Z, S,
+// T, P, RZ, CZ, CP) are kept as phase terms and applied just before the next dense
+// gate on one of their qubits, or at the end of the circuit: they commute with
+// every gate in between, so the product is unchanged (only rounding differs).  A
+// term on the dense gate's target and a non-register bit becomes a twiddle of that
+// gate (the linear phase a butterfly needs); a term on two register bits is applied
+// directly.  SWAP is a relabel and emits nothing.
+//
+// Backward (adjoint) programs visit the stages and their gates in reverse with every
+// gate conjugate-transposed, and emit, for each parametric rotation
+// U = exp(-i theta G / 2) (G = X, Y, Z), an op accumulating Im <lambda|G|psi> at the
+// gate's position, which equals dE/dtheta = 2 Re <lambda| dU/dtheta psi>.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+
+#include "planner.h"
+
+namespace svh {
+
+namespace {
+
+struct Pend {
+    double angle = 0.0;
+    std::vector<int> params;   // RZ parameters whose gradient is evaluated at emission
+};
+
+class Lowerer {
+  public:
+    Lowerer(const Plan& p, const double* params, int eb, int rmax, bool bwd, Program* out)
+        : P_(p), params_(params), eb_(eb), rmax_(rmax), bwd_(bwd), out_(out) {}
+
+    std::string run();
+
+  private:
+    const Plan& P_;
+    const double* params_;
+    int eb_, rmax_;
+    bool bwd_;
+    Program* out_;
+    std::map<uint64_t, Pend> pending_;
+    double gphase_ = 0.0;
+    int regidx_[64];
+    svk::Group* grp_ = nullptr;
+    uint32_t stage_slots_ = 0;
+    uint32_t slot_base_ = 0;
+
+    double theta(const GateRec& g, int i = 0) const {
+        return g.param >= 0 ? params_[g.param] : g.angle[i];
+    }
+    svk::Op& new_op(uint8_t type, int j) {
+        out_->ops.emplace_back();
+        svk::Op& o = out_->ops.back();
+        std::memset(&o, 0, sizeof(o));
+        o.type = type;
+        o.j = (uint8_t)j;
+        grp_->n_ops++;
+        return o;
+    }
+    int new_slot(int param) {
+        out_->slot_param.push_back(param);
+        return (int)(stage_slots_++);
+    }
+    void add_term(uint64_t mask, double angle, int param) {
+        Pend& p = pending_[mask];
+        p.angle += angle;
+        if (param >= 0) p.params.push_back(param);
+    }
+    void emit_grad_z(int bit, int param);
+    void flush_bit(int t);
+    void flush_all();
+    std::string gate(const GateRec& g, const PGate& pg);
+    std::string stage(int s);
+};
+
+void Lowerer::emit_grad_z(int bit, int param) {
+    int r = regidx_[bit];
+    svk::Op& o = new_op(svk::OP_GRAD_Z, r >= 0 ? r : 0);
+    o.u = r >= 0 ? 0 : 1;
+    o.ctrl_fix = r >= 0 ? 0 : (1ull << bit);
+    o.slot = (uint32_t)new_slot(param);
+}
+
+// Apply every pending term that involves physical bit t (a register bit of the
+// current group) — right before a dense gate on t.
+void Lowerer::flush_bit(int t) {
+    const uint64_t tb = 1ull << t;
+    const int jt = regidx_[t];
+    double cangle = 0.0;
+    bool any1 = false;
+    std::vector<svk::Term> terms;
+    std::map<int, double> pair;
+    for (auto it = pending_.begin(); it != pending_.end();) {
+        if (!(it->first & tb)) {
+            ++it;
+            continue;
+        }
+        if (bwd_)
+            for (int prm : it->second.params) emit_grad_z(t, prm);
+        uint64_t other = it->first & ~tb;
+        if (other == 0) {
+            cangle += it->second.angle;
+            any1 = true;
+        } else {
+            int u = __builtin_ctzll(other);
+            if (regidx_[u] >= 0) {
+                pair[regidx_[u]] += it->second.angle;
+            } else {
+                terms.push_back(svk::Term{other, it->second.angle});
+                any1 = true;
+            }
+        }
+        it = pending_.erase(it);
+    }
+    if (any1) {
+        svk::Op& o = new_op(svk::OP_PHASE1, jt);
+        o.m[0] = std::cos(cangle);
+        o.m[1] = std::sin(cangle);
+        o.term_off = (uint32_t)out_->terms.size();
+        o.n_terms = (uint32_t)terms.size();
+        for (auto& x : terms) out_->terms.push_back(x);
+    }
+    for (auto& kv : pair) {
+        svk::Op& o = new_op(svk::OP_PHASE2, jt);
+        o.u = (uint8_t)kv.first;
+        o.m[0] = std::cos(kv.second);
+        o.m[1] = std::sin(kv.second);
+    }
+}
+
+// End of the program: apply every remaining term and the global phase.
+void Lowerer::flush_all() {
+    if (bwd_) {
+        for (auto& kv : pending_)
+            for (int prm : kv.second.params) emit_grad_z(__builtin_ctzll(kv.first), prm);
+    }
+    std::vector<svk::Term> t0;
+    std::map<int, std::pair<double, std::vector<svk::Term>>> t1;
+    std::map<std::pair<int, int>, double> t2;
+    for (auto& kv : pending_) {
+        uint64_t m = kv.first;
+        int regs[2], nreg = 0;
+        uint64_t rest = 0;
+        for (uint64_t x = m; x; x &= x - 1) {
+            int b = __builtin_ctzll(x);
+            if (regidx_[b] >= 0) regs[nreg++] = regidx_[b];
+            else rest |= 1ull << b;
+        }
+        if (nreg == 0) {
+            t0.push_back(svk::Term{m, kv.second.angle});
+        } else if (nreg == 1) {
+            auto& e = t1[regs[0]];
+            if (rest == 0) e.first += kv.second.angle;
+            else e.second.push_back(svk::Term{rest, kv.second.angle});
+        } else {
+            t2[{regs[0], regs[1]}] += kv.second.angle;
+        }
+    }
+    pending_.clear();
+    {
+        svk::Op& o = new_op(svk::OP_PHASE0, 0);
+        o.m[0] = std::cos(gphase_);
+        o.m[1] = std::sin(gphase_);
+        o.term_off = (uint32_t)out_->terms.size();
+        o.n_terms = (uint32_t)t0.size();
+        for (auto& x : t0) out_->terms.push_back(x);
+    }
+    for (auto& kv : t1) {
+        svk::Op& o = new_op(svk::OP_PHASE1, kv.first);
+        o.m[0] = std::cos(kv.second.first);
+        o.m[1] = std::sin(kv.second.first);
+        o.term_off = (uint32_t)out_->terms.size();
+        o.n_terms = (uint32_t)kv.second.second.size();
+        for (auto& x : kv.second.second) out_->terms.push_back(x);
+    }
+    for (auto& kv : t2) {
+        svk::Op& o = new_op(svk::OP_PHASE2, kv.first.first);
+        o.u = (uint8_t)kv.first.second;
+        o.m[0] = std::cos(kv.second);
+        o.m[1] = std::sin(kv.second);
+    }
+}
+
+// 2x2 matrices (row-major re,im pairs).  Backward uses the conjugate transpose.
+static void set_m(double* m, double a, double b, double c, double d, double e, double f, double g,
+                  double h) {
+    m[0] = a; m[1] = b; m[2] = c; m[3] = d; m[4] = e; m[5] = f; m[6] = g; m[7] = h;
+}
+static void dagger(double* m) {
+    double r[8];
+    // (U^dagger)_{ij} = conj(U_{ji})
+    r[0] = m[0]; r[1] = -m[1];
+    r[2] = m[4]; r[3] = -m[5];
+    r[4] = m[2]; r[5] = -m[3];
+    r[6] = m[6]; r[7] = -m[7];
+    std::memcpy(m, r, sizeof(r));
+}
+
+std::string Lowerer::gate(const GateRec& g, const PGate& pg) {
+    const double s = bwd_ ? -1.0 : 1.0;   // angle sign for diagonal terms
+    switch (g.kind) {
+        case K_SWAP:
+            return "";
+        case K_Z: add_term(1ull << pg.p[0], s * M_PI, -1); return "";
+        case K_S: add_term(1ull << pg.p[0], s * M_PI / 2, -1); return "";
+        case K_SDG: add_term(1ull << pg.p[0], -s * M_PI / 2, -1); return "";
+        case K_T: add_term(1ull << pg.p[0], s * M_PI / 4, -1); return "";
+        case K_TDG: add_term(1ull << pg.p[0], -s * M_PI / 4, -1); return "";
+        case K_P:
+            if (bwd_ && g.param >= 0) return "gradient of a P parameter is not supported";
+            add_term(1ull << pg.p[0], s * theta(g), -1);
+            return "";
+        case K_RZ: {
+            double t = theta(g);
+            gphase_ += -s * t / 2;
+            add_term(1ull << pg.p[0], s * t, bwd_ ? g.param : -1);
+            return "";
+        }
+        case K_CZ: add_term((1ull << pg.p[0]) | (1ull << pg.p[1]), s * M_PI, -1); return "";
+        case K_CP:
+            if (bwd_ && g.param >= 0) return "gradient of a CP parameter is not supported";
+            add_term((1ull << pg.p[0]) | (1ull << pg.p[1]), s * theta(g), -1);
+            return "";
+        default: break;
+    }
+    // dense gate on target t (controlled gates: q[1]); t is a register bit
+    const int t = kind_is_controlled(g.kind) ? pg.p[1] : pg.p[0];
+    const int jt = regidx_[t];
+    if (jt < 0) return "internal: dense gate target is not a register bit";
+    flush_bit(t);
+    double m[8];
+    uint8_t type = svk::OP_U;
+    switch (g.kind) {
+        case K_H: {
+            double r = 1.0 / std::sqrt(2.0);
+            set_m(m, r, 0, r, 0, r, 0, -r, 0);
+            type = svk::OP_UR;
+            break;
+        }
+        case K_X: case K_CX: set_m(m, 0, 0, 1, 0, 1, 0, 0, 0); type = svk::OP_X; break;
+        case K_Y: case K_CY: set_m(m, 0, 0, 0, -1, 0, 1, 0, 0); break;
+        case K_RX: {
+            double c = std::cos(theta(g) / 2), sn = std::sin(theta(g) / 2);
+            set_m(m, c, 0, 0, -sn, 0, -sn, c, 0);
+            break;
+        }
+        case K_RY: {
+            double c = std::cos(theta(g) / 2), sn = std::sin(theta(g) / 2);
+            set_m(m, c, 0, -sn, 0, sn, 0, c, 0);
+            type = svk::OP_UR;
+            break;
+        }
+        case K_U3: {
+            double th = g.angle[0], ph = g.angle[1], la = g.angle[2];
+            double c = std::cos(th / 2), sn = std::sin(th / 2);
+            set_m(m, c, 0, -std::cos(la) * sn, -std::sin(la) * sn, std::cos(ph) * sn, std::sin(ph) * sn,
+                  std::cos(ph + la) * c, std::sin(ph + la) * c);
+            break;
+        }
+        default: return "internal: unknown gate kind";
+    }
+    if (bwd_) {
+        dagger(m);
+        if (g.param >= 0) {
+            if (g.kind != K_RX && g.kind != K_RY) return "gradient of this parameter kind is not supported";
+            svk::Op& go = new_op(g.kind == K_RX ? svk::OP_GRAD_X : svk::OP_GRAD_Y, jt);
+            go.slot = (uint32_t)new_slot(g.param);
+        }
+    }
+    svk::Op& o = new_op(type, jt);
+    std::memcpy(o.m, m, sizeof(m));
+    if (kind_is_controlled(g.kind)) {
+        int c = pg.p[0];
+        if (regidx_[c] >= 0) o.ctrl_reg = 1u << regidx_[c];
+        else o.ctrl_fix = 1ull << c;
+    }
+    return "";
+}
+
+std::string Lowerer::stage(int s) {
+    // complex64 tiles are staged in 16-byte chunks of two amplitudes, so the tile
+    // always holds physical bit 0 (a plan without reserved low bits may not)
+    const uint64_t tile = P_.top.local[s] | (eb_ == 8 ? 1ull : 0ull);
+    const int n = P_.n;
+    svk::Stage st;
+    std::memset(&st, 0, sizeof(st));
+    int T = 0;
+    for (int b = 0; b < n; ++b)
+        if ((tile >> b) & 1) st.tile_pos[T++] = (uint8_t)b;
+    if (T > svk::kMaxT) return "tile wider than 14 qubits";
+    int ng = 0;
+    for (int b = 0; b < n; ++b)
+        if (!((tile >> b) & 1)) st.glob_pos[ng++] = (uint8_t)b;
+    const int R = std::min(rmax_, T);
+    st.T = (uint32_t)T;
+    st.R = (uint32_t)R;
+    st.n_glob = (uint32_t)ng;
+    for (int b = 0; b < T; ++b) {
+        st.ptile[b] = 1ull << st.tile_pos[b];
+        st.swbit[b] = svk::swizzle(1u << b, eb_);
+    }
+    int tidx[64];
+    for (int b = 0; b < 64; ++b) tidx[b] = -1;
+    for (int b = 0; b < T; ++b) tidx[st.tile_pos[b]] = b;
+
+    // stage gates in direction order, then the register-level partition
+    std::vector<uint32_t> ids = P_.top.ids[s];
+    if (bwd_) std::reverse(ids.begin(), ids.end());
+    std::vector<PGate> sub;
+    sub.reserve(ids.size());
+    for (uint32_t i : ids) sub.push_back(P_.phys[i]);
+    Partition groups;
+    std::string err = partition_core(n, sub, R, 0, tile, &groups, nullptr);
+    if (!err.empty()) return "register partition: " + err;
+
+    st.group_off = (uint32_t)out_->groups.size();
+    st.n_groups = (uint32_t)groups.local.size();
+    st.slot_off = slot_base_;
+    stage_slots_ = 0;
+    for (size_t gi = 0; gi < groups.local.size(); ++gi) {
+        out_->groups.emplace_back();
+        svk::Group& G = out_->groups.back();
+        std::memset(&G, 0, sizeof(G));
+        G.op_off = (uint32_t)out_->ops.size();
+        grp_ = &G;
+        for (int b = 0; b < 64; ++b) regidx_[b] = -1;
+        int nr = 0, nt = 0;
+        for (int b = 0; b < T; ++b) {
+            if ((groups.local[gi] >> st.tile_pos[b]) & 1) {
+                G.reg_pos[nr] = (uint8_t)b;
+                regidx_[st.tile_pos[b]] = nr;
+                ++nr;
+            } else {
+                G.thr_pos[nt++] = (uint8_t)b;
+            }
+        }
+        if (nr != R) return "internal: register group width mismatch";
+        G.pairs = (eb_ == 8 && G.reg_pos[0] == 0) ? 1 : 0;
+        for (int j = 0; j < R; ++j) G.sreg[j] = svk::swizzle(1u << G.reg_pos[j], eb_);
+        for (int i = 0; i < nt; ++i) {
+            G.sthr[i] = svk::swizzle(1u << G.thr_pos[i], eb_);
+            G.pthr[i] = 1ull << st.tile_pos[G.thr_pos[i]];
+        }
+        for (uint32_t sid : groups.ids[gi]) {
+            uint32_t gid = ids[sid];
+            err = gate(P_.gates[gid], P_.phys[gid]);
+            if (!err.empty()) return err;
+        }
+        if (s == (bwd_ ? 0 : (int)P_.top.local.size() - 1) && gi + 1 == groups.local.size())
+            flush_all();
+        grp_ = nullptr;
+    }
+    (void)tidx;
+    st.n_slots = stage_slots_;
+    slot_base_ += stage_slots_;
+    out_->stages.push_back(st);
+    return "";
+}
+
+std::string Lowerer::run() {
+    out_->stages.clear();
+    out_->groups.clear();
+    out_->ops.clear();
+    out_->terms.clear();
+    out_->slot_param.clear();
+    out_->groups.reserve(4096);
+    const int S = (int)P_.top.local.size();
+    if (S == 0) return "empty plan";
+    for (int k = 0; k < S; ++k) {
+        int s = bwd_ ? S - 1 - k : k;
+        std::string err = stage(s);
+        if (!err.empty()) return err;
+    }
+    out_->identity_map = true;
+    for (int q = 0; q < P_.n; ++q)
+        if (P_.final_map[q] != q) out_->identity_map = false;
+    return "";
+}
+
+}  // namespace
+
+std::string lower(const Plan& plan, const double* params, int elem_bytes, int rmax, bool backward,
+                  Program* out) {
+    if (plan.n_params > 0 && params == nullptr) return "circuit has parameters but params is NULL";
+    Lowerer L(plan, params, elem_bytes, rmax, backward, out);
+    return L.run();
+}
+
+}  // namespace svh

@@ -1,0 +1,90 @@
+// planner.h — host-side partitioner and program lowering (internal).
+#pragma once
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "program.h"
+
+namespace svh {
+
+enum Kind {
+    K_H = 1, K_X, K_Y, K_Z, K_S, K_SDG, K_T, K_TDG, K_RX, K_RY, K_RZ, K_P, K_U3, K_CX,
+    K_CY, K_CZ, K_CP, K_SWAP, K_LAST = K_SWAP
+};
+
+inline bool kind_is_diagonal(int k) {
+    return k == K_Z || k == K_S || k == K_SDG || k == K_T || k == K_TDG || k == K_RZ || k == K_P ||
+           k == K_CZ || k == K_CP;
+}
+inline bool kind_is_controlled(int k) { return k == K_CX || k == K_CY; }
+inline int kind_nq(int k) { return (k >= K_CX) ? 2 : 1; }
+
+struct GateRec {
+    int kind;
+    int nq;
+    int q[2];       // circuit qubits (wires)
+    int param;      // -1 = fixed angles
+    double angle[3];
+};
+
+// A gate as the partitioner sees it: physical bit positions after SWAP relabels.
+struct PGate {
+    int kind;
+    int nq;
+    int p[2];
+};
+
+struct Partition {
+    std::vector<uint64_t> local;                 // physical-bit mask per stage
+    std::vector<std::vector<uint32_t>> ids;      // indices into the gate list, execution order
+};
+
+struct Centrality {
+    std::vector<uint32_t> reach;   // |RN(v)|
+    std::vector<uint64_t> dist;    // sum over RN(v) of (l_x - l_v)
+    std::vector<uint32_t> level;   // critical-path length l_v
+};
+
+// Closeness-centrality partitioner (Sec. 4.1-4.2) over gates given in physical bits.
+// L: local-bit budget; fixed: bits local in every partition; universe: bits that may
+// be used to fill a partition's local set up to min(L, |universe|) after the cut.
+// Returns "" on success or an error message (status SV_ERR_PARTITION).
+std::string partition_core(int nbits, const std::vector<PGate>& gates, int L, uint64_t fixed,
+                           uint64_t universe, Partition* out, Centrality* cc);
+
+// Physical positions of every gate after replaying the SWAP relabels in circuit
+// order, and the final map wire -> physical bit.
+void relabel(int n, const std::vector<GateRec>& gates, std::vector<PGate>* phys,
+             std::vector<int>* final_map);
+
+struct Plan {
+    int n = 0;
+    int n_params = 0;
+    int L = 0;
+    int n_fixed = 0;
+    std::vector<GateRec> gates;
+    std::vector<PGate> phys;
+    std::vector<int> final_map;
+    Partition top;
+    Centrality cc;
+};
+
+// Lowered program of one direction, ready to upload.
+struct Program {
+    std::vector<svk::Stage> stages;
+    std::vector<svk::Group> groups;
+    std::vector<svk::Op> ops;
+    std::vector<svk::Term> terms;
+    std::vector<int> slot_param;   // backward: global gradient slot -> parameter
+    bool identity_map = true;
+};
+
+// Lower a plan with bound parameters.  rmax: register bits per thread.
+// backward: un-apply the stages in reverse (conjugate-transposed gates) and emit
+// gradient ops for parametric RX / RY / RZ gates.  Returns "" or an error.
+std::string lower(const Plan& plan, const double* params, int elem_bytes, int rmax, bool backward,
+                  Program* out);
+
+}  // namespace svh

@@ -1,0 +1,110 @@
+// program.h — device program format shared by the host planner and the kernels.
+//
+// A plan is lowered into a flat program per direction (forward / backward):
+//   Stage[]  one per partition (one HBM sweep each): tile geometry
+//   Group[]  register groups inside a stage (the partitioner re-run with the
+//            register budget, i.e. the paper's next memory level, Sec. 4.2)
+//   Op[]     micro-ops applied to the amplitudes a thread holds in registers
+//   Term[]   phase terms that depend on bits outside the registers
+//
+// Index spaces
+//   physical bit  p in [0, n): bit of the amplitude index in HBM
+//   tile bit      b in [0, T): position inside a shared-memory tile; tile bit b
+//                 is physical bit tile_pos[b] (ascending)
+//   register bit  j in [0, R): bit of the per-thread register index k; register
+//                 bit j is tile bit reg_pos[j] (ascending)
+//   thread bit    i in [0, T-R): bit of threadIdx.x; tile bit thr_pos[i]
+// A thread's "fixed index" is the physical index of its amplitudes with every
+// register bit zero (tile base | thread bits); phase terms and controls on
+// non-register bits are evaluated on it.
+#pragma once
+#include <stdint.h>
+
+#ifdef __CUDACC__
+#define SVK_HD __host__ __device__ __forceinline__
+#else
+#define SVK_HD inline
+#endif
+
+namespace svk {
+
+constexpr int kMaxT = 14;      // widest tile (2^14 amplitudes)
+constexpr int kMaxR = 5;       // widest register group (32 amplitudes per thread)
+constexpr int kMaxQ = 40;      // widest state the planner accepts
+
+enum OpType : uint8_t {
+    OP_U = 0,       // dense complex 2x2 on register bit j (optionally controlled)
+    OP_UR = 1,      // dense real 2x2 on register bit j
+    OP_X = 2,       // swap the pair on register bit j (X / CX target)
+    OP_PHASE0 = 3,  // every amplitude *= c * exp(i * sum of terms on the fixed index)
+    OP_PHASE1 = 4,  // amplitudes with register bit j set *= c * exp(i * sum of terms)
+    OP_PHASE2 = 5,  // amplitudes with register bits j and u set *= c
+    OP_GRAD_X = 6,  // gradient slot += Im <lam| X_j |psi>  (backward only)
+    OP_GRAD_Y = 7,  // gradient slot += Im <lam| Y_j |psi>
+    OP_GRAD_Z = 8,  // gradient slot += Im <lam| Z_b |psi>, b register bit j (u=0) or
+                    // the physical bit in ctrl_fix (u=1)
+};
+
+struct Op {                 // 96 bytes
+    uint8_t type;
+    uint8_t j;              // register bit (target)
+    uint8_t u;              // second register bit (PHASE2) / flag (GRAD_Z)
+    uint8_t pad0;
+    uint32_t ctrl_reg;      // controls on register bits (mask over k)
+    uint64_t ctrl_fix;      // controls on non-register bits (mask over the fixed index)
+    uint32_t term_off;      // first Term of this op
+    uint32_t n_terms;
+    uint32_t slot;          // gradient slot (GRAD ops): index into the stage's slot list
+    uint32_t pad1;
+    double m[8];            // row-major 2x2 (re, im) pairs; PHASE ops use m[0], m[1]
+};
+
+struct Term {               // phase angle added when every bit of mask is set
+    uint64_t mask;
+    double angle;
+};
+
+struct Group {
+    uint32_t op_off, n_ops;
+    uint8_t reg_pos[kMaxR];
+    uint8_t thr_pos[kMaxT];
+    uint8_t pairs;          // tile bit 0 is register bit 0: load amplitude pairs as 16 B
+    uint8_t pad[4];
+    uint32_t sreg[kMaxR];   // swizzled shared-memory element offset of each register bit
+    uint32_t sthr[kMaxT];   // swizzled shared-memory element offset of each thread bit
+    uint64_t pthr[kMaxT];   // physical index value of each thread bit (1 << phys)
+};
+
+struct Stage {
+    uint32_t T, R;          // tile bits, register bits
+    uint32_t n_glob;        // n - T
+    uint32_t group_off, n_groups;
+    uint32_t n_slots;       // gradient slots of this stage (backward)
+    uint32_t slot_off;      // first global slot
+    uint32_t pad;
+    uint8_t glob_pos[kMaxQ];  // physical positions of the global bits (ascending)
+    uint8_t tile_pos[kMaxT];  // physical positions of the tile bits (ascending)
+    uint8_t pad2[2];
+    uint64_t ptile[kMaxT];    // 1 << tile_pos[b]
+    uint32_t swbit[kMaxT];    // swizzled element offset of tile bit b
+};
+
+// Shared-memory swizzle (element index inside a tile -> storage index).  XOR-linear,
+// so sw(a ^ b) = sw(a) ^ sw(b).  complex64 (8 B): XOR bits 1..4 with a fold of the
+// bits above 5 (bit 0 untouched so 16-byte chunks stay whole); complex128 (16 B):
+// XOR bits 0..2 with a fold of the bits above 3.  Spreads strided lanes over banks.
+SVK_HD uint32_t swizzle8(uint32_t t) {
+    uint32_t y = t >> 5;
+    uint32_t f = (y ^ (y >> 5)) & 15u;
+    return t ^ (f << 1);
+}
+SVK_HD uint32_t swizzle16(uint32_t t) {
+    uint32_t y = t >> 3;
+    uint32_t f = (y ^ (y >> 3) ^ (y >> 6) ^ (y >> 9)) & 7u;
+    return t ^ f;
+}
+SVK_HD uint32_t swizzle(uint32_t t, int elem_bytes) {
+    return elem_bytes == 8 ? swizzle8(t) : swizzle16(t);
+}
+
+}  // namespace svk

@@ -1,0 +1,184 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, element by
+element, at sizes spanning several tiles and ragged stage shapes.
+
+Tolerances (from the target): ||psi - psi_ref||_2 <= 2e-5 (complex64),
+<= 1e-12 (complex128); expectation values within 1e-6 relative (max(|E|, 1));
+gradients within 1e-4 relative of the reference gradient (2-norm).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import circuits as C
+from oracle import gradients as GR
+from oracle import observables as O
+from oracle import statevector as S
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 2e-5, 1: 1e-12}
+
+
+@pytest.fixture(scope="module")
+def sv():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2509_14098_gb300 as pkg
+    return pkg
+
+
+def run_gpu(sv, circ, L, psi0=None, dtype=0, params=None, n_fixed=None):
+    plan = sv.Plan(circ, L, n_fixed)
+    st = sv.StateVector(circ.n_qubits, dtype)
+    if psi0 is not None:
+        st.set_host(psi0)
+    st.run(plan, params)
+    return st.get_host().astype(np.complex128), st, plan
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("seed", range(10))
+def test_random_circuits(sv, seed, dtype):
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(3, 15))
+    L = int(rng.integers(max(1, min(n, 5)), min(n, 13) + 1))
+    c = C.random_circuit(n, int(rng.integers(20, 200)), seed)
+    psi0 = C.random_state(n, seed)
+    nf = None if seed % 3 else int(rng.integers(0, 4))
+    got, _, _ = run_gpu(sv, c, L, psi0, dtype, n_fixed=nf)
+    ref = S.simulate(c, None, psi0)
+    assert np.linalg.norm(got - ref) <= TOL[dtype], (n, L)
+
+
+def test_brick16_config(sv):
+    c, _, L = C.workload("brick16")
+    got, st, plan = run_gpu(sv, c, L)
+    ref = S.simulate(c)
+    assert np.linalg.norm(got - ref) <= 2e-5
+    assert abs(st.norm() - 1) < 1e-6
+
+
+@pytest.mark.parametrize("n,L", [(6, 4), (10, 6), (14, 11), (17, 11), (18, 13)])
+def test_qft_matches_oracle_and_fft(sv, n, L):
+    psi0 = C.random_state(n, 2)
+    got, st, _ = run_gpu(sv, C.qft(n), L, psi0)
+    ref = S.simulate(C.qft(n), None, psi0)
+    assert np.linalg.norm(got - ref) <= 2e-5
+    assert np.linalg.norm(got - np.fft.ifft(psi0, norm="ortho")) <= 2e-5
+    assert st.run_info()["permutation_sweeps"] == 1      # bit reversal left by the SWAPs
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_qft_roundtrip_identity(sv, dtype):
+    n = 20
+    psi0 = C.random_state(n, 2)
+    got, st, _ = run_gpu(sv, C.qft_roundtrip(n), 11, psi0, dtype)
+    assert np.linalg.norm(got - psi0) <= TOL[dtype]
+    info = st.run_info()
+    assert info["permutation_sweeps"] == 0               # the two relabels cancel
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("seed", range(4))
+def test_permutation_sweep(sv, seed, dtype):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(4, 19))
+    perm = [int(x) for x in rng.permutation(n)]
+    psi0 = C.random_state(n, seed)
+    st = sv.StateVector(n, dtype)
+    st.set_host(psi0)
+    st.permute(perm)
+    got = st.get_host()
+    assert np.array_equal(got, S.permute_qubits(psi0, n, perm).astype(got.dtype))   # a pure data move: bit-exact
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_norm_and_expval(sv, dtype):
+    n = 13
+    psi = C.random_state(n, 7)
+    st = sv.StateVector(n, dtype)
+    st.set_host(psi)
+    rng = np.random.default_rng(3)
+    terms = [(float(rng.normal()), "".join(rng.choice(list("IXYZ"), size=n))) for _ in range(25)]
+    terms += C.tfim(n).terms
+    obs = C.Observable(n, terms)
+    e_ref = O.expval(psi, obs)
+    tol = 1e-6 * max(1.0, abs(e_ref)) if dtype == 0 else 1e-11
+    assert abs(st.expval(obs) - e_ref) <= tol
+    assert abs(st.norm() - 1.0) <= (1e-6 if dtype == 0 else 1e-12)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_tiny_states(sv, n):
+    c = C.random_circuit(n, 30, n)
+    psi0 = C.random_state(n, n)
+    got, st, _ = run_gpu(sv, c, n, psi0)
+    assert np.linalg.norm(got - S.simulate(c, None, psi0)) <= 2e-5
+    obs = C.tfim(n)
+    assert abs(st.expval(obs) - O.expval(got, obs)) <= 1e-6 * max(1, abs(O.expval(got, obs)))
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_grad_hea12(sv, dtype):
+    c = C.hea(12, 10)                     # the differentiation workload at oracle size
+    p = C.hea_params(c.n_params, 4)
+    obs = C.tfim(12)
+    st = sv.StateVector(12, dtype)
+    e, g = st.grad(sv.Plan(c, 9), p, obs)
+    psi = S.simulate(c, p)
+    e_ref = O.expval(psi, obs)
+    g_ps = GR.parameter_shift(c, p, obs)
+    assert abs(e - e_ref) <= 1e-6 * max(1.0, abs(e_ref))
+    assert np.linalg.norm(g - g_ps) <= 1e-4 * np.linalg.norm(g_ps)
+    # the backward sweep un-applies the circuit: the state returns to |0...0>
+    back = st.get_host().astype(np.complex128)
+    assert np.linalg.norm(back - C.zero_state(12)) <= (1e-4 if dtype == 0 else 1e-10)
+
+
+def test_grad_matches_finite_differences(sv):
+    c = C.hea(6, 3)
+    p = C.hea_params(c.n_params, 9)
+    obs = C.tfim(6)
+    st = sv.StateVector(6)
+    _, g = st.grad(sv.Plan(c, 4), p, obs)
+    g_fd = GR.finite_difference(c, p, obs)
+    assert np.linalg.norm(g - g_fd) <= 1e-4 * np.linalg.norm(g_fd)
+
+
+def test_grad_rx_and_mixed(sv):
+    n = 5
+    gates = []
+    slot = 0
+    for layer in range(3):
+        for q in range(n):
+            gates.append(C.Gate(("RX", "RY", "RZ")[(q + layer) % 3], (q,), slot))
+            slot += 1
+        for q in range(n - 1):
+            gates.append(C.Gate("CZ" if layer % 2 else "CX", (q, q + 1)))
+        gates.append(C.Gate("H", (layer % n,)))
+        gates.append(C.Gate("SWAP", (0, n - 1)))
+    c = C.Circuit(n, gates, slot)
+    p = C.hea_params(slot, 1)
+    obs = C.Observable(n, C.tfim(n).terms + [(0.3, "XYZIY")])
+    st = sv.StateVector(n)
+    e, g = st.grad(sv.Plan(c, 3), p, obs)
+    assert abs(e - O.expval(S.simulate(c, p), obs)) <= 1e-6 * max(1, abs(e))
+    g_ps = GR.parameter_shift(c, p, obs)
+    assert np.linalg.norm(g - g_ps) <= 1e-4 * np.linalg.norm(g_ps)
+
+
+def test_errors_are_reported(sv):
+    from paper_2509_14098_gb300 import _native as N
+    st = sv.StateVector(5)
+    plan = sv.Plan(C.qft(6), 4)
+    with pytest.raises(sv.SvError) as e:
+        st.run(plan)
+    assert e.value.status == N.SV_ERR_ARG
+    c = C.Circuit(3, [C.Gate("P", (0,), 0)], n_params=1)
+    with pytest.raises(sv.SvError) as e:
+        sv.StateVector(3).grad(sv.Plan(c, 2), np.array([0.1]), C.tfim(3))
+    assert e.value.status == N.SV_ERR_UNSUPPORTED

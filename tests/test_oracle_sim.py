@@ -127,3 +127,11 @@ def test_hea_counts():
     c = C.brickwork(32, 24, 3)
     kinds = [g.kind for g in c.gates]
     assert (kinds.count("U3"), kinds.count("CZ")) == (768, 372)
+
+
+def test_dft_amplitude_definition():
+    n = 9
+    psi = C.random_state(n, 5)
+    ref = np.fft.ifft(psi, norm="ortho")
+    for k in (0, 1, 77, 511):
+        assert abs(S.dft_amplitude(psi, k, chunk=100) - ref[k]) < 1e-13
