@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -46,14 +47,23 @@ struct DevBuf {
     }
 };
 
-// Device copy of a lowered program: [stages][groups][ops][terms].
+// Device copy of a lowered, packed program (see svh::Packed for the layout).
 struct DevProgram {
     DevBuf buf;
-    svk::Stage* stages = nullptr;
-    svk::Group* groups = nullptr;
-    svk::Op* ops = nullptr;
-    svk::Term* terms = nullptr;
-    std::vector<uint8_t> host;
+    svh::Packed packed;
+    svk::StageLaunch launch(size_t s, void* psi, void* lam, double* partial) const {
+        const uint8_t* b = (const uint8_t*)buf.p;
+        svk::StageLaunch L;
+        L.psi = psi;
+        L.lam = lam;
+        L.stage = (const svk::Stage*)(b + packed.stage_off) + s;
+        L.groups = (const svk::Group*)(b + packed.group_off);
+        L.ops = b + packed.op_off;
+        L.terms = b + packed.term_off;
+        L.slots = b + packed.slot_off;
+        L.partial = partial;
+        return L;
+    }
 };
 
 size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -112,27 +122,17 @@ static void tock(sv_handle h, cudaEvent_t a, int kind) {
     h->recs.push_back({a, b, kind});
 }
 
-static sv_status upload_program(sv_handle h, const svh::Program& p, DevProgram* d) {
-    const size_t s0 = 0;
-    const size_t s1 = align16(s0 + p.stages.size() * sizeof(svk::Stage));
-    const size_t s2 = align16(s1 + p.groups.size() * sizeof(svk::Group));
-    const size_t s3 = align16(s2 + p.ops.size() * sizeof(svk::Op));
-    const size_t s4 = align16(s3 + std::max<size_t>(1, p.terms.size()) * sizeof(svk::Term));
-    SV_CUDA(d->buf.ensure(s4));
-    d->host.assign(s4, 0);
-    std::memcpy(d->host.data() + s0, p.stages.data(), p.stages.size() * sizeof(svk::Stage));
-    std::memcpy(d->host.data() + s1, p.groups.data(), p.groups.size() * sizeof(svk::Group));
-    std::memcpy(d->host.data() + s2, p.ops.data(), p.ops.size() * sizeof(svk::Op));
-    if (!p.terms.empty())
-        std::memcpy(d->host.data() + s3, p.terms.data(), p.terms.size() * sizeof(svk::Term));
-    // pageable source: the call returns once the data is staged, so the host vector
-    // may be reused immediately; the device copy is stream-ordered.
-    SV_CUDA(cudaMemcpyAsync(d->buf.p, d->host.data(), s4, cudaMemcpyHostToDevice, h->stream));
-    uint8_t* b = (uint8_t*)d->buf.p;
-    d->stages = (svk::Stage*)(b + s0);
-    d->groups = (svk::Group*)(b + s1);
-    d->ops = (svk::Op*)(b + s2);
-    d->terms = (svk::Term*)(b + s3);
+static sv_status upload_program(sv_handle h, const svh::Program& p, DevProgram* d, bool backward) {
+    std::string err = svh::pack(p, (int)h->n, h->eb, &d->packed);
+    if (!err.empty()) return fail(SV_ERR_ARG, err);
+    for (auto& st : d->packed.stages)
+        if (svk::stage_smem_bytes(h->eb, st, backward) > 227 * 1024)
+            return fail(SV_ERR_UNSUPPORTED, "a stage needs more shared memory than a CTA has (lower L or split the circuit)");
+    SV_CUDA(d->buf.ensure(d->packed.blob.size()));
+    // pageable source: the call returns once the data is staged, so the host blob may
+    // be reused immediately; the device copy is stream-ordered.
+    SV_CUDA(cudaMemcpyAsync(d->buf.p, d->packed.blob.data(), d->packed.blob.size(),
+                            cudaMemcpyHostToDevice, h->stream));
     return SV_OK;
 }
 
@@ -582,8 +582,16 @@ sv_status sv_plan_destroy(sv_plan* plan) {
 }
 
 // ---------------- execution ----------------
-static int rmax_fwd(int eb) { return eb == 8 ? 5 : 4; }
-static int rmax_bwd(int eb) { return eb == 8 ? 4 : 3; }
+// Register-group width (amplitudes per thread = 2^R); SVGB_RMAX_FWD / SVGB_RMAX_BWD
+// override the defaults for tuning.
+static int env_int(const char* name, int dflt, int lo, int hi) {
+    const char* v = getenv(name);
+    if (!v) return dflt;
+    int x = atoi(v);
+    return x < lo ? lo : (x > hi ? hi : x);
+}
+static int rmax_fwd(int eb) { return eb == 8 ? env_int("SVGB_RMAX_FWD", 4, 1, 5) : env_int("SVGB_RMAX_FWD", 4, 1, 4); }
+static int rmax_bwd(int eb) { return eb == 8 ? env_int("SVGB_RMAX_BWD", 4, 1, 4) : env_int("SVGB_RMAX_BWD", 3, 1, 3); }
 
 static sv_status run_forward(sv_handle h, const sv_plan* plan, const double* params, bool permute_back) {
     const svh::Plan& P = plan->plan;
@@ -592,14 +600,12 @@ static sv_status run_forward(sv_handle h, const sv_plan* plan, const double* par
     if (!err.empty()) return fail(SV_ERR_ARG, err);
     for (auto& st : prog.stages)
         if (((size_t)h->eb << st.T) > 227 * 1024) return fail(SV_ERR_UNSUPPORTED, "tile too wide for shared memory at this dtype (use L <= 13 for complex128)");
-    sv_status s = upload_program(h, prog, &h->fwd);
+    sv_status s = upload_program(h, prog, &h->fwd, false);
     if (s) return s;
-    for (size_t i = 0; i < prog.stages.size(); ++i) {
-        const svk::Stage& st = prog.stages[i];
-        const uint64_t ntiles = 1ull << (h->n - st.T);
+    const auto& stages = h->fwd.packed.stages;
+    for (size_t i = 0; i < stages.size(); ++i) {
         cudaEvent_t t0 = tick(h);
-        SV_CUDA(svk::launch_stage_fwd(h->eb, (int)st.R, h->psi, h->fwd.stages + i, h->fwd.groups,
-                                      h->fwd.ops, h->fwd.terms, (int)st.T, ntiles, h->stream));
+        SV_CUDA(svk::launch_stage_fwd(h->eb, h->fwd.launch(i, h->psi, nullptr, nullptr), stages[i], h->stream));
         tock(h, t0, TK_STAGE);
         h->info.stage_sweeps += 1;
         h->info.kernel_launches += 1;
@@ -669,7 +675,8 @@ sv_status sv_grad(sv_handle h, const sv_plan* plan, const double* params, const 
     std::string err = svh::lower(P, params, h->eb, rmax_bwd(h->eb), true, &bprog);
     if (!err.empty()) return fail(err.find("not supported") != std::string::npos ? SV_ERR_UNSUPPORTED : SV_ERR_ARG, err);
     for (auto& st : bprog.stages)
-        if (((size_t)h->eb << (st.T + 1)) > 200 * 1024) return fail(SV_ERR_UNSUPPORTED, "tile too wide for the adjoint sweep (psi and lambda tiles must fit shared memory)");
+        if (((size_t)h->eb << (st.T + 1)) > 200 * 1024 || (st.T - st.R) > 9)
+            return fail(SV_ERR_UNSUPPORTED, "tile too wide for the adjoint sweep (psi and lambda tiles must fit shared memory)");
     sv_status s = run_forward(h, plan, params, false);
     if (s) return s;
     // lambda = O psi in the forward program's final physical layout
@@ -681,21 +688,21 @@ sv_status sv_grad(sv_handle h, const sv_plan* plan, const double* params, const 
     if (s) return s;
     double E = 0.0;
     SV_CUDA(cudaMemcpyAsync(&E, h->red.p, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    s = upload_program(h, bprog, &h->bwd);
+    s = upload_program(h, bprog, &h->bwd, true);
     if (s) return s;
     const size_t nslots_total = bprog.slot_param.size();
+    const auto& bst = h->bwd.packed.stages;
     size_t maxpart = 1;
-    for (auto& st : bprog.stages)
+    for (auto& st : bst)
         maxpart = std::max(maxpart, (size_t)st.n_slots << (h->n - st.T));
     SV_CUDA(h->partial.ensure(maxpart * sizeof(double)));
     SV_CUDA(h->slot_sum.ensure(std::max<size_t>(1, nslots_total) * sizeof(double)));
-    for (size_t i = 0; i < bprog.stages.size(); ++i) {
-        const svk::Stage& st = bprog.stages[i];
+    for (size_t i = 0; i < bst.size(); ++i) {
+        const svk::Stage& st = bst[i];
         const uint64_t ntiles = 1ull << (h->n - st.T);
         cudaEvent_t t0 = tick(h);
-        SV_CUDA(svk::launch_stage_bwd(h->eb, (int)st.R, h->psi, h->scratch.p, h->bwd.stages + i,
-                                      h->bwd.groups, h->bwd.ops, h->bwd.terms, (double*)h->partial.p,
-                                      (int)st.T, st.n_slots, ntiles, h->stream));
+        SV_CUDA(svk::launch_stage_bwd(h->eb, h->bwd.launch(i, h->psi, h->scratch.p, (double*)h->partial.p),
+                                      st, h->stream));
         tock(h, t0, TK_BWD);
         h->info.backward_sweeps += 1;
         h->info.kernel_launches += 1;

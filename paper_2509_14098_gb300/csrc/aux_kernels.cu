@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(512) k_pauli(const typename CT<Real>::C* __res
     for (int j = 0; j < R; ++j) sr[j] = sw.swbit[j];
     const bool pairs = sizeof(C) == 8;   // tile bit 0 is register bit 0
     C a[K], o[K];
-    load_regs<C, R>(a, tile, soff, sr, pairs);
+    load_regs<C, C, R>(a, tile, soff, sr, pairs);
 #pragma unroll
     for (int k = 0; k < K; ++k) o[k].x = o[k].y = 0;
     Real wd[K];
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(512) k_pauli(const typename CT<Real>::C* __res
     const uint32_t wmask = blockDim.x >= 32 ? 0xffffffffu : ((1u << blockDim.x) - 1u);
     for (int off = 16; off > 0; off >>= 1)
         if ((uint32_t)off < blockDim.x) ev += __shfl_xor_sync(wmask, ev, off);
-    if (lam != nullptr) store_regs<C, R>(o, tout, soff, sr, pairs);
+    if (lam != nullptr) store_regs<C, C, R>(o, tout, soff, sr, pairs);
     if ((tid & 31) == 0) wsum[tid >> 5] = ev;
     __syncthreads();
     if (tid == 0) {

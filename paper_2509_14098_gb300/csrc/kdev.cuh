@@ -49,12 +49,12 @@ __device__ __forceinline__ double2 expi(double a) {
 }
 
 template <typename Real>
-__device__ __forceinline__ Real term_angle(const Term* __restrict__ terms, uint32_t off, uint32_t n,
-                                           uint64_t fix) {
+__device__ __forceinline__ Real term_angle(const DevTerm<Real>* __restrict__ terms, uint32_t off,
+                                           uint32_t n, uint64_t fix) {
     Real ang = 0;
     for (uint32_t i = 0; i < n; ++i) {
         const uint64_t m = terms[off + i].mask;
-        if ((fix & m) == m) ang += (Real)terms[off + i].angle;
+        if ((fix & m) == m) ang += terms[off + i].angle;
     }
     return ang;
 }
@@ -70,12 +70,12 @@ __device__ __forceinline__ uint64_t tile_base(uint64_t tile, const uint8_t* __re
 // ---------------------------------------------------------------------------
 // register-resident op application
 // ---------------------------------------------------------------------------
-template <int R, int J, typename C, typename Real>
+template <int R, int J, bool CTRL, typename C, typename Real>
 __device__ __forceinline__ void dense_u(C (&a)[1 << R], const Real (&m)[8], uint32_t creg) {
 #pragma unroll
     for (int k = 0; k < (1 << R); ++k) {
         if (k & (1 << J)) continue;
-        if ((k & creg) != creg) continue;
+        if (CTRL && (k & creg) != creg) continue;
         const C x0 = a[k], x1 = a[k | (1 << J)];
         C y0, y1;
         y0.x = m[0] * x0.x - m[1] * x0.y + m[2] * x1.x - m[3] * x1.y;
@@ -86,12 +86,12 @@ __device__ __forceinline__ void dense_u(C (&a)[1 << R], const Real (&m)[8], uint
         a[k | (1 << J)] = y1;
     }
 }
-template <int R, int J, typename C, typename Real>
+template <int R, int J, bool CTRL, typename C, typename Real>
 __device__ __forceinline__ void dense_ur(C (&a)[1 << R], const Real (&m)[8], uint32_t creg) {
 #pragma unroll
     for (int k = 0; k < (1 << R); ++k) {
         if (k & (1 << J)) continue;
-        if ((k & creg) != creg) continue;
+        if (CTRL && (k & creg) != creg) continue;
         const C x0 = a[k], x1 = a[k | (1 << J)];
         C y0, y1;
         y0.x = m[0] * x0.x + m[2] * x1.x;
@@ -102,12 +102,26 @@ __device__ __forceinline__ void dense_ur(C (&a)[1 << R], const Real (&m)[8], uin
         a[k | (1 << J)] = y1;
     }
 }
-template <int R, int J, typename C>
+// complex64 specialisation: one packed FP32x2 multiply + FMA per output amplitude
+template <int R, int J, bool CTRL>
+__device__ __forceinline__ void dense_ur_f2(float2 (&a)[1 << R], const float (&m)[8], uint32_t creg) {
+    const float2 m0 = make_float2(m[0], m[0]), m2 = make_float2(m[2], m[2]);
+    const float2 m4 = make_float2(m[4], m[4]), m6 = make_float2(m[6], m[6]);
+#pragma unroll
+    for (int k = 0; k < (1 << R); ++k) {
+        if (k & (1 << J)) continue;
+        if (CTRL && (k & creg) != creg) continue;
+        const float2 x0 = a[k], x1 = a[k | (1 << J)];
+        a[k] = __ffma2_rn(m2, x1, __fmul2_rn(m0, x0));
+        a[k | (1 << J)] = __ffma2_rn(m6, x1, __fmul2_rn(m4, x0));
+    }
+}
+template <int R, int J, bool CTRL, typename C>
 __device__ __forceinline__ void dense_x(C (&a)[1 << R], uint32_t creg) {
 #pragma unroll
     for (int k = 0; k < (1 << R); ++k) {
         if (k & (1 << J)) continue;
-        if ((k & creg) != creg) continue;
+        if (CTRL && (k & creg) != creg) continue;
         const C t = a[k];
         a[k] = a[k | (1 << J)];
         a[k | (1 << J)] = t;
@@ -118,6 +132,12 @@ __device__ __forceinline__ void phase_bit(C (&a)[1 << R], C w) {
 #pragma unroll
     for (int k = 0; k < (1 << R); ++k)
         if (k & (1 << J)) a[k] = cmul(a[k], w);
+}
+template <int R, int J, int U, typename C>
+__device__ __forceinline__ void phase_pair(C (&a)[1 << R], C w) {
+#pragma unroll
+    for (int k = 0; k < (1 << R); ++k)
+        if ((k & (1 << J)) && (k & (1 << U))) a[k] = cmul(a[k], w);
 }
 
 #define SVK_SWITCH_J(j, R, CALL)                          \
@@ -130,48 +150,302 @@ __device__ __forceinline__ void phase_bit(C (&a)[1 << R], C w) {
         default: break;                                   \
     }
 
-// Apply one (non-gradient) op to a register array.
+// (j, u) with j < u, dispatched to compile-time bit positions
+#define SVK_PAIR(JJ, UU) case (JJ * 8 + UU): if constexpr (R > UU) { phase_pair<R, JJ, UU, C>(a, w); } break;
+
 template <typename Real, int R>
-__device__ __forceinline__ void apply_op(typename CT<Real>::C (&a)[1 << R], const Op& o, uint64_t fix,
-                                         const Term* __restrict__ terms) {
+__device__ __forceinline__ void phase_pair_dispatch(typename CT<Real>::C (&a)[1 << R], int j, int u,
+                                                    typename CT<Real>::C w) {
     using C = typename CT<Real>::C;
-    const uint8_t type = o.type;
-    if (type <= OP_X) {
-        if ((fix & o.ctrl_fix) != o.ctrl_fix) return;   // control on a thread / global bit
-        const uint32_t creg = o.ctrl_reg;
-        if (type == OP_X) {
-            SVK_SWITCH_J(o.j, R, (dense_x<R, J_, C>(a, creg)));
+    switch (j * 8 + u) {
+        SVK_PAIR(0, 1) SVK_PAIR(0, 2) SVK_PAIR(0, 3) SVK_PAIR(0, 4)
+        SVK_PAIR(1, 2) SVK_PAIR(1, 3) SVK_PAIR(1, 4)
+        SVK_PAIR(2, 3) SVK_PAIR(2, 4)
+        SVK_PAIR(3, 4)
+        default: break;
+    }
+}
+#undef SVK_PAIR
+
+// Everything an op needs besides the register array.
+template <typename Real>
+struct OpCtx {
+    uint64_t fix;                                   // thread's fixed physical index
+    const PhaseSlot<Real>* slots;                   // shared memory (thread-bit coefficients)
+    const Real* ang;                                // shared memory: per-tile slot angles
+    uint32_t tid;
+    int TR;
+    const DevTerm<Real>* __restrict__ terms;
+};
+
+template <typename Real>
+__device__ __forceinline__ typename CT<Real>::C phase_factor(const DevOp<Real>& o, const OpCtx<Real>& x) {
+    using C = typename CT<Real>::C;
+    if (o.flags & F_SLOT) {
+        const PhaseSlot<Real>& ps = x.slots[o.slot];
+        Real ang = x.ang[o.slot];
+        if (ps.has_thr)
+            for (int i = 0; i < x.TR; ++i)
+                if ((x.tid >> i) & 1) ang += ps.J[i];
+        return expi(ang);
+    }
+    if (o.flags & F_TW) return expi(term_angle<Real>(x.terms, o.term_off, o.n_terms, x.fix));
+    C w;
+    w.x = o.m[0];
+    w.y = o.m[1];
+    if (o.flags & F_TERMS) w = cmul(w, expi(term_angle<Real>(x.terms, o.term_off, o.n_terms, x.fix)));
+    return w;
+}
+
+// ---------------------------------------------------------------------------
+// complex64 register arrays hold each amplitude as one packed 64-bit register
+// (re in the low half).  The op bodies below are inline PTX whose outputs are tied
+// to their inputs ("+l"): a body leaves every amplitude in the register it came
+// from, so the runtime switch over op kinds and target bits needs no register
+// shuffling at its merge points (measured: ~100 fewer ALU instructions per op).
+// ---------------------------------------------------------------------------
+typedef unsigned long long u64;
+template <typename Real> struct RegT;
+template <> struct RegT<float> { using type = u64; };
+template <> struct RegT<double> { using type = double2; };
+
+__device__ __forceinline__ u64 pack2(float x, float y) {
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+    return r;
+}
+__device__ __forceinline__ float2 unpack2(u64 v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+// real 2x2 on a pair: packed FP32x2 multiply / FMA, in place
+__device__ __forceinline__ void p_ur(u64& x0, u64& x1, u64 m0, u64 m2, u64 m4, u64 m6) {
+    asm volatile("{\n\t.reg .b64 t0, t1;\n\t"
+                 "mul.rn.f32x2 t0, %2, %0;\n\t"
+                 "fma.rn.f32x2 t0, %3, %1, t0;\n\t"
+                 "mul.rn.f32x2 t1, %4, %0;\n\t"
+                 "fma.rn.f32x2 %1, %5, %1, t1;\n\t"
+                 "mov.b64 %0, t0;\n\t}"
+                 : "+l"(x0), "+l"(x1)
+                 : "l"(m0), "l"(m2), "l"(m4), "l"(m6));
+}
+// complex 2x2 on a pair, in place.  m: row-major (re, im); n = -m[1], -m[3], -m[5], -m[7]
+__device__ __forceinline__ void p_u(u64& x0, u64& x1, const float (&m)[8], const float (&n)[4]) {
+    asm volatile("{\n\t.reg .f32 a, b, c, d, p, q, r, s;\n\t"
+                 "mov.b64 {a, b}, %0;\n\t"
+                 "mov.b64 {c, d}, %1;\n\t"
+                 "mul.rn.f32 p, %2, a;\n\tfma.rn.f32 p, %10, b, p;\n\tfma.rn.f32 p, %4, c, p;\n\tfma.rn.f32 p, %11, d, p;\n\t"
+                 "mul.rn.f32 q, %2, b;\n\tfma.rn.f32 q, %3, a, q;\n\tfma.rn.f32 q, %4, d, q;\n\tfma.rn.f32 q, %5, c, q;\n\t"
+                 "mul.rn.f32 r, %6, a;\n\tfma.rn.f32 r, %12, b, r;\n\tfma.rn.f32 r, %8, c, r;\n\tfma.rn.f32 r, %13, d, r;\n\t"
+                 "mul.rn.f32 s, %6, b;\n\tfma.rn.f32 s, %7, a, s;\n\tfma.rn.f32 s, %8, d, s;\n\tfma.rn.f32 s, %9, c, s;\n\t"
+                 "mov.b64 %0, {p, q};\n\t"
+                 "mov.b64 %1, {r, s};\n\t}"
+                 : "+l"(x0), "+l"(x1)
+                 : "f"(m[0]), "f"(m[1]), "f"(m[2]), "f"(m[3]), "f"(m[4]), "f"(m[5]), "f"(m[6]), "f"(m[7]),
+                   "f"(n[0]), "f"(n[1]), "f"(n[2]), "f"(n[3]));
+}
+__device__ __forceinline__ void p_swap(u64& x0, u64& x1) {
+    asm volatile("{\n\t.reg .b64 t;\n\tmov.b64 t, %0;\n\tmov.b64 %0, %1;\n\tmov.b64 %1, t;\n\t}"
+                 : "+l"(x0), "+l"(x1));
+}
+// x *= (wr + i wi), in place; nwi = -wi
+__device__ __forceinline__ void p_cmul(u64& x, float wr, float wi, float nwi) {
+    asm volatile("{\n\t.reg .f32 a, b, p, q;\n\t"
+                 "mov.b64 {a, b}, %0;\n\t"
+                 "mul.rn.f32 p, %1, a;\n\tfma.rn.f32 p, %3, b, p;\n\t"
+                 "mul.rn.f32 q, %2, a;\n\tfma.rn.f32 q, %1, b, q;\n\t"
+                 "mov.b64 %0, {p, q};\n\t}"
+                 : "+l"(x)
+                 : "f"(wr), "f"(wi), "f"(nwi));
+}
+
+template <int R, int J, bool CTRL>
+__device__ __forceinline__ void pd_ur(u64 (&a)[1 << R], const float (&m)[8], uint32_t creg) {
+    const u64 m0 = pack2(m[0], m[0]), m2 = pack2(m[2], m[2]), m4 = pack2(m[4], m[4]), m6 = pack2(m[6], m[6]);
+#pragma unroll
+    for (int k = 0; k < (1 << R); ++k) {
+        if (k & (1 << J)) continue;
+        if (CTRL && (k & creg) != creg) continue;
+        p_ur(a[k], a[k | (1 << J)], m0, m2, m4, m6);
+    }
+}
+template <int R, int J, bool CTRL>
+__device__ __forceinline__ void pd_u(u64 (&a)[1 << R], const float (&m)[8], uint32_t creg) {
+    const float n[4] = {-m[1], -m[3], -m[5], -m[7]};
+#pragma unroll
+    for (int k = 0; k < (1 << R); ++k) {
+        if (k & (1 << J)) continue;
+        if (CTRL && (k & creg) != creg) continue;
+        p_u(a[k], a[k | (1 << J)], m, n);
+    }
+}
+template <int R, int J, bool CTRL>
+__device__ __forceinline__ void pd_x(u64 (&a)[1 << R], uint32_t creg) {
+#pragma unroll
+    for (int k = 0; k < (1 << R); ++k) {
+        if (k & (1 << J)) continue;
+        if (CTRL && (k & creg) != creg) continue;
+        p_swap(a[k], a[k | (1 << J)]);
+    }
+}
+template <int R, int J>
+__device__ __forceinline__ void pd_phase_bit(u64 (&a)[1 << R], float2 w) {
+    const float nwi = -w.y;
+#pragma unroll
+    for (int k = 0; k < (1 << R); ++k)
+        if (k & (1 << J)) p_cmul(a[k], w.x, w.y, nwi);
+}
+template <int R, int J, int U>
+__device__ __forceinline__ void pd_phase_pair(u64 (&a)[1 << R], float2 w) {
+    const float nwi = -w.y;
+#pragma unroll
+    for (int k = 0; k < (1 << R); ++k)
+        if ((k & (1 << J)) && (k & (1 << U))) p_cmul(a[k], w.x, w.y, nwi);
+}
+template <int R>
+__device__ __forceinline__ void pd_phase_all(u64 (&a)[1 << R], float2 w) {
+    const float nwi = -w.y;
+#pragma unroll
+    for (int k = 0; k < (1 << R); ++k) p_cmul(a[k], w.x, w.y, nwi);
+}
+
+// Apply one (non-gradient) op to a register array.  The op is first copied from
+// shared memory into registers (16-byte loads), then one flat switch on its code
+// selects a body specialised for the op kind, control form and register bit(s).
+template <typename Real>
+__device__ __forceinline__ DevOp<Real> load_op(const DevOp<Real>* p) {
+    DevOp<Real> o;
+    const uint4* src = reinterpret_cast<const uint4*>(p);
+    uint4* dst = reinterpret_cast<uint4*>(&o);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(DevOp<Real>) / 16); ++i) dst[i] = src[i];
+    return o;
+}
+
+template <typename Real, int R, int TYPE, bool CTRL, int J>
+__device__ __forceinline__ void dense_case(typename RegT<Real>::type (&a)[1 << R], const DevOp<Real>& o,
+                                           const OpCtx<Real>& x) {
+    using C = typename CT<Real>::C;
+    if constexpr (J < R) {
+        if ((x.fix & o.ctrl_fix) != o.ctrl_fix) return;   // control on a thread / global bit
+        if constexpr (sizeof(Real) == 4) {
+            if (o.flags & F_TW) pd_phase_bit<R, J>(a, phase_factor<Real>(o, x));
+            if constexpr (TYPE == OP_X) pd_x<R, J, CTRL>(a, o.ctrl_reg);
+            else if constexpr (TYPE == OP_UR) pd_ur<R, J, CTRL>(a, o.m, o.ctrl_reg);
+            else pd_u<R, J, CTRL>(a, o.m, o.ctrl_reg);
         } else {
-            Real m[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) m[i] = (Real)o.m[i];
-            if (type == OP_UR) {
-                SVK_SWITCH_J(o.j, R, (dense_ur<R, J_, C, Real>(a, m, creg)));
-            } else {
-                SVK_SWITCH_J(o.j, R, (dense_u<R, J_, C, Real>(a, m, creg)));
-            }
+            if (o.flags & F_TW) phase_bit<R, J, C>(a, phase_factor<Real>(o, x));
+            if constexpr (TYPE == OP_X) dense_x<R, J, CTRL, C>(a, o.ctrl_reg);
+            else if constexpr (TYPE == OP_UR) dense_ur<R, J, CTRL, C, Real>(a, o.m, o.ctrl_reg);
+            else dense_u<R, J, CTRL, C, Real>(a, o.m, o.ctrl_reg);
         }
-    } else if (type == OP_PHASE1) {
-        C w;
-        w.x = (Real)o.m[0];
-        w.y = (Real)o.m[1];
-        if (o.n_terms) w = cmul(w, expi(term_angle<Real>(terms, o.term_off, o.n_terms, fix)));
-        SVK_SWITCH_J(o.j, R, (phase_bit<R, J_, C>(a, w)));
-    } else if (type == OP_PHASE2) {
-        C w;
-        w.x = (Real)o.m[0];
-        w.y = (Real)o.m[1];
-        const uint32_t mk = (1u << o.j) | (1u << o.u);
+    }
+}
+
+template <typename Real, int R, int J>
+__device__ __forceinline__ void phase1_case(typename RegT<Real>::type (&a)[1 << R], const DevOp<Real>& o,
+                                            const OpCtx<Real>& x) {
+    if constexpr (J < R) {
+        if constexpr (sizeof(Real) == 4) pd_phase_bit<R, J>(a, phase_factor<Real>(o, x));
+        else phase_bit<R, J, typename CT<Real>::C>(a, phase_factor<Real>(o, x));
+    }
+}
+template <typename Real, int R, int J, int U>
+__device__ __forceinline__ void phase2_case(typename RegT<Real>::type (&a)[1 << R], const DevOp<Real>& o) {
+    if constexpr (U < R) {
+        typename CT<Real>::C w;
+        w.x = o.m[0];
+        w.y = o.m[1];
+        if constexpr (sizeof(Real) == 4) pd_phase_pair<R, J, U>(a, w);
+        else phase_pair<R, J, U, typename CT<Real>::C>(a, w);
+    }
+}
+
+#define SVK_DENSE_CASES(TYPE, CTRL, BASE)                                                   \
+    case BASE + 0: dense_case<Real, R, TYPE, CTRL, 0>(a, o, x); break;                     \
+    case BASE + 1: dense_case<Real, R, TYPE, CTRL, 1>(a, o, x); break;                     \
+    case BASE + 2: dense_case<Real, R, TYPE, CTRL, 2>(a, o, x); break;                     \
+    case BASE + 3: dense_case<Real, R, TYPE, CTRL, 3>(a, o, x); break;                     \
+    case BASE + 4: dense_case<Real, R, TYPE, CTRL, 4>(a, o, x); break;
+#define SVK_PHASE2_CASE(J, U)                                                               \
+    case C_PHASE2 + (J == 0 ? U - 1 : J == 1 ? U + 2 : J == 2 ? U + 4 : 9):                  \
+        phase2_case<Real, R, J, U>(a, o);                                                   \
+        break;
+
+template <typename Real, int R>
+__device__ __forceinline__ void apply_op(typename RegT<Real>::type (&a)[1 << R], const DevOp<Real>& o,
+                                         const OpCtx<Real>& x) {
+    switch (o.code) {
+        SVK_DENSE_CASES(OP_U, false, 0)
+        SVK_DENSE_CASES(OP_U, true, 5)
+        SVK_DENSE_CASES(OP_UR, false, 10)
+        SVK_DENSE_CASES(OP_UR, true, 15)
+        SVK_DENSE_CASES(OP_X, false, 20)
+        SVK_DENSE_CASES(OP_X, true, 25)
+        case C_PHASE1 + 0: phase1_case<Real, R, 0>(a, o, x); break;
+        case C_PHASE1 + 1: phase1_case<Real, R, 1>(a, o, x); break;
+        case C_PHASE1 + 2: phase1_case<Real, R, 2>(a, o, x); break;
+        case C_PHASE1 + 3: phase1_case<Real, R, 3>(a, o, x); break;
+        case C_PHASE1 + 4: phase1_case<Real, R, 4>(a, o, x); break;
+        SVK_PHASE2_CASE(0, 1) SVK_PHASE2_CASE(0, 2) SVK_PHASE2_CASE(0, 3) SVK_PHASE2_CASE(0, 4)
+        SVK_PHASE2_CASE(1, 2) SVK_PHASE2_CASE(1, 3) SVK_PHASE2_CASE(1, 4)
+        SVK_PHASE2_CASE(2, 3) SVK_PHASE2_CASE(2, 4)
+        SVK_PHASE2_CASE(3, 4)
+        case C_PHASE0: {
+            const typename CT<Real>::C w = phase_factor<Real>(o, x);
+            if constexpr (sizeof(Real) == 4) {
+                pd_phase_all<R>(a, w);
+            } else {
 #pragma unroll
-        for (int k = 0; k < (1 << R); ++k)
-            if ((k & mk) == mk) a[k] = cmul(a[k], w);
-    } else if (type == OP_PHASE0) {
-        C w;
-        w.x = (Real)o.m[0];
-        w.y = (Real)o.m[1];
-        if (o.n_terms) w = cmul(w, expi(term_angle<Real>(terms, o.term_off, o.n_terms, fix)));
-#pragma unroll
-        for (int k = 0; k < (1 << R); ++k) a[k] = cmul(a[k], w);
+                for (int k = 0; k < (1 << R); ++k) a[k] = cmul(a[k], w);
+            }
+            break;
+        }
+        default: break;
+    }
+}
+#undef SVK_DENSE_CASES
+#undef SVK_PHASE2_CASE
+
+// Stage the stage's register groups, ops and phase slots into shared memory.
+template <typename Real>
+__device__ __forceinline__ void stage_prologue(Group* sgr, DevOp<Real>* sops, PhaseSlot<Real>* ssl,
+                                               const Stage& st, const Group* __restrict__ ggr,
+                                               const DevOp<Real>* __restrict__ gops,
+                                               const PhaseSlot<Real>* __restrict__ gsl, uint32_t tid,
+                                               uint32_t nthr) {
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(ggr + st.group_off);
+        uint4* dst = reinterpret_cast<uint4*>(sgr);
+        const uint32_t nw = st.n_groups * (uint32_t)(sizeof(Group) / 16);
+        for (uint32_t i = tid; i < nw; i += nthr) dst[i] = src[i];
+    }
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(gops + st.op_off);
+        uint4* dst = reinterpret_cast<uint4*>(sops);
+        const uint32_t nw = st.n_ops * (uint32_t)(sizeof(DevOp<Real>) / 16);
+        for (uint32_t i = tid; i < nw; i += nthr) dst[i] = src[i];
+    }
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(gsl + st.phase_off);
+        uint4* dst = reinterpret_cast<uint4*>(ssl);
+        const uint32_t nw = st.n_phase * (uint32_t)(sizeof(PhaseSlot<Real>) / 16);
+        for (uint32_t i = tid; i < nw; i += nthr) dst[i] = src[i];
+    }
+}
+
+// Per-tile slot angles: the constant plus the terms on global bits set in this tile.
+template <typename Real>
+__device__ __forceinline__ void tile_angles(Real* sang, const PhaseSlot<Real>* __restrict__ gsl,
+                                            const DevTerm<Real>* __restrict__ terms, const Stage& st,
+                                            uint64_t base, uint32_t tid, uint32_t nthr) {
+    for (uint32_t p = tid; p < st.n_phase; p += nthr) {
+        const PhaseSlot<Real>& ps = gsl[st.phase_off + p];
+        Real ang = ps.cangle;
+        for (uint32_t i = 0; i < ps.n_glob; ++i)
+            if (base & terms[ps.glob_off + i].mask) ang += terms[ps.glob_off + i].angle;
+        sang[p] = ang;
     }
 }
 
@@ -186,33 +460,36 @@ __device__ __forceinline__ uint32_t reg_addr(int k, uint32_t soff, const uint32_
     return a;
 }
 
-template <typename C, int R>
-__device__ __forceinline__ void load_regs(C (&a)[1 << R], const C* tile, uint32_t soff,
+template <typename A, typename C, int R>
+__device__ __forceinline__ void load_regs(A (&a)[1 << R], const C* tile, uint32_t soff,
                                           const uint32_t (&sr)[R], bool pairs) {
+    static_assert(sizeof(A) == sizeof(C), "register / tile element size");
     if (sizeof(C) == 8 && pairs) {
 #pragma unroll
         for (int k = 0; k < (1 << R); k += 2) {
-            const float4 v = *reinterpret_cast<const float4*>(tile + reg_addr<C, R>(k, soff, sr));
-            a[k].x = v.x; a[k].y = v.y; a[k + 1].x = v.z; a[k + 1].y = v.w;
+            const uint4 v = *reinterpret_cast<const uint4*>(tile + reg_addr<C, R>(k, soff, sr));
+            memcpy(&a[k], &v.x, 8);
+            memcpy(&a[k + 1], &v.z, 8);
         }
     } else {
 #pragma unroll
-        for (int k = 0; k < (1 << R); ++k) a[k] = tile[reg_addr<C, R>(k, soff, sr)];
+        for (int k = 0; k < (1 << R); ++k) memcpy(&a[k], tile + reg_addr<C, R>(k, soff, sr), sizeof(C));
     }
 }
-template <typename C, int R>
-__device__ __forceinline__ void store_regs(const C (&a)[1 << R], C* tile, uint32_t soff,
+template <typename A, typename C, int R>
+__device__ __forceinline__ void store_regs(const A (&a)[1 << R], C* tile, uint32_t soff,
                                            const uint32_t (&sr)[R], bool pairs) {
     if (sizeof(C) == 8 && pairs) {
 #pragma unroll
         for (int k = 0; k < (1 << R); k += 2) {
-            float4 v;
-            v.x = a[k].x; v.y = a[k].y; v.z = a[k + 1].x; v.w = a[k + 1].y;
-            *reinterpret_cast<float4*>(tile + reg_addr<C, R>(k, soff, sr)) = v;
+            uint4 v;
+            memcpy(&v.x, &a[k], 8);
+            memcpy(&v.z, &a[k + 1], 8);
+            *reinterpret_cast<uint4*>(tile + reg_addr<C, R>(k, soff, sr)) = v;
         }
     } else {
 #pragma unroll
-        for (int k = 0; k < (1 << R); ++k) tile[reg_addr<C, R>(k, soff, sr)] = a[k];
+        for (int k = 0; k < (1 << R); ++k) memcpy(tile + reg_addr<C, R>(k, soff, sr), &a[k], sizeof(C));
     }
 }
 

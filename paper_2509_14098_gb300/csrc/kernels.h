@@ -7,11 +7,21 @@
 
 namespace svk {
 
-cudaError_t launch_stage_fwd(int elem_bytes, int R, void* psi, const Stage* st, const Group* gr,
-                             const Op* op, const Term* te, int T, uint64_t ntiles, cudaStream_t s);
-cudaError_t launch_stage_bwd(int elem_bytes, int R, void* psi, void* lam, const Stage* st,
-                             const Group* gr, const Op* op, const Term* te, double* partial, int T,
-                             uint32_t nslots, uint64_t ntiles, cudaStream_t s);
+// Device pointers of one stage launch (blob sections + state buffers).
+struct StageLaunch {
+    void* psi;
+    void* lam;                 // backward only
+    const Stage* stage;        // this stage's descriptor (device)
+    const Group* groups;
+    const void* ops;           // DevOp<Real>[]
+    const void* terms;         // DevTerm<Real>[]
+    const void* slots;         // PhaseSlot<Real>[]
+    double* partial;           // backward: per-tile gradient partials
+};
+// hst: host copy of the same stage (launch geometry).
+cudaError_t launch_stage_fwd(int elem_bytes, const StageLaunch& L, const Stage& hst, cudaStream_t s);
+cudaError_t launch_stage_bwd(int elem_bytes, const StageLaunch& L, const Stage& hst, cudaStream_t s);
+size_t stage_smem_bytes(int elem_bytes, const Stage& st, bool backward);
 
 // Bit-permutation sweep descriptor: out[pi(x)] = in[x], pi moves physical bit p to dst[p].
 struct PermDesc {

@@ -76,7 +76,11 @@ class Lowerer {
         if (param >= 0) p.params.push_back(param);
     }
     void emit_grad_z(int bit, int param);
-    void flush_bit(int t);
+    // Apply the pending terms on bit t before a dense gate on t.  Terms on t and a
+    // register partner become PHASE2 ops; the rest (a constant and single-bit terms on
+    // non-register bits) is either emitted as a PHASE1 op or, when fuse is set,
+    // returned for the dense op to apply as its twiddle.
+    void flush_bit(int t, bool fuse, double* cangle_out, std::vector<svk::Term>* terms_out);
     void flush_all();
     std::string gate(const GateRec& g, const PGate& pg);
     std::string stage(int s);
@@ -92,7 +96,7 @@ void Lowerer::emit_grad_z(int bit, int param) {
 
 // Apply every pending term that involves physical bit t (a register bit of the
 // current group) — right before a dense gate on t.
-void Lowerer::flush_bit(int t) {
+void Lowerer::flush_bit(int t, bool fuse, double* cangle_out, std::vector<svk::Term>* terms_out) {
     const uint64_t tb = 1ull << t;
     const int jt = regidx_[t];
     double cangle = 0.0;
@@ -121,20 +125,28 @@ void Lowerer::flush_bit(int t) {
         }
         it = pending_.erase(it);
     }
-    if (any1) {
-        svk::Op& o = new_op(svk::OP_PHASE1, jt);
-        o.m[0] = std::cos(cangle);
-        o.m[1] = std::sin(cangle);
-        o.term_off = (uint32_t)out_->terms.size();
-        o.n_terms = (uint32_t)terms.size();
-        for (auto& x : terms) out_->terms.push_back(x);
-    }
-    for (auto& kv : pair) {
-        svk::Op& o = new_op(svk::OP_PHASE2, jt);
-        o.u = (uint8_t)kv.first;
+    for (auto& kv : pair) {   // diagonal: order among the phases is free
+        int a = jt, b = kv.first;
+        if (a > b) std::swap(a, b);
+        svk::Op& o = new_op(svk::OP_PHASE2, a);
+        o.u = (uint8_t)b;
         o.m[0] = std::cos(kv.second);
         o.m[1] = std::sin(kv.second);
     }
+    *cangle_out = 0.0;
+    terms_out->clear();
+    if (!any1) return;
+    if (fuse) {
+        *cangle_out = cangle;
+        *terms_out = terms;
+        return;
+    }
+    svk::Op& o = new_op(svk::OP_PHASE1, jt);
+    o.m[0] = std::cos(cangle);
+    o.m[1] = std::sin(cangle);
+    o.term_off = (uint32_t)out_->terms.size();
+    o.n_terms = (uint32_t)terms.size();
+    for (auto& x : terms) out_->terms.push_back(x);
 }
 
 // End of the program: apply every remaining term and the global phase.
@@ -162,7 +174,7 @@ void Lowerer::flush_all() {
             if (rest == 0) e.first += kv.second.angle;
             else e.second.push_back(svk::Term{rest, kv.second.angle});
         } else {
-            t2[{regs[0], regs[1]}] += kv.second.angle;
+            t2[{std::min(regs[0], regs[1]), std::max(regs[0], regs[1])}] += kv.second.angle;
         }
     }
     pending_.clear();
@@ -236,7 +248,13 @@ std::string Lowerer::gate(const GateRec& g, const PGate& pg) {
     const int t = kind_is_controlled(g.kind) ? pg.p[1] : pg.p[0];
     const int jt = regidx_[t];
     if (jt < 0) return "internal: dense gate target is not a register bit";
-    flush_bit(t);
+    // The pending phase on t becomes the dense op's twiddle, except for a controlled
+    // gate (the phase applies whatever the control is) and for a parametric gate of
+    // the adjoint program (its gradient op must see the phase un-applied first).
+    const bool fuse = !kind_is_controlled(g.kind) && !(bwd_ && g.param >= 0);
+    double tw_angle = 0.0;
+    std::vector<svk::Term> tw_terms;
+    flush_bit(t, fuse, &tw_angle, &tw_terms);
     double m[8];
     uint8_t type = svk::OP_U;
     switch (g.kind) {
@@ -278,6 +296,13 @@ std::string Lowerer::gate(const GateRec& g, const PGate& pg) {
     }
     svk::Op& o = new_op(type, jt);
     std::memcpy(o.m, m, sizeof(m));
+    if (tw_angle != 0.0 || !tw_terms.empty()) {
+        o.has_tw = 1;
+        o.tw_angle = tw_angle;
+        o.term_off = (uint32_t)out_->terms.size();
+        o.n_terms = (uint32_t)tw_terms.size();
+        for (auto& x : tw_terms) out_->terms.push_back(x);
+    }
     if (kind_is_controlled(g.kind)) {
         int c = pg.p[0];
         if (regidx_[c] >= 0) o.ctrl_reg = 1u << regidx_[c];
@@ -387,6 +412,142 @@ std::string Lowerer::run() {
 }
 
 }  // namespace
+
+template <typename Real>
+static void pack_real(const Program& p, int n, Packed* out) {
+    using DOp = svk::DevOp<Real>;
+    using DTerm = svk::DevTerm<Real>;
+    std::vector<svk::Stage> stages = p.stages;
+    std::vector<svk::Group> groups = p.groups;
+    std::vector<DOp> ops;
+    std::vector<DTerm> terms;
+    std::vector<svk::PhaseSlot<Real>> slots;
+    ops.reserve(p.ops.size());
+    for (auto& st : stages) {
+        const uint32_t first_group = st.group_off;
+        uint32_t first_op = first_group < groups.size() ? p.groups[first_group].op_off : (uint32_t)p.ops.size();
+        uint32_t last_op = first_op;
+        for (uint32_t gi = 0; gi < st.n_groups; ++gi) {
+            const svk::Group& G0 = p.groups[first_group + gi];
+            last_op = G0.op_off + G0.n_ops;
+        }
+        st.op_off = (uint32_t)ops.size();
+        st.n_ops = last_op - first_op;
+        st.phase_off = (uint32_t)slots.size();
+        st.n_phase = 0;
+        st.thr_off = 0;
+        const int TR = (int)st.T - (int)st.R;
+        uint64_t tile_mask = 0;
+        for (uint32_t b = 0; b < st.T; ++b) tile_mask |= 1ull << st.tile_pos[b];
+        for (uint32_t gi = 0; gi < st.n_groups; ++gi) {
+            svk::Group& G = groups[first_group + gi];
+            const svk::Group& G0 = p.groups[first_group + gi];
+            G.op_off = G0.op_off - first_op;
+            for (uint32_t oi = 0; oi < G0.n_ops; ++oi) {
+                const svk::Op& o = p.ops[G0.op_off + oi];
+                DOp d;
+                std::memset(&d, 0, sizeof(d));
+                d.type = o.type;
+                d.j = o.j;
+                d.u = o.u;
+                d.ctrl_reg = o.ctrl_reg;
+                d.ctrl_fix = o.ctrl_fix;
+                d.slot = o.slot;
+                for (int i = 0; i < 8; ++i) d.m[i] = (Real)o.m[i];
+                const bool dense_tw = o.type <= svk::OP_X && o.has_tw;
+                const bool phase = ((o.type == svk::OP_PHASE0 || o.type == svk::OP_PHASE1) && o.n_terms > 0) || dense_tw;
+                if (dense_tw) d.flags |= svk::F_TW;
+                const double cang = dense_tw ? o.tw_angle : std::atan2(o.m[1], o.m[0]);
+                if (phase) {
+                    bool single = true;
+                    for (uint32_t ti = 0; ti < o.n_terms; ++ti)
+                        if (__builtin_popcountll(p.terms[o.term_off + ti].mask) != 1) single = false;
+                    if (!single) {
+                        d.flags |= svk::F_TERMS;
+                        d.term_off = (uint32_t)terms.size();
+                        d.n_terms = o.n_terms;
+                        if (dense_tw) {   // the constant as an always-true (mask 0) term
+                            DTerm t0;
+                            t0.mask = 0;
+                            t0.angle = (Real)o.tw_angle;
+                            t0.pad = 0;
+                            terms.push_back(t0);
+                            d.n_terms++;
+                        }
+                        for (uint32_t ti = 0; ti < o.n_terms; ++ti) {
+                            DTerm t;
+                            t.mask = p.terms[o.term_off + ti].mask;
+                            t.angle = (Real)p.terms[o.term_off + ti].angle;
+                            t.pad = 0;
+                            terms.push_back(t);
+                        }
+                    } else {
+                        // split: global-bit terms per tile, thread-bit terms per thread
+                        d.flags |= svk::F_SLOT;
+                        d.slot = st.n_phase++;
+                        svk::PhaseSlot<Real> ps;
+                        std::memset(&ps, 0, sizeof(ps));
+                        ps.cangle = (Real)cang;
+                        ps.glob_off = (uint32_t)terms.size();
+                        for (uint32_t ti = 0; ti < o.n_terms; ++ti) {
+                            const svk::Term& t = p.terms[o.term_off + ti];
+                            if (t.mask & tile_mask) {
+                                for (int i = 0; i < TR; ++i)
+                                    if (t.mask == G.pthr[i]) {
+                                        ps.J[i] += (Real)t.angle;
+                                        ps.has_thr = 1;
+                                    }
+                            } else {
+                                DTerm dt;
+                                dt.mask = t.mask;
+                                dt.angle = (Real)t.angle;
+                                dt.pad = 0;
+                                terms.push_back(dt);
+                                ps.n_glob++;
+                            }
+                        }
+                        slots.push_back(ps);
+                    }
+                }
+                // flat dispatch code
+                switch (o.type) {
+                    case svk::OP_U: case svk::OP_UR: case svk::OP_X: {
+                        const uint32_t ctrl = (o.ctrl_reg != 0) ? 1u : 0u;
+                        d.code = svk::C_DENSE + ((uint32_t)o.type * 2 + ctrl) * 5 + o.j;
+                        break;
+                    }
+                    case svk::OP_PHASE1: d.code = svk::C_PHASE1 + o.j; break;
+                    case svk::OP_PHASE2: d.code = svk::C_PHASE2 + svk::pair_index(o.j, o.u); break;
+                    case svk::OP_PHASE0: d.code = svk::C_PHASE0; break;
+                    case svk::OP_GRAD_X: d.code = svk::C_GRAD + 0 * 5 + o.j; break;
+                    case svk::OP_GRAD_Y: d.code = svk::C_GRAD + 1 * 5 + o.j; break;
+                    default: d.code = o.u ? svk::C_GRADZ_FIX : svk::C_GRAD + 2 * 5 + o.j; break;
+                }
+                ops.push_back(d);
+            }
+        }
+    }
+    auto put = [&](const void* src, size_t bytes) -> size_t {
+        size_t off = (out->blob.size() + 127) & ~(size_t)127;
+        out->blob.resize(off + bytes + 16, 0);
+        if (bytes) std::memcpy(out->blob.data() + off, src, bytes);
+        return off;
+    };
+    out->blob.clear();
+    out->stage_off = put(stages.data(), stages.size() * sizeof(svk::Stage));
+    out->group_off = put(groups.data(), groups.size() * sizeof(svk::Group));
+    out->op_off = put(ops.data(), ops.size() * sizeof(DOp));
+    out->term_off = put(terms.data(), terms.size() * sizeof(DTerm));
+    out->slot_off = put(slots.data(), slots.size() * sizeof(svk::PhaseSlot<Real>));
+    out->wthr_off = out->slot_off;
+    out->stages = stages;
+}
+
+std::string pack(const Program& p, int n, int elem_bytes, Packed* out) {
+    if (elem_bytes == 8) pack_real<float>(p, n, out);
+    else pack_real<double>(p, n, out);
+    return "";
+}
 
 std::string lower(const Plan& plan, const double* params, int elem_bytes, int rmax, bool backward,
                   Program* out) {

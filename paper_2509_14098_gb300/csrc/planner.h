@@ -81,6 +81,15 @@ struct Program {
     bool identity_map = true;
 };
 
+// Device blob of a lowered program for one precision: Stage[] | Group[] |
+// DevOp<Real>[] | DevTerm<Real>[] | PhaseSlot[] | wthr (complex Real) at the offsets.
+struct Packed {
+    std::vector<uint8_t> blob;
+    size_t stage_off = 0, group_off = 0, op_off = 0, term_off = 0, slot_off = 0, wthr_off = 0;
+    std::vector<svk::Stage> stages;   // with op/phase offsets filled in
+};
+std::string pack(const Program& p, int n, int elem_bytes, Packed* out);
+
 // Lower a plan with bound parameters.  rmax: register bits per thread.
 // backward: un-apply the stages in reverse (conjugate-transposed gates) and emit
 // gradient ops for parametric RX / RY / RZ gates.  Returns "" or an error.

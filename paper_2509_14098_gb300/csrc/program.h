@@ -45,11 +45,12 @@ enum OpType : uint8_t {
                     // the physical bit in ctrl_fix (u=1)
 };
 
-struct Op {                 // 96 bytes
+// Host-side op produced by the lowering (FP64 matrix, generic phase terms).
+struct Op {
     uint8_t type;
     uint8_t j;              // register bit (target)
     uint8_t u;              // second register bit (PHASE2) / flag (GRAD_Z)
-    uint8_t pad0;
+    uint8_t has_tw;         // dense op: phase exp(i (tw_angle + terms)) on the bit-j amplitude first
     uint32_t ctrl_reg;      // controls on register bits (mask over k)
     uint64_t ctrl_fix;      // controls on non-register bits (mask over the fixed index)
     uint32_t term_off;      // first Term of this op
@@ -57,6 +58,7 @@ struct Op {                 // 96 bytes
     uint32_t slot;          // gradient slot (GRAD ops): index into the stage's slot list
     uint32_t pad1;
     double m[8];            // row-major 2x2 (re, im) pairs; PHASE ops use m[0], m[1]
+    double tw_angle;        // dense op twiddle constant (has_tw)
 };
 
 struct Term {               // phase angle added when every bit of mask is set
@@ -64,8 +66,64 @@ struct Term {               // phase angle added when every bit of mask is set
     double angle;
 };
 
-struct Group {
-    uint32_t op_off, n_ops;
+enum OpFlag : uint8_t {
+    F_SLOT = 1,             // PHASE op whose angle comes from phase slot `slot`
+    F_TERMS = 2,            // PHASE op evaluated from its DevTerm list on the fixed index
+    F_TW = 4,               // dense op preceded by a phase on its target bit (F_SLOT / F_TERMS
+                            // give the angle; a dense op's constant is a mask-0 term)
+};
+
+// Device op: 64 bytes (complex64 kernels) / 96 bytes (complex128 kernels).  The
+// kernels stage a stage's ops in shared memory once per CTA.
+template <typename Real>
+struct alignas(16) DevOp {
+    uint8_t type;
+    uint8_t j;
+    uint8_t u;
+    uint8_t flags;
+    uint32_t ctrl_reg;
+    uint64_t ctrl_fix;
+    uint32_t slot;          // phase slot (F_SLOT) or gradient slot (GRAD ops)
+    uint32_t term_off;      // F_TERMS: DevTerm range
+    uint32_t n_terms;
+    uint32_t code;          // flat dispatch code (op_code())
+    Real m[8];
+};
+
+// Flat dispatch codes: one switch selects the op kind, its control form and its
+// compile-time register bit(s).
+enum : uint32_t {
+    C_DENSE = 0,            // + ((type * 2 + controlled) * 5 + j), type in {U, UR, X}: 0..29
+    C_PHASE1 = 30,          // + j
+    C_PHASE2 = 35,          // + pair index of (j < u): 0..9
+    C_PHASE0 = 45,
+    C_GRAD = 46,            // + (kind * 5 + j), kind 0 = X, 1 = Y, 2 = Z on a register bit
+    C_GRADZ_FIX = 61,       // Z on a non-register bit
+};
+SVK_HD uint32_t pair_index(int j, int u) {   // j < u < 5: (0,1..4) -> 0..3, (1,2..4) -> 4..6, (2,3..4) -> 7..8, (3,4) -> 9
+    return (uint32_t)(j == 0 ? u - 1 : j == 1 ? u + 2 : j == 2 ? u + 4 : 9);
+}
+
+template <typename Real>
+struct DevTerm {
+    uint64_t mask;
+    Real angle;
+    Real pad;
+};
+
+// Phase slot of a PHASE op whose terms are all single bits: the angle is
+// cangle + sum of global-bit terms (evaluated once per tile) + sum over the thread
+// bits i of the op's group of J[i] * bit i of threadIdx.x.
+template <typename Real>
+struct alignas(16) PhaseSlot {
+    Real cangle;
+    uint32_t glob_off, n_glob;   // DevTerm range (single global bits)
+    uint32_t has_thr;            // any J[i] != 0
+    Real J[kMaxT];
+};
+
+struct alignas(16) Group {
+    uint32_t op_off, n_ops;       // relative to the stage's first op
     uint8_t reg_pos[kMaxR];
     uint8_t thr_pos[kMaxT];
     uint8_t pairs;          // tile bit 0 is register bit 0: load amplitude pairs as 16 B
@@ -81,6 +139,9 @@ struct Stage {
     uint32_t group_off, n_groups;
     uint32_t n_slots;       // gradient slots of this stage (backward)
     uint32_t slot_off;      // first global slot
+    uint32_t op_off, n_ops; // this stage's ops (groups index relative to op_off)
+    uint32_t phase_off, n_phase;  // phase slots of this stage
+    uint32_t thr_off;       // unused
     uint32_t pad;
     uint8_t glob_pos[kMaxQ];  // physical positions of the global bits (ascending)
     uint8_t tile_pos[kMaxT];  // physical positions of the tile bits (ascending)
