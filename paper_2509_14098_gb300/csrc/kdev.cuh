@@ -47,11 +47,18 @@ __device__ __forceinline__ double2 expi(double a) {
     sincos(a, &s, &c);
     return make_double2(c, s);
 }
+// e^{2 pi i k / 2^32}: the turn count as a signed fraction is already in [-pi, pi)
+__device__ __forceinline__ float2 expi(uint32_t k) {
+    const float a = (float)(int32_t)k * 1.4629180792671596e-09f;   // 2 pi / 2^32
+    float s, c;
+    __sincosf(a, &s, &c);
+    return make_float2(c, s);
+}
 
 template <typename Real>
-__device__ __forceinline__ Real term_angle(const DevTerm<Real>* __restrict__ terms, uint32_t off,
-                                           uint32_t n, uint64_t fix) {
-    Real ang = 0;
+__device__ __forceinline__ typename AngT<Real>::type term_angle(const DevTerm<Real>* __restrict__ terms,
+                                                                uint32_t off, uint32_t n, uint64_t fix) {
+    typename AngT<Real>::type ang = 0;
     for (uint32_t i = 0; i < n; ++i) {
         const uint64_t m = terms[off + i].mask;
         if ((fix & m) == m) ang += terms[off + i].angle;
@@ -172,7 +179,7 @@ template <typename Real>
 struct OpCtx {
     uint64_t fix;                                   // thread's fixed physical index
     const PhaseSlot<Real>* slots;                   // shared memory (thread-bit coefficients)
-    const Real* ang;                                // shared memory: per-tile slot angles
+    const typename AngT<Real>::type* ang;           // shared memory: per-tile slot angles
     uint32_t tid;
     int TR;
     const DevTerm<Real>* __restrict__ terms;
@@ -183,7 +190,7 @@ __device__ __forceinline__ typename CT<Real>::C phase_factor(const DevOp<Real>& 
     using C = typename CT<Real>::C;
     if (o.flags & F_SLOT) {
         const PhaseSlot<Real>& ps = x.slots[o.slot];
-        Real ang = x.ang[o.slot];
+        typename AngT<Real>::type ang = x.ang[o.slot];
         if (ps.has_thr)
             for (int i = 0; i < x.TR; ++i)
                 if ((x.tid >> i) & 1) ang += ps.J[i];
@@ -437,12 +444,13 @@ __device__ __forceinline__ void stage_prologue(Group* sgr, DevOp<Real>* sops, Ph
 
 // Per-tile slot angles: the constant plus the terms on global bits set in this tile.
 template <typename Real>
-__device__ __forceinline__ void tile_angles(Real* sang, const PhaseSlot<Real>* __restrict__ gsl,
+__device__ __forceinline__ void tile_angles(typename AngT<Real>::type* sang,
+                                            const PhaseSlot<Real>* __restrict__ gsl,
                                             const DevTerm<Real>* __restrict__ terms, const Stage& st,
                                             uint64_t base, uint32_t tid, uint32_t nthr) {
     for (uint32_t p = tid; p < st.n_phase; p += nthr) {
         const PhaseSlot<Real>& ps = gsl[st.phase_off + p];
-        Real ang = ps.cangle;
+        typename AngT<Real>::type ang = ps.cangle;
         for (uint32_t i = 0; i < ps.n_glob; ++i)
             if (base & terms[ps.glob_off + i].mask) ang += terms[ps.glob_off + i].angle;
         sang[p] = ang;

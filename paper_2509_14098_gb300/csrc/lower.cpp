@@ -413,6 +413,15 @@ std::string Lowerer::run() {
 
 }  // namespace
 
+// radians -> device angle (turns for complex64, radians for complex128)
+template <typename Real> static typename svk::AngT<Real>::type dev_angle(double rad);
+template <> uint32_t dev_angle<float>(double rad) {
+    double t = rad / (2.0 * M_PI);
+    t -= std::floor(t);
+    return (uint32_t)((uint64_t)std::llround(t * 4294967296.0) & 0xffffffffull);
+}
+template <> double dev_angle<double>(double rad) { return rad; }
+
 template <typename Real>
 static void pack_real(const Program& p, int n, Packed* out) {
     using DOp = svk::DevOp<Real>;
@@ -469,7 +478,7 @@ static void pack_real(const Program& p, int n, Packed* out) {
                         if (dense_tw) {   // the constant as an always-true (mask 0) term
                             DTerm t0;
                             t0.mask = 0;
-                            t0.angle = (Real)o.tw_angle;
+                            t0.angle = dev_angle<Real>(o.tw_angle);
                             t0.pad = 0;
                             terms.push_back(t0);
                             d.n_terms++;
@@ -477,7 +486,7 @@ static void pack_real(const Program& p, int n, Packed* out) {
                         for (uint32_t ti = 0; ti < o.n_terms; ++ti) {
                             DTerm t;
                             t.mask = p.terms[o.term_off + ti].mask;
-                            t.angle = (Real)p.terms[o.term_off + ti].angle;
+                            t.angle = dev_angle<Real>(p.terms[o.term_off + ti].angle);
                             t.pad = 0;
                             terms.push_back(t);
                         }
@@ -487,20 +496,20 @@ static void pack_real(const Program& p, int n, Packed* out) {
                         d.slot = st.n_phase++;
                         svk::PhaseSlot<Real> ps;
                         std::memset(&ps, 0, sizeof(ps));
-                        ps.cangle = (Real)cang;
+                        ps.cangle = dev_angle<Real>(cang);
                         ps.glob_off = (uint32_t)terms.size();
                         for (uint32_t ti = 0; ti < o.n_terms; ++ti) {
                             const svk::Term& t = p.terms[o.term_off + ti];
                             if (t.mask & tile_mask) {
                                 for (int i = 0; i < TR; ++i)
                                     if (t.mask == G.pthr[i]) {
-                                        ps.J[i] += (Real)t.angle;
+                                        ps.J[i] += dev_angle<Real>(t.angle);   // wraps mod 2 pi in turns
                                         ps.has_thr = 1;
                                     }
                             } else {
                                 DTerm dt;
                                 dt.mask = t.mask;
-                                dt.angle = (Real)t.angle;
+                                dt.angle = dev_angle<Real>(t.angle);
                                 dt.pad = 0;
                                 terms.push_back(dt);
                                 ps.n_glob++;

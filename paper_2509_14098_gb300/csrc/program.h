@@ -104,10 +104,17 @@ SVK_HD uint32_t pair_index(int j, int u) {   // j < u < 5: (0,1..4) -> 0..3, (1,
     return (uint32_t)(j == 0 ? u - 1 : j == 1 ? u + 2 : j == 2 ? u + 4 : 9);
 }
 
+// Phase angles on the device: complex64 kernels use 32-bit fixed-point turns
+// (angle = 2 pi k / 2^32), whose sums are exact modulo 2 pi (the QFT's dyadic angles
+// are represented exactly); complex128 kernels use FP64 radians.
+template <typename Real> struct AngT;
+template <> struct AngT<float> { using type = uint32_t; };
+template <> struct AngT<double> { using type = double; };
+
 template <typename Real>
 struct DevTerm {
     uint64_t mask;
-    Real angle;
+    typename AngT<Real>::type angle;
     Real pad;
 };
 
@@ -116,10 +123,10 @@ struct DevTerm {
 // bits i of the op's group of J[i] * bit i of threadIdx.x.
 template <typename Real>
 struct alignas(16) PhaseSlot {
-    Real cangle;
+    typename AngT<Real>::type cangle;
     uint32_t glob_off, n_glob;   // DevTerm range (single global bits)
     uint32_t has_thr;            // any J[i] != 0
-    Real J[kMaxT];
+    typename AngT<Real>::type J[kMaxT];
 };
 
 struct alignas(16) Group {

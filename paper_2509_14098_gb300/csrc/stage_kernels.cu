@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT >= 512 ? 1 : 2)) k_stage_fwd(typen
     Group* sgr = reinterpret_cast<Group*>(buf1 + (1u << T));
     DevOp<Real>* sops = reinterpret_cast<DevOp<Real>*>(sgr + ng);
     PhaseSlot<Real>* ssl = reinterpret_cast<PhaseSlot<Real>*>(sops + st.n_ops);
-    Real* sang = reinterpret_cast<Real*>(ssl + st.n_phase);
+    typename AngT<Real>::type* sang = reinterpret_cast<typename AngT<Real>::type*>(ssl + st.n_phase);
     const bool gtab = group_table_fits(st.n_groups, nthr);
     const uint32_t ngt = gtab ? ng : 0;
     uint64_t* gfix = reinterpret_cast<uint64_t*>(
@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT >= 512 ? 1 : 2)) k_stage_bwd(typen
     Group* sgr = reinterpret_cast<Group*>(tl + (1u << T));
     DevOp<Real>* sops = reinterpret_cast<DevOp<Real>*>(sgr + st.n_groups);
     PhaseSlot<Real>* ssl = reinterpret_cast<PhaseSlot<Real>*>(sops + st.n_ops);
-    Real* sang = reinterpret_cast<Real*>(ssl + st.n_phase);
+    typename AngT<Real>::type* sang = reinterpret_cast<typename AngT<Real>::type*>(ssl + st.n_phase);
     float* gsm = reinterpret_cast<float*>(sang + st.n_phase);
     const uint32_t tid = threadIdx.x, nthr = blockDim.x;
     const uint32_t nw = (nthr + 31) >> 5;
