@@ -238,6 +238,24 @@ sv_status sv_expval(sv_handle h, const sv_observable* obs, double* out);
 /* ||psi||^2 in FP64; synchronises. */
 sv_status sv_norm(sv_handle h, double* out);
 
+/* ||psi||^2 in FP64 without allocating anything (the paper has no counterpart).
+ * For callers that cannot call cudaMalloc: their device memory already belongs to
+ * their own allocator, or an allocation's implicit device synchronisation is not
+ * acceptable where they call.  No handle is needed and nothing is allocated: the
+ * caller passes the state (dev_state: 2^n_qubits amplitudes of dtype, 16-byte
+ * aligned, on the current device) and dev_out (one device double, written with the
+ * result); the per-block partial sums use a file-scope static device array of
+ * 2^14 doubles (128 KiB, held by every GPU that loads the library until exit), one
+ * partial per 2^18 amplitudes, so n_qubits is limited to [1, 32]; larger states are
+ * rejected with SV_ERR_ARG.  The first call on a device looks the array's device
+ * address up (with that device current); make that first call before any stream
+ * capture.  Work is enqueued on cuda_stream (NULL = legacy default stream) and the
+ * call returns without synchronising.  Every call shares the one array: calls that
+ * overlap on the GPU (different streams, or different host threads) race on it and
+ * must be serialised by the caller.  Errors: SV_ERR_ARG, SV_ERR_CUDA. */
+sv_status sv_norm_noalloc(const void* dev_state, uint32_t n_qubits, sv_dtype dtype, void* cuda_stream,
+                          double* dev_out);
+
 /* Adjoint differentiation of E(theta) = <psi(theta)|O|psi(theta)>: runs the
  * forward circuit from the current state, forms lambda = O psi, then un-applies
  * the partitions in reverse to psi and lambda together while accumulating

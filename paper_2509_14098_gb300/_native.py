@@ -85,6 +85,7 @@ _SIGS = {
     "sv_permute": ([_vp, ctypes.POINTER(_u32)], ctypes.c_int),
     "sv_expval": ([_vp, ctypes.POINTER(sv_observable), _dp], ctypes.c_int),
     "sv_norm": ([_vp, _dp], ctypes.c_int),
+    "sv_norm_noalloc": ([_vp, _u32, ctypes.c_int, _vp, _vp], ctypes.c_int),
     "sv_grad": ([_vp, _vp, _dp, ctypes.POINTER(sv_observable), _dp, _dp], ctypes.c_int),
     "sv_timing_enable": ([_vp, ctypes.c_int], ctypes.c_int),
     "sv_timing_read": ([_vp, ctypes.POINTER(sv_timing), ctypes.c_int], ctypes.c_int),

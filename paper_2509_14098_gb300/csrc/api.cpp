@@ -70,6 +70,11 @@ size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 }  // namespace
 
+namespace svh {
+// error reporting for entry points defined in other translation units
+sv_status set_error(sv_status s, const char* msg) { return fail(s, msg); }
+}  // namespace svh
+
 struct sv_plan_s {
     svh::Plan plan;
 };
