@@ -706,14 +706,16 @@ sv_status sv_grad(sv_handle h, const sv_plan* plan, const double* params, const 
         const svk::Stage& st = bst[i];
         const uint64_t ntiles = 1ull << (h->n - st.T);
         cudaEvent_t t0 = tick(h);
+        uint32_t grid = 0;
         SV_CUDA(svk::launch_stage_bwd(h->eb, h->bwd.launch(i, h->psi, h->scratch.p, (double*)h->partial.p),
-                                      st, h->stream));
+                                      st, h->stream, &grid));
         tock(h, t0, TK_BWD);
         h->info.backward_sweeps += 1;
         h->info.kernel_launches += 1;
         h->info.hbm_bytes += 4.0 * (double)state_bytes(h);
+        (void)ntiles;
         if (st.n_slots) {
-            SV_CUDA(svk::launch_reduce_rows((double*)h->partial.p, ntiles, st.n_slots,
+            SV_CUDA(svk::launch_reduce_rows((double*)h->partial.p, grid, st.n_slots,
                                             (double*)h->slot_sum.p + st.slot_off, h->stream));
             h->info.kernel_launches += 1;
         }

@@ -330,58 +330,76 @@ __device__ __forceinline__ DevOp<Real> load_op(const DevOp<Real>* p) {
     return o;
 }
 
-template <typename Real, int R, int TYPE, bool CTRL, int J>
-__device__ __forceinline__ void dense_case(typename RegT<Real>::type (&a)[1 << R], const DevOp<Real>& o,
+template <typename Real, int R, int NV, int TYPE, bool CTRL, int J>
+__device__ __forceinline__ void dense_case(typename RegT<Real>::type (&a)[NV][1 << R], const DevOp<Real>& o,
                                            const OpCtx<Real>& x) {
     using C = typename CT<Real>::C;
     if constexpr (J < R) {
         if ((x.fix & o.ctrl_fix) != o.ctrl_fix) return;   // control on a thread / global bit
-        if constexpr (sizeof(Real) == 4) {
-            if (o.flags & F_TW) pd_phase_bit<R, J>(a, phase_factor<Real>(o, x));
-            if constexpr (TYPE == OP_X) pd_x<R, J, CTRL>(a, o.ctrl_reg);
-            else if constexpr (TYPE == OP_UR) pd_ur<R, J, CTRL>(a, o.m, o.ctrl_reg);
-            else pd_u<R, J, CTRL>(a, o.m, o.ctrl_reg);
-        } else {
-            if (o.flags & F_TW) phase_bit<R, J, C>(a, phase_factor<Real>(o, x));
-            if constexpr (TYPE == OP_X) dense_x<R, J, CTRL, C>(a, o.ctrl_reg);
-            else if constexpr (TYPE == OP_UR) dense_ur<R, J, CTRL, C, Real>(a, o.m, o.ctrl_reg);
-            else dense_u<R, J, CTRL, C, Real>(a, o.m, o.ctrl_reg);
+        if (o.flags & F_TW) {
+            const C w = phase_factor<Real>(o, x);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                if constexpr (sizeof(Real) == 4) pd_phase_bit<R, J>(a[v], w);
+                else phase_bit<R, J, C>(a[v], w);
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            if constexpr (sizeof(Real) == 4) {
+                if constexpr (TYPE == OP_X) pd_x<R, J, CTRL>(a[v], o.ctrl_reg);
+                else if constexpr (TYPE == OP_UR) pd_ur<R, J, CTRL>(a[v], o.m, o.ctrl_reg);
+                else pd_u<R, J, CTRL>(a[v], o.m, o.ctrl_reg);
+            } else {
+                if constexpr (TYPE == OP_X) dense_x<R, J, CTRL, C>(a[v], o.ctrl_reg);
+                else if constexpr (TYPE == OP_UR) dense_ur<R, J, CTRL, C, Real>(a[v], o.m, o.ctrl_reg);
+                else dense_u<R, J, CTRL, C, Real>(a[v], o.m, o.ctrl_reg);
+            }
         }
     }
 }
 
-template <typename Real, int R, int J>
-__device__ __forceinline__ void phase1_case(typename RegT<Real>::type (&a)[1 << R], const DevOp<Real>& o,
+template <typename Real, int R, int NV, int J>
+__device__ __forceinline__ void phase1_case(typename RegT<Real>::type (&a)[NV][1 << R], const DevOp<Real>& o,
                                             const OpCtx<Real>& x) {
     if constexpr (J < R) {
-        if constexpr (sizeof(Real) == 4) pd_phase_bit<R, J>(a, phase_factor<Real>(o, x));
-        else phase_bit<R, J, typename CT<Real>::C>(a, phase_factor<Real>(o, x));
+        const typename CT<Real>::C w = phase_factor<Real>(o, x);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            if constexpr (sizeof(Real) == 4) pd_phase_bit<R, J>(a[v], w);
+            else phase_bit<R, J, typename CT<Real>::C>(a[v], w);
+        }
     }
 }
-template <typename Real, int R, int J, int U>
-__device__ __forceinline__ void phase2_case(typename RegT<Real>::type (&a)[1 << R], const DevOp<Real>& o) {
+template <typename Real, int R, int NV, int J, int U>
+__device__ __forceinline__ void phase2_case(typename RegT<Real>::type (&a)[NV][1 << R], const DevOp<Real>& o) {
     if constexpr (U < R) {
         typename CT<Real>::C w;
         w.x = o.m[0];
         w.y = o.m[1];
-        if constexpr (sizeof(Real) == 4) pd_phase_pair<R, J, U>(a, w);
-        else phase_pair<R, J, U, typename CT<Real>::C>(a, w);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            if constexpr (sizeof(Real) == 4) pd_phase_pair<R, J, U>(a[v], w);
+            else phase_pair<R, J, U, typename CT<Real>::C>(a[v], w);
+        }
     }
 }
 
 #define SVK_DENSE_CASES(TYPE, CTRL, BASE)                                                   \
-    case BASE + 0: dense_case<Real, R, TYPE, CTRL, 0>(a, o, x); break;                     \
-    case BASE + 1: dense_case<Real, R, TYPE, CTRL, 1>(a, o, x); break;                     \
-    case BASE + 2: dense_case<Real, R, TYPE, CTRL, 2>(a, o, x); break;                     \
-    case BASE + 3: dense_case<Real, R, TYPE, CTRL, 3>(a, o, x); break;                     \
-    case BASE + 4: dense_case<Real, R, TYPE, CTRL, 4>(a, o, x); break;
+    case BASE + 0: dense_case<Real, R, NV, TYPE, CTRL, 0>(a, o, x); break;                 \
+    case BASE + 1: dense_case<Real, R, NV, TYPE, CTRL, 1>(a, o, x); break;                 \
+    case BASE + 2: dense_case<Real, R, NV, TYPE, CTRL, 2>(a, o, x); break;                 \
+    case BASE + 3: dense_case<Real, R, NV, TYPE, CTRL, 3>(a, o, x); break;                 \
+    case BASE + 4: dense_case<Real, R, NV, TYPE, CTRL, 4>(a, o, x); break;
 #define SVK_PHASE2_CASE(J, U)                                                               \
     case C_PHASE2 + (J == 0 ? U - 1 : J == 1 ? U + 2 : J == 2 ? U + 4 : 9):                  \
-        phase2_case<Real, R, J, U>(a, o);                                                   \
+        phase2_case<Real, R, NV, J, U>(a, o);                                               \
         break;
 
-template <typename Real, int R>
-__device__ __forceinline__ void apply_op(typename RegT<Real>::type (&a)[1 << R], const DevOp<Real>& o,
+// Apply one (non-gradient) op to NV register arrays (forward: psi; adjoint: psi and
+// lambda), with one dispatch and one phase evaluation.
+template <typename Real, int R, int NV>
+__device__ __forceinline__ void apply_op(typename RegT<Real>::type (&a)[NV][1 << R], const DevOp<Real>& o,
                                          const OpCtx<Real>& x) {
     switch (o.code) {
         SVK_DENSE_CASES(OP_U, false, 0)
@@ -390,22 +408,25 @@ __device__ __forceinline__ void apply_op(typename RegT<Real>::type (&a)[1 << R],
         SVK_DENSE_CASES(OP_UR, true, 15)
         SVK_DENSE_CASES(OP_X, false, 20)
         SVK_DENSE_CASES(OP_X, true, 25)
-        case C_PHASE1 + 0: phase1_case<Real, R, 0>(a, o, x); break;
-        case C_PHASE1 + 1: phase1_case<Real, R, 1>(a, o, x); break;
-        case C_PHASE1 + 2: phase1_case<Real, R, 2>(a, o, x); break;
-        case C_PHASE1 + 3: phase1_case<Real, R, 3>(a, o, x); break;
-        case C_PHASE1 + 4: phase1_case<Real, R, 4>(a, o, x); break;
+        case C_PHASE1 + 0: phase1_case<Real, R, NV, 0>(a, o, x); break;
+        case C_PHASE1 + 1: phase1_case<Real, R, NV, 1>(a, o, x); break;
+        case C_PHASE1 + 2: phase1_case<Real, R, NV, 2>(a, o, x); break;
+        case C_PHASE1 + 3: phase1_case<Real, R, NV, 3>(a, o, x); break;
+        case C_PHASE1 + 4: phase1_case<Real, R, NV, 4>(a, o, x); break;
         SVK_PHASE2_CASE(0, 1) SVK_PHASE2_CASE(0, 2) SVK_PHASE2_CASE(0, 3) SVK_PHASE2_CASE(0, 4)
         SVK_PHASE2_CASE(1, 2) SVK_PHASE2_CASE(1, 3) SVK_PHASE2_CASE(1, 4)
         SVK_PHASE2_CASE(2, 3) SVK_PHASE2_CASE(2, 4)
         SVK_PHASE2_CASE(3, 4)
         case C_PHASE0: {
             const typename CT<Real>::C w = phase_factor<Real>(o, x);
-            if constexpr (sizeof(Real) == 4) {
-                pd_phase_all<R>(a, w);
-            } else {
 #pragma unroll
-                for (int k = 0; k < (1 << R); ++k) a[k] = cmul(a[k], w);
+            for (int v = 0; v < NV; ++v) {
+                if constexpr (sizeof(Real) == 4) {
+                    pd_phase_all<R>(a[v], w);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < (1 << R); ++k) a[v][k] = cmul(a[v][k], w);
+                }
             }
             break;
         }

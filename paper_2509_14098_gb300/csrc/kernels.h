@@ -20,7 +20,9 @@ struct StageLaunch {
 };
 // hst: host copy of the same stage (launch geometry).
 cudaError_t launch_stage_fwd(int elem_bytes, const StageLaunch& L, const Stage& hst, cudaStream_t s);
-cudaError_t launch_stage_bwd(int elem_bytes, const StageLaunch& L, const Stage& hst, cudaStream_t s);
+// grid_out: CTAs launched (rows of per-CTA gradient partials written to L.partial)
+cudaError_t launch_stage_bwd(int elem_bytes, const StageLaunch& L, const Stage& hst, cudaStream_t s,
+                             uint32_t* grid_out);
 size_t stage_smem_bytes(int elem_bytes, const Stage& st, bool backward);
 
 // Bit-permutation sweep descriptor: out[pi(x)] = in[x], pi moves physical bit p to dst[p].

@@ -24,150 +24,6 @@ __host__ __device__ __forceinline__ bool group_table_fits(uint32_t n_groups, uin
     return (size_t)n_groups * nthr * 12 <= 24 * 1024;
 }
 
-// Persistent: CTA b handles tiles b, b + gridDim.x, ... and prefetches the next tile
-// into the second buffer (cp.async) while it computes the current one.  Everything
-// that does not depend on the tile (chunk offsets, each group's thread offsets) is
-// computed once; the tile base advances by an addition in the masked bit space of
-// the global bits: base(t + G) = ((base(t) | ~gmask) + pdep(G)) & gmask.
-template <typename Real, int R, int MAXT>
-__global__ void __launch_bounds__(MAXT, (MAXT >= 512 ? 1 : 2)) k_stage_fwd(typename CT<Real>::C* __restrict__ psi,
-                                                    const Stage* __restrict__ stp,
-                                                    const Group* __restrict__ groups,
-                                                    const DevOp<Real>* __restrict__ gops,
-                                                    const DevTerm<Real>* __restrict__ terms,
-                                                    const PhaseSlot<Real>* __restrict__ slots) {
-    using C = typename CT<Real>::C;
-    constexpr int APC = 16 / (int)sizeof(C);
-    constexpr int LA = APC == 2 ? 1 : 0;
-    constexpr int NCH = (1 << R) / APC;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const Stage& st = *stp;
-    const int T = (int)st.T;
-    const int TR = T - R;
-    const uint32_t tid = threadIdx.x, nthr = blockDim.x;
-    const uint32_t ng = st.n_groups;
-    C* buf0 = reinterpret_cast<C*>(smem_raw);
-    C* buf1 = buf0 + (1u << T);
-    Group* sgr = reinterpret_cast<Group*>(buf1 + (1u << T));
-    DevOp<Real>* sops = reinterpret_cast<DevOp<Real>*>(sgr + ng);
-    PhaseSlot<Real>* ssl = reinterpret_cast<PhaseSlot<Real>*>(sops + st.n_ops);
-    typename AngT<Real>::type* sang = reinterpret_cast<typename AngT<Real>::type*>(ssl + st.n_phase);
-    const bool gtab = group_table_fits(st.n_groups, nthr);
-    const uint32_t ngt = gtab ? ng : 0;
-    uint64_t* gfix = reinterpret_cast<uint64_t*>(
-        (reinterpret_cast<uintptr_t>(sang + st.n_phase) + 15) & ~(uintptr_t)15);   // [ngt][nthr]
-    uint64_t* chp = gfix + (size_t)ngt * nthr;                                      // [NCH]
-    uint32_t* gsoff = reinterpret_cast<uint32_t*>(chp + NCH);                         // [ngt][nthr]
-    uint32_t* chs = gsoff + (size_t)ngt * nthr;                                       // [NCH]
-    const uint64_t ntiles = 1ull << st.n_glob;
-
-    uint64_t t = blockIdx.x;
-    if (t >= ntiles) return;
-    // tile-independent offsets
-    uint64_t gmask = 0, pstep = 0, base = 0;
-    for (uint32_t i = 0; i < st.n_glob; ++i) {
-        const uint64_t b = 1ull << st.glob_pos[i];
-        gmask |= b;
-        if ((gridDim.x >> i) & 1) pstep |= b;
-        if ((t >> i) & 1) base |= b;
-    }
-    uint64_t ptid = 0;
-    uint32_t stid = 0;
-    for (int b = 0; b < TR; ++b)
-        if ((tid >> b) & 1) {
-            ptid ^= st.ptile[b + LA];
-            stid ^= st.swbit[b + LA];
-        }
-    // first load (chunk offsets for i computed inline once; tables for later tiles)
-#pragma unroll
-    for (int i = 0; i < NCH; ++i) {
-        uint64_t pi = 0;
-        uint32_t si = 0;
-#pragma unroll
-        for (int b = 0; (1 << b) < NCH; ++b)
-            if ((i >> b) & 1) {
-                pi ^= st.ptile[TR + LA + b];
-                si ^= st.swbit[TR + LA + b];
-            }
-        cp_async16(buf0 + (stid ^ si), psi + (base | (ptid ^ pi)));
-        if (tid == 0) {
-            chp[i] = pi;
-            chs[i] = si;
-        }
-    }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-    stage_prologue<Real>(sgr, sops, ssl, st, groups, gops, slots, tid, nthr);
-    for (uint32_t g = 0; g < ngt; ++g) {
-        const Group& G = groups[st.group_off + g];
-        uint64_t f = 0;
-        uint32_t so = 0;
-        for (int i = 0; i < TR; ++i)
-            if ((tid >> i) & 1) {
-                f ^= G.pthr[i];
-                so ^= G.sthr[i];
-            }
-        gfix[g * nthr + tid] = f;
-        gsoff[g * nthr + tid] = so;
-    }
-    __syncthreads();
-
-    OpCtx<Real> x;
-    x.slots = ssl;
-    x.ang = sang;
-    x.tid = tid;
-    x.TR = TR;
-    x.terms = terms;
-    for (uint32_t it = 0; t < ntiles; t += gridDim.x, ++it) {
-        C* cur = (it & 1) ? buf1 : buf0;
-        C* nxt = (it & 1) ? buf0 : buf1;
-        const uint64_t tn = t + gridDim.x;
-        const uint64_t bn = ((base | ~gmask) + pstep) & gmask;
-        if (tn < ntiles) {
-#pragma unroll
-            for (int i = 0; i < NCH; ++i) cp_async16(nxt + (stid ^ chs[i]), psi + (bn | (ptid ^ chp[i])));
-            asm volatile("cp.async.commit_group;\ncp.async.wait_group 1;\n" ::: "memory");
-        } else {
-            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-        }
-        if (st.n_phase) tile_angles<Real>(sang, slots, terms, st, base, tid, nthr);
-        __syncthreads();
-        for (uint32_t g = 0; g < ng; ++g) {
-            const Group& G = sgr[g];
-            uint64_t f = 0;
-            uint32_t soff = 0;
-            if (gtab) {
-                f = gfix[g * nthr + tid];
-                soff = gsoff[g * nthr + tid];
-            } else {
-                for (int i = 0; i < TR; ++i)
-                    if ((tid >> i) & 1) {
-                        f ^= G.pthr[i];
-                        soff ^= G.sthr[i];
-                    }
-            }
-            x.fix = base ^ f;
-            uint32_t sr[R];
-#pragma unroll
-            for (int j = 0; j < R; ++j) sr[j] = G.sreg[j];
-            const bool pairs = G.pairs != 0;
-            typename RegT<Real>::type a[1 << R];
-            load_regs<typename RegT<Real>::type, C, R>(a, cur, soff, sr, pairs);
-            const DevOp<Real>* op = sops + G.op_off;
-            const uint32_t nops = G.n_ops;
-            for (uint32_t oi = 0; oi < nops; ++oi) apply_op<Real, R>(a, load_op<Real>(op + oi), x);
-            store_regs<typename RegT<Real>::type, C, R>(a, cur, soff, sr, pairs);
-            __syncthreads();
-        }
-#pragma unroll
-        for (int i = 0; i < NCH; ++i) {
-            const float4 v = *reinterpret_cast<const float4*>(cur + (stid ^ chs[i]));
-            *reinterpret_cast<float4*>(psi + (base | (ptid ^ chp[i]))) = v;
-        }
-        base = bn;
-        __syncthreads();   // cur is refilled by the prefetch of the next iteration but one
-    }
-}
-
 // ---------------------------------------------------------------------------
 // backward
 // ---------------------------------------------------------------------------
@@ -186,7 +42,7 @@ template <> __device__ __forceinline__ double2 to_c<double>(double2 v) { return 
 
 template <typename Real, int R, int J>
 __device__ __forceinline__ Real grad_pairs(const typename RegT<Real>::type (&ps)[1 << R],
-                                           const typename RegT<Real>::type (&la)[1 << R], uint8_t type) {
+                                           const typename RegT<Real>::type (&la)[1 << R], int type) {
     Real acc = 0;
 #pragma unroll
     for (int k = 0; k < (1 << R); ++k) {
@@ -206,39 +62,130 @@ __device__ __forceinline__ Real grad_pairs(const typename RegT<Real>::type (&ps)
     return acc;
 }
 
-template <typename Real, int R, int MAXT>
-__global__ void __launch_bounds__(MAXT, (MAXT >= 512 ? 1 : 2)) k_stage_bwd(typename CT<Real>::C* __restrict__ psi,
-                                                   typename CT<Real>::C* __restrict__ lam,
-                                                   const Stage* __restrict__ stp,
-                                                   const Group* __restrict__ groups,
-                                                   const DevOp<Real>* __restrict__ gops,
-                                                   const DevTerm<Real>* __restrict__ terms,
-                                                   const PhaseSlot<Real>* __restrict__ slots,
-                                                   double* __restrict__ partial) {
+// ---------------------------------------------------------------------------
+// shared-memory layout of k_stage (identical on host and device)
+// ---------------------------------------------------------------------------
+struct SmemLayout {
+    size_t groups, ops, slots, ang, gfix, chp, gsoff, chs, gsm, total;
+};
+__host__ __device__ __forceinline__ size_t align_up(size_t x, size_t a) { return (x + a - 1) & ~(a - 1); }
+__host__ __device__ __forceinline__ SmemLayout smem_layout(int elem_bytes, int nv, int nb, uint32_t T,
+                                                           uint32_t n_groups, uint32_t n_ops, uint32_t n_phase,
+                                                           uint32_t n_slots, uint32_t nthr, int nch) {
+    const size_t opb = elem_bytes == 8 ? sizeof(DevOp<float>) : sizeof(DevOp<double>);
+    const size_t slb = elem_bytes == 8 ? sizeof(PhaseSlot<float>) : sizeof(PhaseSlot<double>);
+    const size_t angb = elem_bytes == 8 ? sizeof(uint32_t) : sizeof(double);
+    const uint32_t ngt = group_table_fits(n_groups, nthr) ? n_groups : 0;
+    SmemLayout L;
+    size_t o = ((size_t)elem_bytes << T) * nb * nv;   // nv vectors x nb buffers
+    L.groups = o;  o += n_groups * sizeof(Group);
+    L.ops = o;     o += n_ops * opb;
+    L.slots = o;   o += n_phase * slb;
+    L.ang = o;     o = align_up(o + n_phase * angb, 16);
+    L.gfix = o;    o += (size_t)ngt * nthr * 8;
+    L.chp = o;     o += (size_t)nch * 8;
+    L.gsoff = o;   o += (size_t)ngt * nthr * 4;
+    L.chs = o;     o = align_up(o + (size_t)nch * 4, 16);
+    L.gsm = o;     o += (nv == 2) ? (size_t)n_slots * ((nthr + 31) / 32) * sizeof(float) : 0;
+    L.total = o;
+    return L;
+}
+
+// ---------------------------------------------------------------------------
+// The stage sweep.  NV = 1: forward (psi).  NV = 2: adjoint (psi and lambda together,
+// gradient ops accumulate Im <lambda|G|psi>).
+// Persistent: CTA b handles tiles b, b + gridDim.x, ... and prefetches the next tile
+// into the second buffer (cp.async) while it computes the current one.  Everything
+// that does not depend on the tile (chunk offsets, each group's thread offsets) is
+// computed once; the tile base advances by an addition in the masked bit space of
+// the global bits: base(t + G) = ((base(t) | ~gmask) + pdep(G)) & gmask.  Gradient
+// partial sums accumulate per CTA in FP64 (per warp, fixed order) and are written once.
+// ---------------------------------------------------------------------------
+template <typename Real, int R, int MAXT, int NV, int NB>
+__global__ void __launch_bounds__(MAXT, (MAXT >= 512 ? 1 : 2))
+    k_stage(typename CT<Real>::C* __restrict__ psi, typename CT<Real>::C* __restrict__ lam,
+            const Stage* __restrict__ stp, const Group* __restrict__ groups,
+            const DevOp<Real>* __restrict__ gops, const DevTerm<Real>* __restrict__ terms,
+            const PhaseSlot<Real>* __restrict__ slots, double* __restrict__ partial) {
     using C = typename CT<Real>::C;
+    using A = typename RegT<Real>::type;
+    using Ang = typename AngT<Real>::type;
+    constexpr int APC = 16 / (int)sizeof(C);
+    constexpr int LA = APC == 2 ? 1 : 0;
+    constexpr int NCH = (1 << R) / APC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Stage& st = *stp;
     const int T = (int)st.T;
     const int TR = T - R;
-    C* tp = reinterpret_cast<C*>(smem_raw);
-    C* tl = tp + (1u << T);
-    Group* sgr = reinterpret_cast<Group*>(tl + (1u << T));
-    DevOp<Real>* sops = reinterpret_cast<DevOp<Real>*>(sgr + st.n_groups);
-    PhaseSlot<Real>* ssl = reinterpret_cast<PhaseSlot<Real>*>(sops + st.n_ops);
-    typename AngT<Real>::type* sang = reinterpret_cast<typename AngT<Real>::type*>(ssl + st.n_phase);
-    float* gsm = reinterpret_cast<float*>(sang + st.n_phase);
     const uint32_t tid = threadIdx.x, nthr = blockDim.x;
-    const uint32_t nw = (nthr + 31) >> 5;
-    const uint32_t warp = tid >> 5, lane = tid & 31;
+    const uint32_t nw = (nthr + 31) >> 5, warp = tid >> 5, lane = tid & 31;
+    const uint32_t ng = st.n_groups;
     const uint32_t nslots = st.n_slots;
-    const uint64_t base = tile_base(blockIdx.x, st.glob_pos);
+    const SmemLayout Ly = smem_layout((int)sizeof(C), NV, NB, st.T, ng, st.n_ops, st.n_phase, nslots, nthr, NCH);
+    C* tiles = reinterpret_cast<C*>(smem_raw);              // tile (v, b) at (v * NB + b) << T
+    Group* sgr = reinterpret_cast<Group*>(smem_raw + Ly.groups);
+    DevOp<Real>* sops = reinterpret_cast<DevOp<Real>*>(smem_raw + Ly.ops);
+    PhaseSlot<Real>* ssl = reinterpret_cast<PhaseSlot<Real>*>(smem_raw + Ly.slots);
+    Ang* sang = reinterpret_cast<Ang*>(smem_raw + Ly.ang);
+    uint64_t* gfix = reinterpret_cast<uint64_t*>(smem_raw + Ly.gfix);
+    uint64_t* chp = reinterpret_cast<uint64_t*>(smem_raw + Ly.chp);
+    uint32_t* gsoff = reinterpret_cast<uint32_t*>(smem_raw + Ly.gsoff);
+    uint32_t* chs = reinterpret_cast<uint32_t*>(smem_raw + Ly.chs);
+    float* gsm = reinterpret_cast<float*>(smem_raw + Ly.gsm);
+    const bool gtab = group_table_fits(ng, nthr);
+    const uint64_t ntiles = 1ull << st.n_glob;
+    C* vec[2] = {psi, lam};
 
-    tile_load<C, R>(tp, psi, base, st.ptile, st.swbit, TR, tid);
-    tile_load<C, R>(tl, lam, base, st.ptile, st.swbit, TR, tid);
+    uint64_t t = blockIdx.x;
+    if (t >= ntiles) return;
+    uint64_t gmask = 0, pstep = 0, base = 0;
+    for (uint32_t i = 0; i < st.n_glob; ++i) {
+        const uint64_t b = 1ull << st.glob_pos[i];
+        gmask |= b;
+        if ((gridDim.x >> i) & 1) pstep |= b;
+        if ((t >> i) & 1) base |= b;
+    }
+    uint64_t ptid = 0;
+    uint32_t stid = 0;
+    for (int b = 0; b < TR; ++b)
+        if ((tid >> b) & 1) {
+            ptid ^= st.ptile[b + LA];
+            stid ^= st.swbit[b + LA];
+        }
+#pragma unroll
+    for (int i = 0; i < NCH; ++i) {
+        uint64_t pi = 0;
+        uint32_t si = 0;
+#pragma unroll
+        for (int b = 0; (1 << b) < NCH; ++b)
+            if ((i >> b) & 1) {
+                pi ^= st.ptile[TR + LA + b];
+                si ^= st.swbit[TR + LA + b];
+            }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) cp_async16(tiles + ((size_t)(v * NB) << T) + (stid ^ si), vec[v] + (base | (ptid ^ pi)));
+        if (tid == 0) {
+            chp[i] = pi;
+            chs[i] = si;
+        }
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
     stage_prologue<Real>(sgr, sops, ssl, st, groups, gops, slots, tid, nthr);
-    tile_angles<Real>(sang, slots, terms, st, base, tid, nthr);
-    for (uint32_t i = tid; i < nslots * nw; i += nthr) gsm[i] = 0.f;
-    cp_async_commit_wait_all();
+    if (gtab)
+        for (uint32_t g = 0; g < ng; ++g) {
+            const Group& G = groups[st.group_off + g];
+            uint64_t f = 0;
+            uint32_t so = 0;
+            for (int i = 0; i < TR; ++i)
+                if ((tid >> i) & 1) {
+                    f ^= G.pthr[i];
+                    so ^= G.sthr[i];
+                }
+            gfix[g * nthr + tid] = f;
+            gsoff[g * nthr + tid] = so;
+        }
+    if (NV == 2)
+        for (uint32_t i = tid; i < nslots * nw; i += nthr) gsm[i] = 0.f;
     __syncthreads();
 
     OpCtx<Real> x;
@@ -248,83 +195,125 @@ __global__ void __launch_bounds__(MAXT, (MAXT >= 512 ? 1 : 2)) k_stage_bwd(typen
     x.TR = TR;
     x.terms = terms;
     const uint32_t wmask = nthr >= 32 ? 0xffffffffu : ((1u << nthr) - 1u);
-    for (uint32_t g = 0; g < st.n_groups; ++g) {
-        const Group& G = sgr[g];
-        uint64_t fix = base;
-        uint32_t soff = 0;
-        for (int i = 0; i < TR; ++i)
-            if ((tid >> i) & 1) {
-                fix ^= G.pthr[i];
-                soff ^= G.sthr[i];
+    for (uint32_t it = 0; t < ntiles; t += gridDim.x, ++it) {
+        const int cb = NB == 2 ? (int)(it & 1) : 0;
+        const uint64_t tn = t + gridDim.x;
+        const uint64_t bn = ((base | ~gmask) + pstep) & gmask;
+        if (NB == 2 && tn < ntiles) {   // prefetch the next tile into the other buffer
+#pragma unroll
+            for (int i = 0; i < NCH; ++i)
+#pragma unroll
+                for (int v = 0; v < NV; ++v)
+                    cp_async16(tiles + ((size_t)(v * NB + (cb ^ 1)) << T) + (stid ^ chs[i]),
+                               vec[v] + (bn | (ptid ^ chp[i])));
+            asm volatile("cp.async.commit_group;\ncp.async.wait_group 1;\n" ::: "memory");
+        } else {
+            if (NB == 1 && it > 0) {       // one buffer: load this tile now (the first came with the prologue)
+#pragma unroll
+                for (int i = 0; i < NCH; ++i)
+#pragma unroll
+                    for (int v = 0; v < NV; ++v)
+                        cp_async16(tiles + ((size_t)(v * NB) << T) + (stid ^ chs[i]), vec[v] + (base | (ptid ^ chp[i])));
+                asm volatile("cp.async.commit_group;\n" ::: "memory");
             }
-        x.fix = fix;
-        uint32_t sr[R];
-#pragma unroll
-        for (int j = 0; j < R; ++j) sr[j] = G.sreg[j];
-        const bool pairs = G.pairs != 0;
-        typename RegT<Real>::type ps[1 << R], la[1 << R];
-        load_regs<typename RegT<Real>::type, C, R>(ps, tp, soff, sr, pairs);
-        load_regs<typename RegT<Real>::type, C, R>(la, tl, soff, sr, pairs);
-        const DevOp<Real>* op = sops + G.op_off;
-        for (uint32_t oi = 0; oi < G.n_ops; ++oi) {
-            const DevOp<Real> o = load_op<Real>(op + oi);
-            if (o.type >= OP_GRAD_X) {
-                Real acc = 0;
-                if (o.type == OP_GRAD_Z && o.u) {
-                    // Z on a non-register bit: a sign per thread
-#pragma unroll
-                    for (int k = 0; k < (1 << R); ++k) acc += im_conj_mul<Real>(to_c<Real>(la[k]), to_c<Real>(ps[k]));
-                    if ((fix & o.ctrl_fix) != 0) acc = -acc;
-                } else {
-                    SVK_SWITCH_J(o.j, R, (acc = grad_pairs<Real, R, J_>(ps, la, o.type)));
-                }
-                float v = (float)acc;
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1)
-                    if ((uint32_t)off < nthr) v += __shfl_xor_sync(wmask, v, off);
-                if (lane == 0) gsm[o.slot * nw + warp] += v;
-            } else {
-                apply_op<Real, R>(ps, o, x);
-                apply_op<Real, R>(la, o, x);
-            }
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         }
-        store_regs<typename RegT<Real>::type, C, R>(ps, tp, soff, sr, pairs);
-        store_regs<typename RegT<Real>::type, C, R>(la, tl, soff, sr, pairs);
+        if (st.n_phase) tile_angles<Real>(sang, slots, terms, st, base, tid, nthr);
         __syncthreads();
+        C* cur0 = tiles + ((size_t)cb << T);
+        C* cur1 = tiles + ((size_t)(NB + cb) << T);
+        for (uint32_t g = 0; g < ng; ++g) {
+            const Group& G = sgr[g];
+            uint64_t f = 0;
+            uint32_t soff = 0;
+            if (gtab) {
+                f = gfix[g * nthr + tid];
+                soff = gsoff[g * nthr + tid];
+            } else {
+                for (int i = 0; i < TR; ++i)
+                    if ((tid >> i) & 1) {
+                        f ^= G.pthr[i];
+                        soff ^= G.sthr[i];
+                    }
+            }
+            x.fix = base ^ f;
+            uint32_t sr[R];
+#pragma unroll
+            for (int j = 0; j < R; ++j) sr[j] = G.sreg[j];
+            const bool pairs = G.pairs != 0;
+            const DevOp<Real>* op = sops + G.op_off;
+            const uint32_t nops = G.n_ops;
+            A a[NV][1 << R];
+            load_regs<A, C, R>(a[0], cur0, soff, sr, pairs);
+            if constexpr (NV == 2) load_regs<A, C, R>(a[NV - 1], cur1, soff, sr, pairs);
+            for (uint32_t oi = 0; oi < nops; ++oi) {
+                const DevOp<Real> o = load_op<Real>(op + oi);
+                if (NV == 2 && o.type >= OP_GRAD_X) {
+                    const auto& ps = a[0];
+                    const auto& la = a[NV - 1];
+                    Real acc = 0;
+                    if (o.type == OP_GRAD_Z && o.u) {   // Z on a non-register bit: a sign per thread
+#pragma unroll
+                        for (int k = 0; k < (1 << R); ++k) acc += im_conj_mul<Real>(to_c<Real>(la[k]), to_c<Real>(ps[k]));
+                        if ((x.fix & o.ctrl_fix) != 0) acc = -acc;
+                    } else {
+                        SVK_SWITCH_J(o.j, R, (acc = grad_pairs<Real, R, J_>(ps, la, o.type)));
+                    }
+                    float v = (float)acc;   // FP32 over the warp, per warp across this CTA's tiles
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1)
+                        if ((uint32_t)off < nthr) v += __shfl_xor_sync(wmask, v, off);
+                    if (lane == 0) gsm[o.slot * nw + warp] += v;
+                } else {
+                    apply_op<Real, R, NV>(a, o, x);
+                }
+            }
+            store_regs<A, C, R>(a[0], cur0, soff, sr, pairs);
+            if constexpr (NV == 2) store_regs<A, C, R>(a[NV - 1], cur1, soff, sr, pairs);
+            __syncthreads();
+        }
+#pragma unroll
+        for (int i = 0; i < NCH; ++i)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const float4 val = *reinterpret_cast<const float4*>(tiles + ((size_t)(v * NB + cb) << T) + (stid ^ chs[i]));
+                *reinterpret_cast<float4*>(vec[v] + (base | (ptid ^ chp[i]))) = val;
+            }
+        base = bn;
+        __syncthreads();   // the current buffers are refilled by the prefetch after next
     }
-    tile_store<C, R>(tp, psi, base, st.ptile, st.swbit, TR, tid);
-    tile_store<C, R>(tl, lam, base, st.ptile, st.swbit, TR, tid);
-    for (uint32_t s = tid; s < nslots; s += nthr) {
-        double sum = 0.0;
-        for (uint32_t w = 0; w < nw; ++w) sum += (double)gsm[s * nw + w];
-        partial[(size_t)blockIdx.x * nslots + s] = sum;
-    }
+    if (NV == 2)
+        for (uint32_t s = tid; s < nslots; s += nthr) {
+            double sum = 0.0;
+            for (uint32_t w = 0; w < nw; ++w) sum += (double)gsm[s * nw + w];
+            partial[(size_t)blockIdx.x * nslots + s] = sum;
+        }
 }
 
 // ---------------------------------------------------------------------------
 // launch wrappers
 // ---------------------------------------------------------------------------
+static size_t smem_bytes_nb(int elem_bytes, const Stage& st, int nv, int nb) {
+    const int R = (int)st.R;
+    const int nch = (1 << R) / (16 / elem_bytes);
+    return smem_layout(elem_bytes, nv, nb, st.T, st.n_groups, st.n_ops, st.n_phase, st.n_slots,
+                       1u << (st.T - st.R), nch > 0 ? nch : 1).total;
+}
+// the smaller (single-buffered) footprint: the launch never needs more than this
 size_t stage_smem_bytes(int elem_bytes, const Stage& st, bool backward) {
-    const size_t opb = elem_bytes == 8 ? sizeof(DevOp<float>) : sizeof(DevOp<double>);
-    const size_t slb = elem_bytes == 8 ? sizeof(PhaseSlot<float>) : sizeof(PhaseSlot<double>);
-    const uint32_t nthr = 1u << (st.T - st.R);
-    // two tiles (forward: double buffer; backward: psi and lambda) + staged program
-    size_t b = ((size_t)elem_bytes << st.T) * 2 + st.n_groups * sizeof(Group) + st.n_ops * opb +
-               st.n_phase * (slb + (size_t)elem_bytes);
-    if (!backward)   // per-group thread offsets (when they fit) and chunk tables (+ slack)
-        b += 16 + (group_table_fits(st.n_groups, nthr) ? (size_t)st.n_groups * nthr * 12 : 0) + 32 * 12;
-    if (backward) b += (size_t)st.n_slots * ((nthr + 31) / 32) * sizeof(float);
-    return b;
+    return smem_bytes_nb(elem_bytes, st, backward ? 2 : 1, 1);
 }
 
-template <typename Real, int R, int MAXT>
-static cudaError_t launch_fwd_RT(const StageLaunch& L, const Stage& hst, cudaStream_t s) {
+template <typename Real, int R, int MAXT, int NV, int NB>
+static cudaError_t try_launch(const StageLaunch& L, const Stage& hst, cudaStream_t s, uint32_t* grid_out,
+                              int min_per_sm, bool* launched) {
     using C = typename CT<Real>::C;
-    const size_t smem = stage_smem_bytes(sizeof(C), hst, false);
-    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+    *launched = false;
+    const size_t smem = smem_bytes_nb(sizeof(C), hst, NV, NB);
+    if (smem > 227 * 1024) return cudaSuccess;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_stage_fwd<Real, R, MAXT>,
+        cudaError_t e = cudaFuncSetAttribute(k_stage<Real, R, MAXT, NV, NB>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         if (e != cudaSuccess) return e;
         configured = true;
@@ -334,84 +323,66 @@ static cudaError_t launch_fwd_RT(const StageLaunch& L, const Stage& hst, cudaStr
     int per_sm = 0, dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage_fwd<Real, R, MAXT>, nthr, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage<Real, R, MAXT, NV, NB>, nthr, smem);
     if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (per_sm < min_per_sm || per_sm < 1) return cudaSuccess;
     const uint64_t grid = std::min<uint64_t>(ntiles, (uint64_t)per_sm * (uint64_t)nsm);
-    k_stage_fwd<Real, R, MAXT><<<(unsigned)grid, nthr, smem, s>>>(
-        (C*)L.psi, L.stage, L.groups, (const DevOp<Real>*)L.ops, (const DevTerm<Real>*)L.terms,
-        (const PhaseSlot<Real>*)L.slots);
+    if (grid_out) *grid_out = (uint32_t)grid;
+    k_stage<Real, R, MAXT, NV, NB><<<(unsigned)grid, nthr, smem, s>>>(
+        (C*)L.psi, (C*)L.lam, L.stage, L.groups, (const DevOp<Real>*)L.ops, (const DevTerm<Real>*)L.terms,
+        (const PhaseSlot<Real>*)L.slots, L.partial);
+    *launched = true;
     return cudaGetLastError();
 }
-// 256-thread bound (up to 255 registers) unless the tile needs 512 threads
-template <typename Real, int R>
-static cudaError_t launch_fwd_R(const StageLaunch& L, const Stage& hst, cudaStream_t s) {
-    if ((hst.T - R) <= 8) return launch_fwd_RT<Real, R, 256>(L, hst, s);
-    if ((hst.T - R) == 9) return launch_fwd_RT<Real, R, 512>(L, hst, s);
+
+// double-buffered tiles while that still leaves >= 2 CTAs per SM, else single-buffered
+template <typename Real, int R, int MAXT, int NV>
+static cudaError_t launch_RT(const StageLaunch& L, const Stage& hst, cudaStream_t s, uint32_t* grid_out) {
+    bool ok = false;
+    cudaError_t e = try_launch<Real, R, MAXT, NV, 2>(L, hst, s, grid_out, 2, &ok);
+    if (e != cudaSuccess || ok) return e;
+    e = try_launch<Real, R, MAXT, NV, 1>(L, hst, s, grid_out, 1, &ok);
+    if (e != cudaSuccess) return e;
+    return ok ? cudaSuccess : cudaErrorInvalidConfiguration;
+}
+// 256-thread bound (128 registers, 2 CTAs) unless the tile needs 512 threads
+template <typename Real, int R, int NV>
+static cudaError_t launch_R(const StageLaunch& L, const Stage& hst, cudaStream_t s, uint32_t* grid_out) {
+    if ((hst.T - R) <= 8) return launch_RT<Real, R, 256, NV>(L, hst, s, grid_out);
+    if ((hst.T - R) == 9) return launch_RT<Real, R, 512, NV>(L, hst, s, grid_out);
     return cudaErrorInvalidConfiguration;
+}
+
+template <int NV>
+static cudaError_t launch_any(int elem_bytes, const StageLaunch& L, const Stage& hst, cudaStream_t s,
+                              uint32_t* grid_out) {
+    if (elem_bytes == 8) {
+        switch (hst.R) {
+            case 1: return launch_R<float, 1, NV>(L, hst, s, grid_out);
+            case 2: return launch_R<float, 2, NV>(L, hst, s, grid_out);
+            case 3: return launch_R<float, 3, NV>(L, hst, s, grid_out);
+            case 4: return launch_R<float, 4, NV>(L, hst, s, grid_out);
+            case 5: if constexpr (NV == 1) return launch_R<float, 5, NV>(L, hst, s, grid_out);
+                    break;
+        }
+    } else {
+        switch (hst.R) {
+            case 1: return launch_R<double, 1, NV>(L, hst, s, grid_out);
+            case 2: return launch_R<double, 2, NV>(L, hst, s, grid_out);
+            case 3: return launch_R<double, 3, NV>(L, hst, s, grid_out);
+            case 4: if constexpr (NV == 1) return launch_R<double, 4, NV>(L, hst, s, grid_out);
+                    break;
+        }
+    }
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_stage_fwd(int elem_bytes, const StageLaunch& L, const Stage& hst, cudaStream_t s) {
-    if (elem_bytes == 8) {
-        switch (hst.R) {
-            case 1: return launch_fwd_R<float, 1>(L, hst, s);
-            case 2: return launch_fwd_R<float, 2>(L, hst, s);
-            case 3: return launch_fwd_R<float, 3>(L, hst, s);
-            case 4: return launch_fwd_R<float, 4>(L, hst, s);
-            case 5: return launch_fwd_R<float, 5>(L, hst, s);
-        }
-    } else {
-        switch (hst.R) {
-            case 1: return launch_fwd_R<double, 1>(L, hst, s);
-            case 2: return launch_fwd_R<double, 2>(L, hst, s);
-            case 3: return launch_fwd_R<double, 3>(L, hst, s);
-            case 4: return launch_fwd_R<double, 4>(L, hst, s);
-        }
-    }
-    return cudaErrorInvalidValue;
+    return launch_any<1>(elem_bytes, L, hst, s, nullptr);
 }
-
-template <typename Real, int R, int MAXT>
-static cudaError_t launch_bwd_RT(const StageLaunch& L, const Stage& hst, cudaStream_t s) {
-    using C = typename CT<Real>::C;
-    const size_t smem = stage_smem_bytes(sizeof(C), hst, true);
-    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_stage_bwd<Real, R, MAXT>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    const uint64_t ntiles = 1ull << hst.n_glob;
-    k_stage_bwd<Real, R, MAXT><<<(unsigned)ntiles, 1u << (hst.T - R), smem, s>>>(
-        (C*)L.psi, (C*)L.lam, L.stage, L.groups, (const DevOp<Real>*)L.ops, (const DevTerm<Real>*)L.terms,
-        (const PhaseSlot<Real>*)L.slots, L.partial);
-    return cudaGetLastError();
-}
-template <typename Real, int R>
-static cudaError_t launch_bwd_R(const StageLaunch& L, const Stage& hst, cudaStream_t s) {
-    if ((hst.T - R) <= 8) return launch_bwd_RT<Real, R, 256>(L, hst, s);
-    if ((hst.T - R) == 9) return launch_bwd_RT<Real, R, 512>(L, hst, s);
-    return cudaErrorInvalidConfiguration;
-}
-
-cudaError_t launch_stage_bwd(int elem_bytes, const StageLaunch& L, const Stage& hst, cudaStream_t s) {
-    if (elem_bytes == 8) {
-        switch (hst.R) {
-            case 1: return launch_bwd_R<float, 1>(L, hst, s);
-            case 2: return launch_bwd_R<float, 2>(L, hst, s);
-            case 3: return launch_bwd_R<float, 3>(L, hst, s);
-            case 4: return launch_bwd_R<float, 4>(L, hst, s);
-        }
-    } else {
-        switch (hst.R) {
-            case 1: return launch_bwd_R<double, 1>(L, hst, s);
-            case 2: return launch_bwd_R<double, 2>(L, hst, s);
-            case 3: return launch_bwd_R<double, 3>(L, hst, s);
-        }
-    }
-    return cudaErrorInvalidValue;
+cudaError_t launch_stage_bwd(int elem_bytes, const StageLaunch& L, const Stage& hst, cudaStream_t s,
+                             uint32_t* grid_out) {
+    return launch_any<2>(elem_bytes, L, hst, s, grid_out);
 }
 
 }  // namespace svk
