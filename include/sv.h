@@ -197,6 +197,15 @@ sv_status sv_partition(const sv_circuit* circuit, uint32_t L, sv_plan** out);
  * paper's unconstrained partitioner, e.g. for its worked examples). */
 sv_status sv_partition_ex(const sv_circuit* circuit, uint32_t L, uint32_t n_fixed, sv_plan** out);
 
+/* Partition for the split-precision tensor-core stages: the same DAG, closeness and
+ * frontier pass, but without the two exemptions (every qubit of every gate must be
+ * local; SWAP stays a relabel), so each partition is one fixed dense unitary on its k
+ * local qubits, fused in FP64 and applied as a GEMM over all 2^(n-k) columns
+ * (sv_run with SV_PREC_TF32X3 or SV_PREC_BF16X3; complex64 states, n >= k + 4).
+ * k in {5, 6, 7} (k = 5 stages run as k = 6 with an identity qubit).  Such a plan can
+ * also run on the CUDA cores (SV_PREC_CUDACORE).  Errors as sv_partition. */
+sv_status sv_partition_gemm(const sv_circuit* circuit, uint32_t k, sv_plan** out);
+
 /* Partition summary.  local_masks[s] = physical-bit mask of stage s's local set
  * (after SWAP relabelling); gate_counts[s] = gates in stage s.  Either array may be
  * NULL; each must hold n_stages entries (query n_stages first with both NULL). */
@@ -221,7 +230,9 @@ sv_status sv_plan_destroy(sv_plan* plan);
  * kernel per partition, then a bit-permutation sweep if the SWAP relabels leave
  * a non-identity qubit map.  params: host array of the circuit's n_params angles
  * (NULL if n_params == 0).  prec: SV_PREC_CUDACORE, or a tensor-core mode (needs a
- * plan from sv_partition_gemm).  Async.
+ * plan from sv_partition_gemm; one tcgen05 GEMM kernel per partition, then the
+ * call synchronises to check the kernels' bounded waits, SV_ERR_TIMEOUT if one gave
+ * up).  Async for SV_PREC_CUDACORE.
  * Errors: SV_ERR_ARG (width mismatch, null params), SV_ERR_UNSUPPORTED
  * (precision / dtype / plan combination), SV_ERR_CUDA. */
 sv_status sv_run(sv_handle h, const sv_plan* plan, const double* params, sv_prec prec);

@@ -112,9 +112,15 @@ def physical_qubits(circuit):
     return out, where
 
 
-def need(gate, phys):
-    """Physical bits a gate requires to be local (Sec. 4.2 exemptions)."""
-    if gate.kind in DIAGONAL or gate.kind == "SWAP":
+def need(gate, phys, strict=False):
+    """Physical bits a gate requires to be local (Sec. 4.2 exemptions).  strict: no
+    exemptions (every qubit of a gate local, SWAP still a relabel) — used when each
+    partition must be one fixed dense unitary on its local qubits."""
+    if gate.kind == "SWAP":
+        return frozenset()
+    if strict:
+        return frozenset(phys)
+    if gate.kind in DIAGONAL:
         return frozenset()
     if gate.kind in CONTROLLED:
         return frozenset((phys[1],))
@@ -125,7 +131,7 @@ class PartitionError(Exception):
     pass
 
 
-def partition(circuit, L, fixed=()):
+def partition(circuit, L, fixed=(), strict=False):
     """Forward frontier pass.  Returns a list of stages (local_bits frozenset, [gate ids in
     execution order]) and the final circuit-qubit -> physical-bit map."""
     gates = circuit.gates
@@ -133,7 +139,7 @@ def partition(circuit, L, fixed=()):
     preds, _, _ = build_dag(circuit)
     cc, _, _, _ = closeness(circuit)
     phys, final_map = physical_qubits(circuit)
-    needs = [need(g, p) for g, p in zip(gates, phys)]
+    needs = [need(g, p, strict) for g, p in zip(gates, phys)]
     fixed = frozenset(fixed)
     if len(fixed) > L:
         raise PartitionError("fixed bits exceed the budget")
@@ -179,7 +185,7 @@ def partition(circuit, L, fixed=()):
     return stages, final_map
 
 
-def validate(circuit, stages, L, fixed=()):
+def validate(circuit, stages, L, fixed=(), strict=False):
     """Invariants: every gate exactly once; the concatenated order respects every
     dependency; each stage's gates need only its local bits; |local| <= L; fixed bits local."""
     preds, _, _ = build_dag(circuit)
@@ -194,7 +200,7 @@ def validate(circuit, stages, L, fixed=()):
         for i in ids:
             if i in seen:
                 return False, f"gate {i} twice"
-            if not need(circuit.gates[i], phys[i]) <= local:
+            if not need(circuit.gates[i], phys[i], strict) <= local:
                 return False, f"gate {i} needs a non-local bit"
             for p in preds[i]:
                 if p not in seen:

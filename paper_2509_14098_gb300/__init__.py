@@ -19,13 +19,16 @@ __all__ = ["Plan", "StateVector", "SvError", "partition", "SV_C64", "SV_C128",
 class Plan:
     """Host-side partition of a circuit (sv_partition / sv_partition_ex)."""
 
-    def __init__(self, circuit, L, n_fixed=None):
+    def __init__(self, circuit, L, n_fixed=None, gemm=False):
+        """gemm=True: partition for tensor-core stages (sv_partition_gemm, L = fusion width k)."""
         self.circuit = circuit
         self.L = L
         c, self._gates = N.circuit_struct(circuit)
         self._c = c
         h = ctypes.c_void_p()
-        if n_fixed is None:
+        if gemm:
+            N.check(N.lib.sv_partition_gemm(ctypes.byref(c), L, ctypes.byref(h)))
+        elif n_fixed is None:
             N.check(N.lib.sv_partition(ctypes.byref(c), L, ctypes.byref(h)))
         else:
             N.check(N.lib.sv_partition_ex(ctypes.byref(c), L, n_fixed, ctypes.byref(h)))

@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include "gemm.h"
 #include "kernels.h"
 #include "planner.h"
 #include "sv.h"
@@ -92,6 +93,9 @@ struct sv_handle_s {
     DevBuf slot_sum;     // per-slot gradient sums
     DevBuf red;          // reduction partials and results
     DevBuf aux;          // Pauli sweeps / permutation descriptors
+    DevBuf gemm;         // tensor-core stage descriptors + operand chunks
+    DevBuf status;       // device-side error flag (bounded waits)
+    std::vector<uint8_t> gemm_host;
     std::vector<uint8_t> aux_host;
     sv_run_info info{};
     // kernel timing: event pairs recorded around sweep launches
@@ -430,6 +434,8 @@ sv_status sv_destroy(sv_handle h) {
     h->slot_sum.release();
     h->red.release();
     h->aux.release();
+    h->gemm.release();
+    h->status.release();
     delete h;
     return SV_OK;
 }
@@ -483,7 +489,7 @@ sv_status sv_last_run_info(sv_handle h, sv_run_info* out) {
 }
 
 // ---------------- partitioning ----------------
-static sv_status build_plan(const sv_circuit* c, uint32_t L, uint32_t n_fixed, sv_plan** out) {
+static sv_status build_plan(const sv_circuit* c, uint32_t L, uint32_t n_fixed, sv_plan** out, bool strict = false) {
     if (!out) return fail(SV_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!c || (c->n_gates && !c->gates)) return fail(SV_ERR_ARG, "null circuit");
@@ -527,7 +533,8 @@ static sv_status build_plan(const sv_circuit* c, uint32_t L, uint32_t n_fixed, s
     P.n_fixed = nf;
     const uint64_t fixed = nf ? ((1ull << nf) - 1) : 0;
     const uint64_t universe = (P.n >= 64) ? ~0ull : ((1ull << P.n) - 1);
-    std::string err = svh::partition_core(P.n, P.phys, (int)L, fixed, universe, &P.top, &P.cc);
+    std::string err = svh::partition_core(P.n, P.phys, (int)L, fixed, universe, &P.top, &P.cc, strict);
+    if (strict) P.gemm_k = (int)L;
     if (!err.empty()) {
         delete p;
         return fail(SV_ERR_PARTITION, err);
@@ -542,6 +549,11 @@ sv_status sv_partition(const sv_circuit* circuit, uint32_t L, sv_plan** out) {
 }
 sv_status sv_partition_ex(const sv_circuit* circuit, uint32_t L, uint32_t n_fixed, sv_plan** out) {
     return build_plan(circuit, L, n_fixed, out);
+}
+
+sv_status sv_partition_gemm(const sv_circuit* circuit, uint32_t k, sv_plan** out) {
+    if (k < 5 || k > 7) return fail(SV_ERR_ARG, "fusion width k must be 5, 6 or 7");
+    return build_plan(circuit, k, 0, out, true);
 }
 
 sv_status sv_plan_stages(const sv_plan* plan, uint32_t* n_stages, uint64_t* local_masks,
@@ -625,12 +637,56 @@ static sv_status run_forward(sv_handle h, const sv_plan* plan, const double* par
     return SV_OK;
 }
 
+static sv_status run_gemm(sv_handle h, const sv_plan* plan, const double* params, int prec) {
+    const svh::Plan& P = plan->plan;
+    svh::GemmProgram gp;
+    std::string err = svh::plan_gemm(P, params, prec, &gp);
+    if (!err.empty()) return fail(SV_ERR_UNSUPPORTED, err);
+    const size_t sb = gp.stages.size() * sizeof(svk::GemmStage);
+    const size_t aoff = align16(sb);
+    const size_t total = aoff + gp.ablob.size();
+    for (auto& st : gp.stages)
+        if (svk::gemm_smem_bytes(st) > 227 * 1024) return fail(SV_ERR_UNSUPPORTED, "tensor-core stage too wide");
+    SV_CUDA(h->gemm.ensure(total));
+    SV_CUDA(h->status.ensure(sizeof(int)));
+    h->gemm_host.assign(total, 0);
+    std::memcpy(h->gemm_host.data(), gp.stages.data(), sb);
+    std::memcpy(h->gemm_host.data() + aoff, gp.ablob.data(), gp.ablob.size());
+    SV_CUDA(cudaMemcpyAsync(h->gemm.p, h->gemm_host.data(), total, cudaMemcpyHostToDevice, h->stream));
+    SV_CUDA(cudaMemsetAsync(h->status.p, 0, sizeof(int), h->stream));
+    for (size_t i = 0; i < gp.stages.size(); ++i) {
+        cudaEvent_t t0 = tick(h);
+        SV_CUDA(svk::launch_gemm_stage(prec, h->psi, (const svk::GemmStage*)h->gemm.p + i, gp.stages[i],
+                                       (const uint8_t*)h->gemm.p + aoff, (int*)h->status.p, h->stream));
+        tock(h, t0, TK_STAGE);
+        h->info.stage_sweeps += 1;
+        h->info.kernel_launches += 1;
+        h->info.hbm_bytes += 2.0 * (double)state_bytes(h);
+    }
+    if (!gp.identity_map) {
+        std::vector<uint32_t> m(P.n);
+        for (int q = 0; q < P.n; ++q) m[q] = (uint32_t)P.final_map[q];
+        sv_status s = do_permute(h, m.data());
+        if (s) return s;
+    }
+    int st = 0;
+    SV_CUDA(cudaMemcpyAsync(&st, h->status.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    SV_CUDA(cudaStreamSynchronize(h->stream));
+    if (st) return fail(SV_ERR_TIMEOUT, "a tensor-core stage gave up waiting for its MMAs");
+    return SV_OK;
+}
+
 sv_status sv_run(sv_handle h, const sv_plan* plan, const double* params, sv_prec prec) {
     if (check_handle(h) || !plan) return fail(SV_ERR_ARG, "null argument");
     if (plan->plan.n != (int)h->n) return fail(SV_ERR_ARG, "plan width differs from the state");
     if (plan->plan.n_params > 0 && !params) return fail(SV_ERR_ARG, "params is NULL");
-    if (prec != SV_PREC_CUDACORE) return fail(SV_ERR_UNSUPPORTED, "tensor-core precision needs a GEMM plan");
     h->info = sv_run_info{};
+    if (prec == SV_PREC_TF32X3 || prec == SV_PREC_BF16X3) {
+        if (plan->plan.gemm_k == 0) return fail(SV_ERR_UNSUPPORTED, "tensor-core precision needs a plan from sv_partition_gemm");
+        if (h->dt != SV_C64) return fail(SV_ERR_UNSUPPORTED, "tensor-core stages operate on complex64 states");
+        return run_gemm(h, plan, params, prec == SV_PREC_TF32X3 ? 1 : 2);
+    }
+    if (prec != SV_PREC_CUDACORE) return fail(SV_ERR_ARG, "bad precision");
     return run_forward(h, plan, params, true);
 }
 

@@ -1,0 +1,215 @@
+// gemm_plan.cpp — host side of the split-precision tensor-core stage.
+//
+// A plan partitioned without exemptions (every gate's qubits local) makes each
+// partition one fixed unitary U on its k local qubits.  U is formed in FP64 by
+// applying the partition's gates, in order, to the 2^k basis vectors (local index bit
+// j = the j-th lowest local physical bit).  Its real embedding acts on columns of
+// interleaved (re, im) floats: Ut[2i+a][2j+b] = Re U_ij if a == b, Im U_ij if (a, b) =
+// (1, 0), -Im U_ij if (a, b) = (0, 1).  Ut is split as Ut ~ hi + lo with both halves
+// rounded to nearest (TF32: hi = rn(x), lo = rn(x - hi); BF16 likewise) and stored per
+// K-chunk of 32 columns in the tensor cores' canonical no-swizzle K-major layout.
+#include <cmath>
+#include <complex>
+#include <cstring>
+
+#include "gemm.h"
+#include "planner.h"
+
+namespace svh {
+
+typedef std::complex<double> cd;
+
+static void gate_full(const GateRec& g, const double* params, int* nq, cd m[16]) {
+    auto th = [&](int i) { return g.param >= 0 ? params[g.param] : g.angle[i]; };
+    const cd I(0, 1);
+    const double r = 1.0 / std::sqrt(2.0);
+    cd u[4] = {1, 0, 0, 1};
+    *nq = kind_nq(g.kind);
+    switch (g.kind) {
+        case K_H: u[0] = r; u[1] = r; u[2] = r; u[3] = -r; break;
+        case K_X: case K_CX: u[0] = 0; u[1] = 1; u[2] = 1; u[3] = 0; break;
+        case K_Y: case K_CY: u[0] = 0; u[1] = -I; u[2] = I; u[3] = 0; break;
+        case K_Z: case K_CZ: u[3] = -1; break;
+        case K_S: u[3] = I; break;
+        case K_SDG: u[3] = -I; break;
+        case K_T: u[3] = std::polar(1.0, M_PI / 4); break;
+        case K_TDG: u[3] = std::polar(1.0, -M_PI / 4); break;
+        case K_RX: { double c = std::cos(th(0) / 2), s = std::sin(th(0) / 2); u[0] = c; u[1] = -I * s; u[2] = -I * s; u[3] = c; break; }
+        case K_RY: { double c = std::cos(th(0) / 2), s = std::sin(th(0) / 2); u[0] = c; u[1] = -s; u[2] = s; u[3] = c; break; }
+        case K_RZ: u[0] = std::polar(1.0, -th(0) / 2); u[3] = std::polar(1.0, th(0) / 2); break;
+        case K_P: case K_CP: u[3] = std::polar(1.0, th(0)); break;
+        case K_U3: {
+            double t = g.angle[0], p = g.angle[1], l = g.angle[2];
+            u[0] = std::cos(t / 2); u[1] = -std::polar(1.0, l) * std::sin(t / 2);
+            u[2] = std::polar(1.0, p) * std::sin(t / 2); u[3] = std::polar(1.0, p + l) * std::cos(t / 2);
+            break;
+        }
+        default: break;
+    }
+    if (*nq == 1) {
+        for (int i = 0; i < 4; ++i) m[i] = u[i];
+        return;
+    }
+    // two-qubit: index 2*b(q0) + b(q1); controlled gates act with u on q1 when q0 = 1
+    for (int i = 0; i < 16; ++i) m[i] = 0;
+    if (g.kind == K_SWAP) {
+        m[0] = 1; m[1 * 4 + 2] = 1; m[2 * 4 + 1] = 1; m[15] = 1;
+        return;
+    }
+    m[0] = 1; m[5] = 1;
+    m[2 * 4 + 2] = u[0]; m[2 * 4 + 3] = u[1]; m[3 * 4 + 2] = u[2]; m[3 * 4 + 3] = u[3];
+}
+
+// round to the nearest TF32 value (ties to even)
+static float rn_tf32(float x) {
+    uint32_t b;
+    std::memcpy(&b, &x, 4);
+    b = (b + 0x0FFFu + ((b >> 13) & 1u)) & 0xFFFFE000u;
+    float r;
+    std::memcpy(&r, &b, 4);
+    return r;
+}
+static void split_tf32(float x, float* hi, float* lo) {
+    *hi = rn_tf32(x);
+    *lo = rn_tf32(x - *hi);
+}
+static uint16_t to_bf16(float x) {   // round to nearest even
+    uint32_t b;
+    std::memcpy(&b, &x, 4);
+    uint32_t r = b + 0x7FFFu + ((b >> 16) & 1u);
+    return (uint16_t)(r >> 16);
+}
+static float from_bf16(uint16_t h) {
+    uint32_t b = (uint32_t)h << 16;
+    float x;
+    std::memcpy(&x, &b, 4);
+    return x;
+}
+
+std::string plan_gemm(const Plan& P, const double* params, int prec, GemmProgram* out) {
+    out->stages.clear();
+    out->ablob.clear();
+    const int n = P.n;
+    for (size_t s = 0; s < P.top.local.size(); ++s) {
+        uint64_t local = P.top.local[s];
+        int k = __builtin_popcountll(local);
+        // widen to at least 6 local qubits (an M = 128 accumulator) with identity qubits
+        for (int b = 0; b < n && k < 6; ++b)
+            if (!((local >> b) & 1)) { local |= 1ull << b; ++k; }
+        if (k < 6 || k > 7) return "tensor-core stages need 6 or 7 local qubits (k in 5..7, n >= 6)";
+        if (n - k < 4) return "tensor-core stages need at least 16 columns (n >= k + 4)";
+        svk::GemmStage st;
+        std::memset(&st, 0, sizeof(st));
+        int lp[8], nl = 0;
+        for (int b = 0; b < n; ++b)
+            if ((local >> b) & 1) lp[nl++] = b;
+        st.keff = (uint32_t)k;
+        st.nacc = (uint32_t)((2u << k) / 128);
+        st.nchunk = (uint32_t)((2u << k) / 32);
+        const int ncb = std::min(7, n - k);
+        st.ncol_bits = (uint32_t)ncb;
+        int cp[7], nc = 0, ng = 0;
+        for (int b = 0; b < n; ++b) {
+            if ((local >> b) & 1) continue;
+            if (nc < ncb) cp[nc++] = b;
+            else st.glob_pos[ng++] = (uint8_t)b;
+        }
+        st.n_glob = (uint32_t)ng;
+        // chunk-varying bits (local 0..3, column bits) sorted by physical position
+        int var[11], role[11], nv = 0;
+        for (int j = 0; j < 4; ++j) { var[nv] = lp[j]; role[nv] = j; ++nv; }
+        for (int c = 0; c < ncb; ++c) { var[nv] = cp[c]; role[nv] = 8 + c; ++nv; }
+        for (int a = 0; a < nv; ++a)
+            for (int b2 = a + 1; b2 < nv; ++b2)
+                if (var[b2] < var[a]) { std::swap(var[a], var[b2]); std::swap(role[a], role[b2]); }
+        st.nvar = (uint32_t)nv;
+        for (int a = 0; a < nv; ++a) {
+            st.var_phys[a] = 1ull << var[a];
+            st.var_role[a] = (uint8_t)role[a];
+        }
+        for (int j = 4; j < k; ++j) st.hi_local[j - 4] = 1ull << lp[j];
+        // fused unitary over the local qubits (index bit j <-> lp[j])
+        const int D = 1 << k;
+        int lidx[64];
+        for (int b = 0; b < 64; ++b) lidx[b] = -1;
+        for (int j = 0; j < k; ++j) lidx[lp[j]] = j;
+        std::vector<cd> U((size_t)D * D, 0.0);
+        for (int c = 0; c < D; ++c) U[(size_t)c * D + c] = 1.0;   // column-major: U[col][row]
+        for (uint32_t gi : P.top.ids[s]) {
+            const GateRec& g = P.gates[gi];
+            const PGate& pg = P.phys[gi];
+            if (g.kind == K_SWAP) continue;   // relabel
+            int nq;
+            cd m[16];
+            gate_full(g, params, &nq, m);
+            if (nq == 1) {
+                const int q = lidx[pg.p[0]];
+                if (q < 0) return "internal: gate outside the local set";
+                for (int c = 0; c < D; ++c) {
+                    cd* col = &U[(size_t)c * D];
+                    for (int i = 0; i < D; ++i)
+                        if (!((i >> q) & 1)) {
+                            cd a0 = col[i], a1 = col[i | (1 << q)];
+                            col[i] = m[0] * a0 + m[1] * a1;
+                            col[i | (1 << q)] = m[2] * a0 + m[3] * a1;
+                        }
+                }
+            } else {
+                const int q0 = lidx[pg.p[0]], q1 = lidx[pg.p[1]];
+                if (q0 < 0 || q1 < 0) return "internal: gate outside the local set";
+                for (int c = 0; c < D; ++c) {
+                    cd* col = &U[(size_t)c * D];
+                    for (int i = 0; i < D; ++i) {
+                        if ((i >> q0) & 1 || (i >> q1) & 1) continue;
+                        int idx[4] = {i, i | (1 << q1), i | (1 << q0), i | (1 << q0) | (1 << q1)};
+                        cd v[4] = {col[idx[0]], col[idx[1]], col[idx[2]], col[idx[3]]};
+                        for (int r = 0; r < 4; ++r) {
+                            cd acc = 0;
+                            for (int q = 0; q < 4; ++q) acc += m[r * 4 + q] * v[q];
+                            col[idx[r]] = acc;
+                        }
+                    }
+                }
+            }
+        }
+        // real embedding, split, canonical chunks
+        const int M = 2 * D;   // rows = cols of Ut
+        st.a_off = (uint64_t)out->ablob.size();
+        const bool tf32 = prec == 1;
+        const size_t chunk_bytes = tf32 ? (size_t)M * 128 * 2 : (size_t)M * 64 * 2;
+        st.a_chunk_bytes = (uint32_t)chunk_bytes;
+        out->ablob.resize(out->ablob.size() + chunk_bytes * st.nchunk, 0);
+        uint8_t* base = out->ablob.data() + st.a_off;
+        for (int m = 0; m < M; ++m) {
+            const int i = m >> 1, a = m & 1;
+            for (int kk = 0; kk < M; ++kk) {
+                const int j = kk >> 1, b = kk & 1;
+                const cd u = U[(size_t)j * D + i];
+                const double v = (a == b) ? u.real() : (a == 1 ? u.imag() : -u.imag());
+                const float x = (float)v;
+                const int c = kk / 32, kl = kk % 32;
+                uint8_t* ch = base + (size_t)c * chunk_bytes;
+                if (tf32) {
+                    float hi, lo;
+                    split_tf32(x, &hi, &lo);
+                    const size_t off = (size_t)(m / 8) * 1024 + (kl / 4) * 128 + (m % 8) * 16 + (kl % 4) * 4;
+                    std::memcpy(ch + off, &hi, 4);
+                    std::memcpy(ch + chunk_bytes / 2 + off, &lo, 4);
+                } else {
+                    const uint16_t hi = to_bf16(x);
+                    const uint16_t lo = to_bf16(x - from_bf16(hi));
+                    const size_t off = (size_t)(m / 8) * 512 + (kl / 8) * 128 + (m % 8) * 16 + (kl % 8) * 2;
+                    std::memcpy(ch + off, &hi, 2);
+                    std::memcpy(ch + chunk_bytes / 2 + off, &lo, 2);
+                }
+            }
+        }
+        out->stages.push_back(st);
+    }
+    out->identity_map = true;
+    for (int q = 0; q < n; ++q)
+        if (P.final_map[q] != q) out->identity_map = false;
+    return "";
+}
+
+}  // namespace svh

@@ -70,4 +70,10 @@ cudaError_t launch_reduce_rows(const double* in, uint64_t n, uint32_t rows, doub
 // state set to |0...0>
 cudaError_t launch_zero_state(int elem_bytes, void* psi, uint64_t n_amp, cudaStream_t s);
 
+struct GemmStage;
+size_t gemm_smem_bytes(const GemmStage& st);
+// prec 1 = TF32x3, 2 = BF16x3; d_status receives 1 if a bounded wait gave up
+cudaError_t launch_gemm_stage(int prec, void* psi, const GemmStage* d_stage, const GemmStage& hst,
+                              const uint8_t* d_ablob, int* d_status, cudaStream_t s);
+
 }  // namespace svk

@@ -29,8 +29,14 @@ namespace svh {
 
 static inline int popc64(uint64_t x) { return __builtin_popcountll(x); }
 
-static uint64_t need_mask(const PGate& g) {
-    if (kind_is_diagonal(g.kind) || g.kind == K_SWAP) return 0;
+static uint64_t need_mask(const PGate& g, bool strict) {
+    if (g.kind == K_SWAP) return 0;
+    if (strict) {
+        uint64_t m = 0;
+        for (int i = 0; i < g.nq; ++i) m |= 1ull << g.p[i];
+        return m;
+    }
+    if (kind_is_diagonal(g.kind)) return 0;
     if (kind_is_controlled(g.kind)) return 1ull << g.p[1];
     uint64_t m = 0;
     for (int i = 0; i < g.nq; ++i) m |= 1ull << g.p[i];
@@ -56,7 +62,7 @@ void relabel(int n, const std::vector<GateRec>& gates, std::vector<PGate>* phys,
 }
 
 std::string partition_core(int nbits, const std::vector<PGate>& gates, int L, uint64_t fixed,
-                           uint64_t universe, Partition* out, Centrality* ccout) {
+                           uint64_t universe, Partition* out, Centrality* ccout, bool strict) {
     const int G = (int)gates.size();
     out->local.clear();
     out->ids.clear();
@@ -127,7 +133,7 @@ std::string partition_core(int nbits, const std::vector<PGate>& gates, int L, ui
 
     // --- Step B forward: frontier partition.
     std::vector<uint64_t> need(G);
-    for (int i = 0; i < G; ++i) need[i] = need_mask(gates[i]);
+    for (int i = 0; i < G; ++i) need[i] = need_mask(gates[i], strict);
     std::vector<char> done(G, 0);
     auto ready = [&](int i) {
         for (int p : preds[i])

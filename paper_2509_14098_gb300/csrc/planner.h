@@ -51,8 +51,9 @@ struct Centrality {
 // L: local-bit budget; fixed: bits local in every partition; universe: bits that may
 // be used to fill a partition's local set up to min(L, |universe|) after the cut.
 // Returns "" on success or an error message (status SV_ERR_PARTITION).
+// strict: no exemptions (every qubit of a gate must be local; SWAP stays a relabel).
 std::string partition_core(int nbits, const std::vector<PGate>& gates, int L, uint64_t fixed,
-                           uint64_t universe, Partition* out, Centrality* cc);
+                           uint64_t universe, Partition* out, Centrality* cc, bool strict = false);
 
 // Physical positions of every gate after replaying the SWAP relabels in circuit
 // order, and the final map wire -> physical bit.
@@ -64,6 +65,7 @@ struct Plan {
     int n_params = 0;
     int L = 0;
     int n_fixed = 0;
+    int gemm_k = 0;             // > 0: partitioned without exemptions for tensor-core stages
     std::vector<GateRec> gates;
     std::vector<PGate> phys;
     std::vector<int> final_map;
