@@ -278,6 +278,77 @@ sv_status sv_norm_noalloc(const void* dev_state, uint32_t n_qubits, sv_dtype dty
 sv_status sv_grad(sv_handle h, const sv_plan* plan, const double* params, const sv_observable* obs,
                   double* expval_out, double* grad_out);
 
+/* ---------------------------------------------------------------------------
+ * Batched circuits (many small circuits, one persistent launch)
+ *
+ * The paper partitions one circuit at a time; this form runs many independent
+ * circuits of uneven width together.  Each circuit is partitioned by closeness
+ * centrality exactly as sv_partition does (budget L = its tile width), except that
+ * parametric RZ gates need their qubit (they are lowered as dense ops so that the
+ * program's structure does not depend on the angles).  Circuits with the same
+ * structure share one lowered program; the kernel forms every RX / RY / RZ matrix
+ * from the circuit's own parameters.  One CTA runs one circuit (forward stages, E =
+ * <psi|O|psi>, lambda = O psi, adjoint stages with gradient accumulation, Sec. 4.2
+ * partitions as in sv_grad), taking circuits largest first from a device queue.  A
+ * circuit whose tile holds all its qubits never leaves shared memory.  The whole
+ * evaluation (parameter upload, queue reset, the launch, result download) is one
+ * CUDA graph, captured when the batch is built.
+ * ------------------------------------------------------------------------- */
+typedef struct sv_batch_s sv_batch;
+
+/* Per-width tuning table: for circuits of n qubits, L[n] = tile width (qubits held
+ * in shared memory per tile, 7..13; a circuit with n <= L[n] is held whole) and
+ * k[n] = register-group width (qubits whose gates one thread applies from registers
+ * between shared-memory passes, 2..4, at most L[n] - 5; the fusion width of this
+ * form).  0 = default (L = min(n, 13), k = 4). */
+typedef struct {
+    uint8_t L[41];
+    uint8_t k[41];
+} sv_tune;
+
+typedef struct {
+    uint32_t n_circuits;
+    uint32_t n_programs;         /* distinct lowered structures                          */
+    uint32_t n_resident;         /* circuits held whole in shared memory                 */
+    uint32_t total_params;
+    uint64_t workspace_bytes;    /* HBM workspace (psi and lambda of multi-stage circuits) */
+    uint32_t smem_bytes;         /* dynamic shared memory per CTA                        */
+    uint32_t grid;               /* CTAs of the persistent launch                        */
+    uint32_t graph;              /* 1: the evaluation is a captured CUDA graph           */
+    uint32_t pad;
+    double   last_ms;            /* device time of the last sv_run_batch (graph launch)  */
+} sv_batch_info;
+
+/* Build a batch.  circuits[i] (n_qubits in [7, 30]) and observables[i] (a sum of
+ * Z strings: every Pauli factor I or Z; n_qubits must match) describe circuit i;
+ * its parameters are params[param_off_i ...] with param_off_i the sum of the
+ * n_params of the circuits before it, and the gradient uses the same layout.
+ * Parametric gates: RX, RY, RZ only.  tune: NULL = defaults.  cuda_stream as for
+ * sv_create.  Everything is copied; the inputs may be freed on return.
+ * Errors: SV_ERR_ARG, SV_ERR_UNSUPPORTED (X / Y observable factors, parametric
+ * P / CP, shared memory above the per-CTA limit), SV_ERR_PARTITION, SV_ERR_OOM,
+ * SV_ERR_CUDA. */
+sv_status sv_batch_create(const sv_circuit* circuits, const sv_observable* observables, uint32_t n_circuits,
+                          const sv_tune* tune, void* cuda_stream, sv_batch** out);
+
+/* Evaluate every circuit at params (host, total_params): expval_out[i] (host,
+ * n_circuits) = <psi_i|O_i|psi_i> reduced in FP64, grad_out (host, total_params,
+ * may be NULL) = dE_i/dtheta by the adjoint method.  Replays the captured graph and
+ * synchronises.  Errors: SV_ERR_ARG, SV_ERR_CUDA. */
+sv_status sv_run_batch(sv_batch* b, const double* params, double* expval_out, double* grad_out);
+
+/* Autotuner: for every distinct width n in the batch, time the candidate
+ * (L, k) pairs on up to one wave (one circuit per SM) of the batch's own circuits of
+ * that width (CUDA events, one warm-up then one timed run; candidates: L = n with
+ * k in {2, 3, 4} for n <= 13, L in {11, 12, 13} with k in {3, 4} for wider circuits),
+ * keep the fastest, rebuild the batch with the chosen table and re-capture its
+ * graph.  params: as for sv_run_batch (the timing runs use them).  table_out (may be
+ * NULL) receives the table.  Errors: as sv_batch_create. */
+sv_status sv_autotune(sv_batch* b, const double* params, sv_tune* table_out);
+
+sv_status sv_batch_info_get(const sv_batch* b, sv_batch_info* out);
+sv_status sv_batch_destroy(sv_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

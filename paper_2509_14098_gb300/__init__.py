@@ -12,7 +12,7 @@ import numpy as np
 from . import _native as N
 from ._native import SvError, SV_C64, SV_C128, SV_PREC_CUDACORE, SV_PREC_TF32X3, SV_PREC_BF16X3
 
-__all__ = ["Plan", "StateVector", "SvError", "partition", "SV_C64", "SV_C128",
+__all__ = ["Plan", "StateVector", "Batch", "SvError", "partition", "SV_C64", "SV_C128",
            "SV_PREC_CUDACORE", "SV_PREC_TF32X3", "SV_PREC_BF16X3"]
 
 
@@ -163,3 +163,71 @@ class StateVector:
         info = N.sv_run_info()
         N.check(N.lib.sv_last_run_info(self.handle, ctypes.byref(info)))
         return {f: getattr(info, f) for f, _ in N.sv_run_info._fields_}
+
+
+class Batch:
+    """Many circuits evaluated together (sv_batch_create / sv_run_batch): E_i =
+    <psi_i|O_i|psi_i> and dE_i/dtheta for every circuit, in one persistent launch
+    replayed from a captured CUDA graph.  observables: one Z-string sum per circuit.
+    tune: {n: (L, k)} or None."""
+
+    def __init__(self, circuits, observables, tune=None, stream=None):
+        if len(circuits) != len(observables):
+            raise ValueError("one observable per circuit")
+        self.n_params = [c.n_params for c in circuits]
+        self.total_params = sum(self.n_params)
+        cs = (N.sv_circuit * len(circuits))()
+        os_ = (N.sv_observable * len(circuits))()
+        keep = []
+        for i, (c, o) in enumerate(zip(circuits, observables)):
+            cst, arr = N.circuit_struct(c)
+            ost, ok = N.observable_struct(o)
+            cs[i] = cst
+            os_[i] = ost
+            keep.append((arr, ok))
+        t = None
+        if tune:
+            t = N.sv_tune()
+            for n, (L, k) in tune.items():
+                t.L[n], t.k[n] = L, k
+        h = ctypes.c_void_p()
+        st = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+        N.check(N.lib.sv_batch_create(cs, os_, len(circuits), None if t is None else ctypes.byref(t), st,
+                                      ctypes.byref(h)))
+        self.n = len(circuits)
+        self.handle = h
+
+    def close(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            N.lib.sv_batch_destroy(h)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+    def _params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float64).reshape(-1)
+        if p.size != self.total_params:
+            raise ValueError(f"expected {self.total_params} parameters, got {p.size}")
+        return p
+
+    def run(self, params):
+        """(E per circuit, gradient in the parameters' layout)."""
+        p = self._params(params)
+        e = np.zeros(self.n, dtype=np.float64)
+        g = np.zeros(max(1, self.total_params), dtype=np.float64)
+        N.check(N.lib.sv_run_batch(self.handle, N.as_double_ptr(p), N.as_double_ptr(e), N.as_double_ptr(g)))
+        return e, g[: self.total_params]
+
+    def autotune(self, params):
+        """Time (L, k) candidates per width, rebuild with the best; returns {n: (L, k)}."""
+        p = self._params(params)
+        t = N.sv_tune()
+        N.check(N.lib.sv_autotune(self.handle, N.as_double_ptr(p), ctypes.byref(t)))
+        return {n: (t.L[n], t.k[n]) for n in range(41) if t.L[n]}
+
+    def info(self):
+        i = N.sv_batch_info()
+        N.check(N.lib.sv_batch_info_get(self.handle, ctypes.byref(i)))
+        return {f: getattr(i, f) for f, _ in N.sv_batch_info._fields_ if f != "pad"}

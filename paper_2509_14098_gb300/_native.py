@@ -56,6 +56,17 @@ class sv_timing(ctypes.Structure):
                 ("observable_launches", ctypes.c_uint32)]
 
 
+class sv_tune(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_uint8 * 41), ("k", ctypes.c_uint8 * 41)]
+
+
+class sv_batch_info(ctypes.Structure):
+    _fields_ = [("n_circuits", ctypes.c_uint32), ("n_programs", ctypes.c_uint32), ("n_resident", ctypes.c_uint32),
+                ("total_params", ctypes.c_uint32), ("workspace_bytes", ctypes.c_uint64),
+                ("smem_bytes", ctypes.c_uint32), ("grid", ctypes.c_uint32), ("graph", ctypes.c_uint32),
+                ("pad", ctypes.c_uint32), ("last_ms", ctypes.c_double)]
+
+
 assert ctypes.sizeof(sv_gate) == 40
 
 if not os.path.exists(LIB_PATH):
@@ -90,6 +101,12 @@ _SIGS = {
     "sv_grad": ([_vp, _vp, _dp, ctypes.POINTER(sv_observable), _dp, _dp], ctypes.c_int),
     "sv_timing_enable": ([_vp, ctypes.c_int], ctypes.c_int),
     "sv_timing_read": ([_vp, ctypes.POINTER(sv_timing), ctypes.c_int], ctypes.c_int),
+    "sv_batch_create": ([ctypes.POINTER(sv_circuit), ctypes.POINTER(sv_observable), _u32, ctypes.POINTER(sv_tune), _vp,
+                         ctypes.POINTER(_vp)], ctypes.c_int),
+    "sv_run_batch": ([_vp, _dp, _dp, _dp], ctypes.c_int),
+    "sv_autotune": ([_vp, _dp, ctypes.POINTER(sv_tune)], ctypes.c_int),
+    "sv_batch_info_get": ([_vp, ctypes.POINTER(sv_batch_info)], ctypes.c_int),
+    "sv_batch_destroy": ([_vp], ctypes.c_int),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(lib, _name)

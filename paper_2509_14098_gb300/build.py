@@ -33,8 +33,27 @@ def _run(cmd):
     return r.stdout
 
 
+# stage_inst.cu is compiled once per (precision, direction, register width): the
+# stage-sweep instantiations are the bulk of the device code, so they build in parallel.
+STAGE_INST = ([("float", 1, r) for r in range(1, 6)] + [("float", 2, r) for r in range(1, 5)] +
+              [("double", 1, r) for r in range(1, 5)] + [("double", 2, r) for r in range(1, 4)])
+
+
 def sources():
     return sorted(f for f in os.listdir(CSRC) if f.endswith((".cu", ".cpp")))
+
+
+def units():
+    """(source file, object name, extra defines) of every translation unit."""
+    out = []
+    for f in sources():
+        if f == "stage_inst.cu":
+            for real, nv, r in STAGE_INST:
+                out.append((f, f"stage_inst_{real}_nv{nv}_r{r}.o",
+                            [f"-DSVK_INST_REAL={real}", f"-DSVK_INST_NV={nv}", f"-DSVK_INST_R={r}"]))
+        else:
+            out.append((f, f + ".o", []))
+    return out
 
 
 def build(verbose=False, force=False):
@@ -47,9 +66,9 @@ def build(verbose=False, force=False):
     newest_header = max(os.path.getmtime(h) for h in headers)
     jobs = []
     objs = []
-    for f in sources():
+    for f, oname, defs in units():
         src = os.path.join(CSRC, f)
-        obj = os.path.join(BUILD, f + ".o")
+        obj = os.path.join(BUILD, oname)
         objs.append(obj)
         if (not force and os.path.exists(obj)
                 and os.path.getmtime(obj) >= max(os.path.getmtime(src), newest_header)):
@@ -57,13 +76,13 @@ def build(verbose=False, force=False):
         if f.endswith(".cu"):
             cmd = [nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3",
                    "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-                   "-Xptxas", "-v" if verbose else "-O3", "-c", src, "-o", obj] + inc
+                   "-Xptxas", "-v" if verbose else "-O3", "-c", src, "-o", obj] + defs + inc
         else:
             cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", "-Wno-unused-function",
                    "-I", os.path.join(cuda, "include"), "-c", src, "-o", obj] + inc
         jobs.append(cmd)
     if jobs:
-        with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
+        with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
             outs = list(ex.map(_run, jobs))
         if verbose:
             for o in outs:

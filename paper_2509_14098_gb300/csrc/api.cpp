@@ -11,6 +11,7 @@
 #include "gemm.h"
 #include "kernels.h"
 #include "planner.h"
+#include "internal.h"
 #include "sv.h"
 
 namespace {
@@ -74,6 +75,36 @@ size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 namespace svh {
 // error reporting for entry points defined in other translation units
 sv_status set_error(sv_status s, const char* msg) { return fail(s, msg); }
+
+std::string gates_from_circuit(const sv_circuit* c, std::vector<GateRec>* out) {
+    out->clear();
+    out->reserve(c->n_gates);
+    for (uint32_t i = 0; i < c->n_gates; ++i) {
+        const sv_gate& g = c->gates[i];
+        const std::string at = "gate " + std::to_string(i) + ": ";
+        GateRec r;
+        r.kind = g.kind;
+        if (g.kind < K_H || g.kind > K_LAST) return at + "unknown kind";
+        r.nq = kind_nq(g.kind);
+        if (g.nq != r.nq) return at + "wrong qubit count";
+        for (int k = 0; k < r.nq; ++k) {
+            if (g.q[k] >= c->n_qubits) return at + "qubit out of range";
+            r.q[k] = g.q[k];
+        }
+        if (r.nq == 1) r.q[1] = -1;
+        if (r.nq == 2 && r.q[0] == r.q[1]) return at + "repeated qubit";
+        r.param = g.param;
+        if (g.param >= 0) {
+            bool ok = g.kind == K_RX || g.kind == K_RY || g.kind == K_RZ || g.kind == K_P || g.kind == K_CP;
+            if (!ok || (uint32_t)g.param >= c->n_params) return at + "bad parameter slot";
+        } else if (g.param != -1) {
+            return at + "param must be -1 or a slot";
+        }
+        for (int k = 0; k < 3; ++k) r.angle[k] = g.angle[k];
+        out->push_back(r);
+    }
+    return "";
+}
 }  // namespace svh
 
 struct sv_plan_s {
@@ -497,37 +528,16 @@ static sv_status build_plan(const sv_circuit* c, uint32_t L, uint32_t n_fixed, s
     if (L < 1 || L > (uint32_t)svk::kMaxT) return fail(SV_ERR_ARG, "L must be in [1, 14]");
     if (c->n_gates == 0) return fail(SV_ERR_ARG, "empty circuit");
     if (c->n_gates > 32768) return fail(SV_ERR_ARG, "more than 32768 gates");
+    std::vector<svh::GateRec> gates;
+    std::string gerr = svh::gates_from_circuit(c, &gates);
+    if (!gerr.empty()) return fail(SV_ERR_ARG, gerr);
     sv_plan* p = new (std::nothrow) sv_plan();
     if (!p) return fail(SV_ERR_OOM, "host allocation failed");
     svh::Plan& P = p->plan;
     P.n = (int)c->n_qubits;
     P.n_params = (int)c->n_params;
     P.L = (int)L;
-    for (uint32_t i = 0; i < c->n_gates; ++i) {
-        const sv_gate& g = c->gates[i];
-        svh::GateRec r;
-        r.kind = g.kind;
-        if (g.kind < svh::K_H || g.kind > svh::K_LAST) { delete p; return fail(SV_ERR_ARG, "gate " + std::to_string(i) + ": unknown kind"); }
-        r.nq = svh::kind_nq(g.kind);
-        if (g.nq != r.nq) { delete p; return fail(SV_ERR_ARG, "gate " + std::to_string(i) + ": wrong qubit count"); }
-        for (int k = 0; k < r.nq; ++k) {
-            if (g.q[k] >= c->n_qubits) { delete p; return fail(SV_ERR_ARG, "gate " + std::to_string(i) + ": qubit out of range"); }
-            r.q[k] = g.q[k];
-        }
-        if (r.nq == 1) r.q[1] = -1;
-        if (r.nq == 2 && r.q[0] == r.q[1]) { delete p; return fail(SV_ERR_ARG, "gate " + std::to_string(i) + ": repeated qubit"); }
-        r.param = g.param;
-        if (g.param >= 0) {
-            bool ok = g.kind == svh::K_RX || g.kind == svh::K_RY || g.kind == svh::K_RZ ||
-                      g.kind == svh::K_P || g.kind == svh::K_CP;
-            if (!ok || (uint32_t)g.param >= c->n_params) { delete p; return fail(SV_ERR_ARG, "gate " + std::to_string(i) + ": bad parameter slot"); }
-        } else if (g.param != -1) {
-            delete p;
-            return fail(SV_ERR_ARG, "gate " + std::to_string(i) + ": param must be -1 or a slot");
-        }
-        for (int k = 0; k < 3; ++k) r.angle[k] = g.angle[k];
-        P.gates.push_back(r);
-    }
+    P.gates = std::move(gates);
     svh::relabel(P.n, P.gates, &P.phys, &P.final_map);
     const int nf = (int)std::min<uint32_t>(n_fixed, std::min<uint32_t>(L, c->n_qubits));
     P.n_fixed = nf;

@@ -581,4 +581,40 @@ __device__ __forceinline__ void tile_store(const C* tile, C* __restrict__ g, uin
     }
 }
 
+// Adjoint gradient terms: Im <lambda| G_j |psi> over the pairs of register bit j.
+template <typename Real>
+__device__ __forceinline__ Real im_conj_mul(typename CT<Real>::C l, typename CT<Real>::C p) {
+    return l.x * p.y - l.y * p.x;   // Im(conj(l) p)
+}
+template <typename Real>
+__device__ __forceinline__ Real re_conj_mul(typename CT<Real>::C l, typename CT<Real>::C p) {
+    return l.x * p.x + l.y * p.y;   // Re(conj(l) p)
+}
+
+template <typename Real> __device__ __forceinline__ typename CT<Real>::C to_c(typename RegT<Real>::type v);
+template <> __device__ __forceinline__ float2 to_c<float>(u64 v) { return unpack2(v); }
+template <> __device__ __forceinline__ double2 to_c<double>(double2 v) { return v; }
+
+template <typename Real, int R, int J>
+__device__ __forceinline__ Real grad_pairs(const typename RegT<Real>::type (&ps)[1 << R],
+                                           const typename RegT<Real>::type (&la)[1 << R], int type) {
+    Real acc = 0;
+#pragma unroll
+    for (int k = 0; k < (1 << R); ++k) {
+        if (k & (1 << J)) continue;
+        const int k1 = k | (1 << J);
+        const auto l0 = to_c<Real>(la[k]), l1 = to_c<Real>(la[k1]);
+        const auto p0 = to_c<Real>(ps[k]), p1 = to_c<Real>(ps[k1]);
+        if (type == OP_GRAD_X) {
+            acc += im_conj_mul<Real>(l0, p1) + im_conj_mul<Real>(l1, p0);
+        } else if (type == OP_GRAD_Y) {
+            // Y|0> = i|1>, Y|1> = -i|0>:  Im(conj(l0)(-i p1)) + Im(conj(l1)(i p0))
+            acc += -re_conj_mul<Real>(l0, p1) + re_conj_mul<Real>(l1, p0);
+        } else {
+            acc += im_conj_mul<Real>(l0, p0) - im_conj_mul<Real>(l1, p1);
+        }
+    }
+    return acc;
+}
+
 }  // namespace svk

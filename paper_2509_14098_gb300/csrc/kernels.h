@@ -76,4 +76,11 @@ size_t gemm_smem_bytes(const GemmStage& st);
 cudaError_t launch_gemm_stage(int prec, void* psi, const GemmStage* d_stage, const GemmStage& hst,
                               const uint8_t* d_ablob, int* d_status, cudaStream_t s);
 
+// batched circuits (batch.h): one persistent launch of `grid` CTAs
+struct BatchArgs;
+cudaError_t launch_batch(const BatchArgs& a, int grid, cudaStream_t s);
+// CTAs of the batch kernel that fit on one SM with `smem` bytes of dynamic shared memory
+cudaError_t batch_occupancy(size_t smem, int* per_sm);
+int batch_threads();
+
 }  // namespace svk

@@ -36,8 +36,8 @@ struct Pend {
 
 class Lowerer {
   public:
-    Lowerer(const Plan& p, const double* params, int eb, int rmax, bool bwd, Program* out)
-        : P_(p), params_(params), eb_(eb), rmax_(rmax), bwd_(bwd), out_(out) {}
+    Lowerer(const Plan& p, const double* params, int eb, int rmax, bool bwd, bool bind, Program* out)
+        : P_(p), params_(params), eb_(eb), rmax_(rmax), bwd_(bwd), bind_(bind), out_(out) {}
 
     std::string run();
 
@@ -45,7 +45,7 @@ class Lowerer {
     const Plan& P_;
     const double* params_;
     int eb_, rmax_;
-    bool bwd_;
+    bool bwd_, bind_;
     Program* out_;
     std::map<uint64_t, Pend> pending_;
     double gphase_ = 0.0;
@@ -55,7 +55,8 @@ class Lowerer {
     uint32_t slot_base_ = 0;
 
     double theta(const GateRec& g, int i = 0) const {
-        return g.param >= 0 ? params_[g.param] : g.angle[i];
+        if (g.param >= 0) return params_ ? params_[g.param] : 0.0;   // bind mode: formed on the device
+        return g.angle[i];
     }
     svk::Op& new_op(uint8_t type, int j) {
         out_->ops.emplace_back();
@@ -228,10 +229,12 @@ std::string Lowerer::gate(const GateRec& g, const PGate& pg) {
         case K_T: add_term(1ull << pg.p[0], s * M_PI / 4, -1); return "";
         case K_TDG: add_term(1ull << pg.p[0], -s * M_PI / 4, -1); return "";
         case K_P:
+            if (bind_ && g.param >= 0) return "a parametric P gate cannot be bound on the device";
             if (bwd_ && g.param >= 0) return "gradient of a P parameter is not supported";
             add_term(1ull << pg.p[0], s * theta(g), -1);
             return "";
         case K_RZ: {
+            if (bind_ && g.param >= 0) break;   // dense op with a device-formed matrix
             double t = theta(g);
             gphase_ += -s * t / 2;
             add_term(1ull << pg.p[0], s * t, bwd_ ? g.param : -1);
@@ -239,6 +242,7 @@ std::string Lowerer::gate(const GateRec& g, const PGate& pg) {
         }
         case K_CZ: add_term((1ull << pg.p[0]) | (1ull << pg.p[1]), s * M_PI, -1); return "";
         case K_CP:
+            if (bind_ && g.param >= 0) return "a parametric CP gate cannot be bound on the device";
             if (bwd_ && g.param >= 0) return "gradient of a CP parameter is not supported";
             add_term((1ull << pg.p[0]) | (1ull << pg.p[1]), s * theta(g), -1);
             return "";
@@ -251,7 +255,8 @@ std::string Lowerer::gate(const GateRec& g, const PGate& pg) {
     // The pending phase on t becomes the dense op's twiddle, except for a controlled
     // gate (the phase applies whatever the control is) and for a parametric gate of
     // the adjoint program (its gradient op must see the phase un-applied first).
-    const bool fuse = !kind_is_controlled(g.kind) && !(bwd_ && g.param >= 0);
+    // A bound op's matrix is replaced on the device, so it takes no twiddle either.
+    const bool fuse = !kind_is_controlled(g.kind) && !((bwd_ || bind_) && g.param >= 0);
     double tw_angle = 0.0;
     std::vector<svk::Term> tw_terms;
     flush_bit(t, fuse, &tw_angle, &tw_terms);
@@ -277,6 +282,11 @@ std::string Lowerer::gate(const GateRec& g, const PGate& pg) {
             type = svk::OP_UR;
             break;
         }
+        case K_RZ: {   // bind mode only: diag(exp(-i t/2), exp(i t/2))
+            double c = std::cos(theta(g) / 2), sn = std::sin(theta(g) / 2);
+            set_m(m, c, -sn, 0, 0, 0, 0, c, sn);
+            break;
+        }
         case K_U3: {
             double th = g.angle[0], ph = g.angle[1], la = g.angle[2];
             double c = std::cos(th / 2), sn = std::sin(th / 2);
@@ -289,13 +299,19 @@ std::string Lowerer::gate(const GateRec& g, const PGate& pg) {
     if (bwd_) {
         dagger(m);
         if (g.param >= 0) {
-            if (g.kind != K_RX && g.kind != K_RY) return "gradient of this parameter kind is not supported";
-            svk::Op& go = new_op(g.kind == K_RX ? svk::OP_GRAD_X : svk::OP_GRAD_Y, jt);
+            if (g.kind != K_RX && g.kind != K_RY && g.kind != K_RZ)
+                return "gradient of this parameter kind is not supported";
+            svk::Op& go = new_op(g.kind == K_RX ? svk::OP_GRAD_X : g.kind == K_RY ? svk::OP_GRAD_Y : svk::OP_GRAD_Z, jt);
             go.slot = (uint32_t)new_slot(g.param);
         }
     }
     svk::Op& o = new_op(type, jt);
     std::memcpy(o.m, m, sizeof(m));
+    if (bind_ && g.param >= 0) {
+        o.bparam1 = (uint32_t)g.param + 1;
+        o.bkind = (uint8_t)((g.kind == K_RX ? svk::BK_RX : g.kind == K_RY ? svk::BK_RY : svk::BK_RZ) |
+                            (bwd_ ? svk::BK_DAGGER : 0));
+    }
     if (tw_angle != 0.0 || !tw_terms.empty()) {
         o.has_tw = 1;
         o.tw_angle = tw_angle;
@@ -463,6 +479,11 @@ static void pack_real(const Program& p, int n, Packed* out) {
                 d.ctrl_fix = o.ctrl_fix;
                 d.slot = o.slot;
                 for (int i = 0; i < 8; ++i) d.m[i] = (Real)o.m[i];
+                if (o.bparam1) {
+                    d.flags |= svk::F_BIND;
+                    d.term_off = o.bparam1 - 1;
+                    d.u = o.bkind;
+                }
                 const bool dense_tw = o.type <= svk::OP_X && o.has_tw;
                 const bool phase = ((o.type == svk::OP_PHASE0 || o.type == svk::OP_PHASE1) && o.n_terms > 0) || dense_tw;
                 if (dense_tw) d.flags |= svk::F_TW;
@@ -549,6 +570,10 @@ static void pack_real(const Program& p, int n, Packed* out) {
     out->term_off = put(terms.data(), terms.size() * sizeof(DTerm));
     out->slot_off = put(slots.data(), slots.size() * sizeof(svk::PhaseSlot<Real>));
     out->wthr_off = out->slot_off;
+    out->n_groups = groups.size();
+    out->n_ops = ops.size();
+    out->n_terms = terms.size();
+    out->n_slots = slots.size();
     out->stages = stages;
 }
 
@@ -559,9 +584,9 @@ std::string pack(const Program& p, int n, int elem_bytes, Packed* out) {
 }
 
 std::string lower(const Plan& plan, const double* params, int elem_bytes, int rmax, bool backward,
-                  Program* out) {
-    if (plan.n_params > 0 && params == nullptr) return "circuit has parameters but params is NULL";
-    Lowerer L(plan, params, elem_bytes, rmax, backward, out);
+                  Program* out, bool bind) {
+    if (plan.n_params > 0 && params == nullptr && !bind) return "circuit has parameters but params is NULL";
+    Lowerer L(plan, params, elem_bytes, rmax, backward, bind, out);
     return L.run();
 }
 

@@ -31,7 +31,7 @@ static inline int popc64(uint64_t x) { return __builtin_popcountll(x); }
 
 static uint64_t need_mask(const PGate& g, bool strict) {
     if (g.kind == K_SWAP) return 0;
-    if (strict) {
+    if (strict || g.bound) {
         uint64_t m = 0;
         for (int i = 0; i < g.nq; ++i) m |= 1ull << g.p[i];
         return m;

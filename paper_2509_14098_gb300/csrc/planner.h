@@ -34,6 +34,7 @@ struct PGate {
     int kind;
     int nq;
     int p[2];
+    bool bound = false;   // parametric RZ lowered as a dense op (bind mode): needs its qubit
 };
 
 struct Partition {
@@ -88,6 +89,7 @@ struct Program {
 struct Packed {
     std::vector<uint8_t> blob;
     size_t stage_off = 0, group_off = 0, op_off = 0, term_off = 0, slot_off = 0, wthr_off = 0;
+    size_t n_groups = 0, n_ops = 0, n_terms = 0, n_slots = 0;   // element counts of the sections
     std::vector<svk::Stage> stages;   // with op/phase offsets filled in
 };
 std::string pack(const Program& p, int n, int elem_bytes, Packed* out);
@@ -95,7 +97,12 @@ std::string pack(const Program& p, int n, int elem_bytes, Packed* out);
 // Lower a plan with bound parameters.  rmax: register bits per thread.
 // backward: un-apply the stages in reverse (conjugate-transposed gates) and emit
 // gradient ops for parametric RX / RY / RZ gates.  Returns "" or an error.
+// bind: parametric RX / RY / RZ become dense ops flagged F_BIND (no twiddle fused, RZ
+// kept on a register bit, which the plan's partition must guarantee via
+// PGate::bound), so the program's structure does not depend on the parameters;
+// params may then be NULL (the kernel forms those matrices).  Parametric P / CP are
+// rejected in this mode.
 std::string lower(const Plan& plan, const double* params, int elem_bytes, int rmax, bool backward,
-                  Program* out);
+                  Program* out, bool bind = false);
 
 }  // namespace svh

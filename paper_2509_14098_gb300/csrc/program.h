@@ -56,9 +56,10 @@ struct Op {
     uint32_t term_off;      // first Term of this op
     uint32_t n_terms;
     uint32_t slot;          // gradient slot (GRAD ops): index into the stage's slot list
-    uint32_t pad1;
+    uint32_t bparam1;       // bound dense op: parameter index + 1 (0 = matrix fixed at lowering)
     double m[8];            // row-major 2x2 (re, im) pairs; PHASE ops use m[0], m[1]
     double tw_angle;        // dense op twiddle constant (has_tw)
+    uint8_t bkind;          // bound dense op: BK_RX / BK_RY / BK_RZ, | BK_DAGGER for the adjoint
 };
 
 struct Term {               // phase angle added when every bit of mask is set
@@ -71,7 +72,13 @@ enum OpFlag : uint8_t {
     F_TERMS = 2,            // PHASE op evaluated from its DevTerm list on the fixed index
     F_TW = 4,               // dense op preceded by a phase on its target bit (F_SLOT / F_TERMS
                             // give the angle; a dense op's constant is a mask-0 term)
+    F_BIND = 8,             // dense op whose matrix the kernel forms from a parameter:
+                            // term_off = parameter index, u = BK_* kind (| BK_DAGGER)
 };
+
+// Parametric rotations whose matrix is formed on the device (batched programs are
+// lowered once and replayed with new parameters).
+enum BindKind : uint8_t { BK_RX = 1, BK_RY = 2, BK_RZ = 3, BK_DAGGER = 4 };
 
 // Device op: 64 bytes (complex64 kernels) / 96 bytes (complex128 kernels).  The
 // kernels stage a stage's ops in shared memory once per CTA.
