@@ -42,7 +42,11 @@ def parse():
     ap.add_argument("--n", type=int, default=N_QUBITS)
     ap.add_argument("--grad-n", type=int, default=28)
     ap.add_argument("--grad-L", type=int, default=12)
-    ap.add_argument("--no-extras", action="store_true", help="skip e2e, grad ratio and CPU baseline")
+    ap.add_argument("--no-extras", action="store_true", help="skip e2e, grad ratio, batch and CPU baseline")
+    ap.add_argument("--part", default="all", choices=["all", "batch"],
+                    help="batch: only the batched-circuit section (for profiling)")
+    ap.add_argument("--batch-count", type=int, default=2048)
+    ap.add_argument("--no-autotune", action="store_true", help="batch section with the default (L, k) table")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--sample-seconds", type=float, default=12.0, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -150,7 +154,7 @@ def peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("stage_kernels.cu", "kdev.cuh", "program.h", "lower.cpp"):
+    for f in ("stage_impl.cuh", "stage_layout.cuh", "kdev.cuh", "program.h", "lower.cpp"):
         h.update(open(os.path.join(ROOT, "paper_2509_14098_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -219,6 +223,71 @@ def main_reference(args):
     }))
 
 
+def batch_section(args, steps):
+    """Batched form: count HEA circuits (n uniform in [10, 20], 6 layers, 12 n
+    parameters each, sum ZZ open chain), E and the adjoint gradient of every circuit
+    per evaluation (one graph launch), after the autotuner; against looping the plain
+    path (sv_grad per circuit, partitions cached) over the same batch."""
+    import numpy as np
+    import torch
+
+    import circuits as C
+    import paper_2509_14098_gb300 as sv
+    spec = C.batch_spec(args.batch_count, seed=5, n_lo=10, n_hi=20, layers=6)
+    circs = [c for c, _ in spec]
+    obs = [C.zz_chain(c.n_qubits) for c in circs]
+    params = np.concatenate([p for _, p in spec])
+    t0 = time.perf_counter()
+    b = sv.Batch(circs, obs)
+    build_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    table = {} if args.no_autotune else b.autotune(params)
+    tune_s = time.perf_counter() - t0
+    for _ in range(2):
+        e, g = b.run(params)
+    dev_ms, wall_ms = [], []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        e, g = b.run(params)
+        wall_ms.append((time.perf_counter() - t0) * 1e3)
+        dev_ms.append(b.info()["last_ms"])
+    info = b.info()
+    out = {"workload": f"{len(circs)} HEA circuits, n ~ U[10, 20], 6 layers, sum ZZ, seed 5",
+           "circuits_per_s": len(circs) / (statistics.median(wall_ms) * 1e-3),
+           "ms_per_batch_device": statistics.median(dev_ms), "ms_per_batch_wall": statistics.median(wall_ms),
+           "build_s": build_s, "autotune_s": tune_s,
+           "tune": {str(k): list(v) for k, v in sorted(table.items())},
+           "programs": info["n_programs"], "resident_circuits": info["n_resident"],
+           "workspace_gb": info["workspace_bytes"] / 1e9, "smem_bytes": info["smem_bytes"], "grid": info["grid"],
+           "graph": bool(info["graph"]), "launches_per_batch": 1}
+    b.close()
+    if args.part == "all":
+        plans = [sv.Plan(c, min(12, c.n_qubits)) for c in circs]
+        offs = np.concatenate([[0], np.cumsum([c.n_params for c in circs])])
+        sts = {}
+        for i in range(min(16, len(circs))):   # warm-up: one handle per width
+            st = sts.setdefault(circs[i].n_qubits, sv.StateVector(circs[i].n_qubits))
+            st.reset()
+            st.grad(plans[i], params[offs[i]:offs[i + 1]], obs[i])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e_loop = np.zeros(len(circs))
+        for i, c in enumerate(circs):
+            st = sts.get(c.n_qubits)
+            if st is None:
+                st = sts[c.n_qubits] = sv.StateVector(c.n_qubits)
+            st.reset()
+            e_loop[i], _ = st.grad(plans[i], params[offs[i]:offs[i + 1]], obs[i])
+        torch.cuda.synchronize()
+        loop_s = time.perf_counter() - t0
+        for st in sts.values():
+            st.close()
+        out["loop_circuits_per_s"] = len(circs) / loop_s
+        out["speedup_vs_loop"] = out["circuits_per_s"] / out["loop_circuits_per_s"]
+        out["max_abs_dE_vs_loop"] = float(np.max(np.abs(e_loop - e)))
+    return out
+
+
 def main_ours(args):
     import ctypes
 
@@ -234,6 +303,11 @@ def main_ours(args):
     world, rank, local, pg = dist_setup(args)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.part == "batch":
+        r = batch_section(args, args.steps)
+        if rank == 0:
+            print(json.dumps({"part": "batch", "batch": r}))
+        return
     n, L = args.n, args.L
     circ = C.qft_roundtrip(n)
     gen = torch.Generator(device=dev)
@@ -295,9 +369,13 @@ def main_ours(args):
 
     extras = {}
     if rank == 0 and not args.no_extras:
-        # parity check of the timed result: QFT then inverse QFT is the identity
+        # parity check: one QFT then inverse QFT (the identity) from a fresh copy of the input
+        psi.copy_(ref_copy)
+        st.run(sv.Plan(circ, L))
+        st.synchronize()
         err = float(torch.linalg.vector_norm(psi - ref_copy).item())
         extras["roundtrip_error_l2"] = err
+        extras["roundtrip_error_tolerance"] = 2e-5
         del ref_copy
         # end to end through the C ABI with host buffers (pinned)
         host_in = torch.empty(1 << n, dtype=torch.complex64, pin_memory=True)
@@ -361,6 +439,7 @@ def main_ours(args):
             "definition": "(time(sv_grad) - time(sv_run)) / time(sv_run): lambda formation + backward over forward",
         }
         g.close()
+        extras["batch"] = batch_section(args, 3)
     cpu = None
     if rank == 0 and world == 1 and not args.no_extras:
         cpu = run_cpu_sample(args.sample_seconds)
