@@ -142,6 +142,8 @@ __device__ __noinline__ void run_groups(float2* cur0, float2* cur1, const Stage*
     OpCtx<float> x;
     x.slots = ssl;
     x.ang = sang;
+    x.tang = nullptr;   // virtual threads: the thread-bit terms are summed per op
+    x.nthr = nvt;
     x.TR = TR;
     x.terms = terms;
     for (uint32_t g = 0; g < S->n_groups; ++g) {

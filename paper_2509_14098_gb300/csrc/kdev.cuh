@@ -180,7 +180,9 @@ struct OpCtx {
     uint64_t fix;                                   // thread's fixed physical index
     const PhaseSlot<Real>* slots;                   // shared memory (thread-bit coefficients)
     const typename AngT<Real>::type* ang;           // shared memory: per-tile slot angles
-    uint32_t tid;
+    const typename AngT<Real>::type* tang;          // shared memory [slot][thread]: sum of the slot's
+                                                    // thread-bit terms for each thread, or nullptr
+    uint32_t tid, nthr;
     int TR;
     const DevTerm<Real>* __restrict__ terms;
 };
@@ -189,11 +191,15 @@ template <typename Real>
 __device__ __forceinline__ typename CT<Real>::C phase_factor(const DevOp<Real>& o, const OpCtx<Real>& x) {
     using C = typename CT<Real>::C;
     if (o.flags & F_SLOT) {
-        const PhaseSlot<Real>& ps = x.slots[o.slot];
         typename AngT<Real>::type ang = x.ang[o.slot];
-        if (ps.has_thr)
-            for (int i = 0; i < x.TR; ++i)
-                if ((x.tid >> i) & 1) ang += ps.J[i];
+        if (x.tang) {
+            ang += x.tang[o.slot * x.nthr + x.tid];
+        } else {
+            const PhaseSlot<Real>& ps = x.slots[o.slot];
+            if (ps.has_thr)
+                for (int i = 0; i < x.TR; ++i)
+                    if ((x.tid >> i) & 1) ang += ps.J[i];
+        }
         return expi(ang);
     }
     if (o.flags & F_TW) return expi(term_angle<Real>(x.terms, o.term_off, o.n_terms, x.fix));

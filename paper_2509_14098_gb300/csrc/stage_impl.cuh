@@ -23,6 +23,18 @@
 #include "kernels.h"
 #include "stage_layout.cuh"
 
+// Occupancy of <= 256-thread launches.  The sweep is issue-latency bound, so the
+// forward kernel trades registers for resident warps (64 registers, single-buffered
+// tiles: measured 10 % faster on the QFT30 stages than 128 registers with
+// double-buffered tiles); the adjoint kernel, which holds psi and lambda in
+// registers, keeps 128 registers and double buffering.
+#ifndef SVK_MINB_FWD
+#define SVK_MINB_FWD 4
+#endif
+#ifndef SVK_MINB_BWD
+#define SVK_MINB_BWD 2
+#endif
+
 namespace svk {
 
 // ---------------------------------------------------------------------------
@@ -36,7 +48,7 @@ namespace svk {
 // partial sums accumulate per CTA in FP64 (per warp, fixed order) and are written once.
 // ---------------------------------------------------------------------------
 template <typename Real, int R, int MAXT, int NV, int NB>
-__global__ void __launch_bounds__(MAXT, (MAXT >= 512 ? 1 : 2))
+__global__ void __launch_bounds__(MAXT, (MAXT >= 512 ? 1 : (NV == 1 ? SVK_MINB_FWD : SVK_MINB_BWD)))
     k_stage(typename CT<Real>::C* __restrict__ psi, typename CT<Real>::C* __restrict__ lam,
             const Stage* __restrict__ stp, const Group* __restrict__ groups,
             const DevOp<Real>* __restrict__ gops, const DevTerm<Real>* __restrict__ terms,
@@ -66,6 +78,8 @@ __global__ void __launch_bounds__(MAXT, (MAXT >= 512 ? 1 : 2))
     uint32_t* gsoff = reinterpret_cast<uint32_t*>(smem_raw + Ly.gsoff);
     uint32_t* chs = reinterpret_cast<uint32_t*>(smem_raw + Ly.chs);
     float* gsm = reinterpret_cast<float*>(smem_raw + Ly.gsm);
+    Ang* tang = reinterpret_cast<Ang*>(smem_raw + Ly.tang);
+    const bool ttab = angle_table_fits(st.n_phase, nthr, sizeof(Ang));
     const bool gtab = group_table_fits(ng, nthr);
     const uint64_t ntiles = 1ull << st.n_glob;
     C* vec[2] = {psi, lam};
@@ -120,12 +134,22 @@ __global__ void __launch_bounds__(MAXT, (MAXT >= 512 ? 1 : 2))
         }
     if (NV == 2)
         for (uint32_t i = tid; i < nslots * nw; i += nthr) gsm[i] = 0.f;
+    if (ttab)   // each thread's own column: the thread-bit part of every phase slot
+        for (uint32_t p = 0; p < st.n_phase; ++p) {
+            const PhaseSlot<Real>& ps = slots[st.phase_off + p];
+            Ang a = 0;
+            for (int i = 0; i < TR; ++i)
+                if ((tid >> i) & 1) a += ps.J[i];
+            tang[p * nthr + tid] = a;
+        }
     __syncthreads();
 
     OpCtx<Real> x;
     x.slots = ssl;
     x.ang = sang;
     x.tid = tid;
+    x.nthr = nthr;
+    x.tang = ttab ? tang : nullptr;
     x.TR = TR;
     x.terms = terms;
     const uint32_t wmask = nthr >= 32 ? 0xffffffffu : ((1u << nthr) - 1u);
@@ -258,17 +282,21 @@ static cudaError_t try_launch(const StageLaunch& L, const Stage& hst, cudaStream
     return cudaGetLastError();
 }
 
-// double-buffered tiles while that still leaves >= 2 CTAs per SM, else single-buffered
+// adjoint: double-buffered tiles while that still leaves >= 2 CTAs per SM, else single-
+// buffered; forward: single-buffered (occupancy hides the loads, see SVK_MINB_FWD)
 template <typename Real, int R, int MAXT, int NV>
 static cudaError_t launch_RT(const StageLaunch& L, const Stage& hst, cudaStream_t s, uint32_t* grid_out) {
     bool ok = false;
-    cudaError_t e = try_launch<Real, R, MAXT, NV, 2>(L, hst, s, grid_out, 2, &ok);
-    if (e != cudaSuccess || ok) return e;
+    cudaError_t e = cudaSuccess;
+    if constexpr (NV == 2) {
+        e = try_launch<Real, R, MAXT, NV, 2>(L, hst, s, grid_out, 2, &ok);
+        if (e != cudaSuccess || ok) return e;
+    }
     e = try_launch<Real, R, MAXT, NV, 1>(L, hst, s, grid_out, 1, &ok);
     if (e != cudaSuccess) return e;
     return ok ? cudaSuccess : cudaErrorInvalidConfiguration;
 }
-// 256-thread bound (128 registers, 2 CTAs) unless the tile needs 512 threads
+// 256-thread bound unless the tile needs 512 threads
 template <typename Real, int R, int NV>
 cudaError_t launch_R(const StageLaunch& L, const Stage& hst, cudaStream_t s, uint32_t* grid_out) {
     if ((hst.T - R) <= 8) return launch_RT<Real, R, 256, NV>(L, hst, s, grid_out);

@@ -12,12 +12,16 @@ namespace svk {
 __host__ __device__ __forceinline__ bool group_table_fits(uint32_t n_groups, uint32_t nthr) {
     return (size_t)n_groups * nthr * 12 <= 24 * 1024;
 }
+// per-(phase slot, thread) thread-bit angle table, likewise
+__host__ __device__ __forceinline__ bool angle_table_fits(uint32_t n_phase, uint32_t nthr, size_t angb) {
+    return (size_t)n_phase * nthr * angb <= 16 * 1024;
+}
 
 // ---------------------------------------------------------------------------
 // shared-memory layout of k_stage (identical on host and device)
 // ---------------------------------------------------------------------------
 struct SmemLayout {
-    size_t groups, ops, slots, ang, gfix, chp, gsoff, chs, gsm, total;
+    size_t groups, ops, slots, ang, gfix, chp, gsoff, chs, gsm, tang, total;
 };
 __host__ __device__ __forceinline__ size_t align_up(size_t x, size_t a) { return (x + a - 1) & ~(a - 1); }
 __host__ __device__ __forceinline__ SmemLayout smem_layout(int elem_bytes, int nv, int nb, uint32_t T,
@@ -37,7 +41,8 @@ __host__ __device__ __forceinline__ SmemLayout smem_layout(int elem_bytes, int n
     L.chp = o;     o += (size_t)nch * 8;
     L.gsoff = o;   o += (size_t)ngt * nthr * 4;
     L.chs = o;     o = align_up(o + (size_t)nch * 4, 16);
-    L.gsm = o;     o += (nv == 2) ? (size_t)n_slots * ((nthr + 31) / 32) * sizeof(float) : 0;
+    L.gsm = o;     o = align_up(o + ((nv == 2) ? (size_t)n_slots * ((nthr + 31) / 32) * sizeof(float) : 0), 16);
+    L.tang = o;    o += angle_table_fits(n_phase, nthr, angb) ? (size_t)n_phase * nthr * angb : 0;
     L.total = o;
     return L;
 }
