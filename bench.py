@@ -43,8 +43,12 @@ def parse():
     ap.add_argument("--grad-n", type=int, default=28)
     ap.add_argument("--grad-L", type=int, default=12)
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, grad ratio, batch and CPU baseline")
-    ap.add_argument("--part", default="all", choices=["all", "batch"],
-                    help="batch: only the batched-circuit section (for profiling)")
+    ap.add_argument("--part", default="all", choices=["all", "batch", "gemm"],
+                    help="batch / gemm: only that section (for profiling)")
+    ap.add_argument("--gemm-n", type=int, default=32)
+    ap.add_argument("--gemm-k", default="5,6,7")
+    ap.add_argument("--gemm-prec", default="1,2", help="1 = TF32x3, 2 = BF16x3")
+    ap.add_argument("--no-c128", action="store_true", help="gemm section without the complex128 reference")
     ap.add_argument("--batch-count", type=int, default=2048)
     ap.add_argument("--no-autotune", action="store_true", help="batch section with the default (L, k) table")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
@@ -288,6 +292,61 @@ def batch_section(args, steps):
     return out
 
 
+def gemm_section(args):
+    """Precision / tensor-core stages: brickwork of depth 24 (U3 with uniform angles
+    plus CZ, seed 3) on gemm_n qubits from a random complex64 state; each (k, precision)
+    runs the partition without exemptions as tcgen05 GEMM stages.  Reported: time per
+    circuit, stages (= HBM passes), per-stage time and algorithmic GB/s, and the error
+    against the complex128 CUDA-core run of the same circuit and input."""
+    import torch
+
+    import circuits as C
+    import paper_2509_14098_gb300 as sv
+    n = args.gemm_n
+    circ = C.brickwork(n, 24, 3)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(3)
+    psi0 = torch.randn(1 << n, dtype=torch.complex64, device="cuda", generator=gen)
+    psi0 /= torch.linalg.vector_norm(psi0)
+    ref = None
+    if not args.no_c128:
+        r = psi0.to(torch.complex128)
+        st = sv.StateVector(n, sv.SV_C128, tensor=r)
+        st.run(sv.Plan(circ, 11))
+        st.synchronize()
+        st.close()
+        ref = r.to(torch.complex64)   # rounding to complex64 adds <= 6e-8 relative per amplitude
+        del r
+        torch.cuda.empty_cache()
+    psi = torch.empty_like(psi0)
+    st = sv.StateVector(n, tensor=psi)
+    bytes_pass = 2.0 * (1 << n) * 8
+    rows = []
+    cfgs = [(int(k), int(p)) for p in args.gemm_prec.split(",") for k in args.gemm_k.split(",")] + [(11, 0)]
+    for k, prec in cfgs:
+        plan = sv.Plan(circ, k, gemm=(prec != 0))
+        psi.copy_(psi0)
+        st.run(plan, None, prec)              # warm-up (and the result compared below)
+        st.synchronize()
+        err = float(torch.linalg.vector_norm(psi - ref).item()) if ref is not None else None
+        psi.copy_(psi0)
+        st.timing(True)
+        st.timing(reset=True)
+        t0 = time.perf_counter()
+        st.run(plan, None, prec)
+        st.synchronize()
+        wall = (time.perf_counter() - t0) * 1e3
+        tm = st.timing(reset=True)
+        st.timing(False)
+        per = tm["stage_ms"] / max(1, tm["stage_launches"])
+        rows.append({"k": k, "prec": {0: "cudacore_c64_L11", 1: "tf32x3", 2: "bf16x3"}[prec],
+                     "stages": tm["stage_launches"], "ms_circuit": wall, "ms_per_stage": per,
+                     "gbs_per_stage": bytes_pass / (per * 1e-3) / 1e9, "err_l2_vs_c128": err})
+    st.close()
+    return {"workload": f"brickwork n={n}, depth 24, seed 3, random complex64 input", "runs": rows,
+            "reference": "complex128 CUDA-core run (L=11)" if ref is not None else None}
+
+
 def main_ours(args):
     import ctypes
 
@@ -307,6 +366,11 @@ def main_ours(args):
         r = batch_section(args, args.steps)
         if rank == 0:
             print(json.dumps({"part": "batch", "batch": r}))
+        return
+    if args.part == "gemm":
+        r = gemm_section(args)
+        if rank == 0:
+            print(json.dumps({"part": "gemm", "gemm": r}))
         return
     n, L = args.n, args.L
     circ = C.qft_roundtrip(n)
@@ -440,6 +504,8 @@ def main_ours(args):
         }
         g.close()
         extras["batch"] = batch_section(args, 3)
+        torch.cuda.empty_cache()
+        extras["tensor_core_stages"] = gemm_section(args)
     cpu = None
     if rank == 0 and world == 1 and not args.no_extras:
         cpu = run_cpu_sample(args.sample_seconds)

@@ -654,14 +654,14 @@ static sv_status run_gemm(sv_handle h, const sv_plan* plan, const double* params
     if (!err.empty()) return fail(SV_ERR_UNSUPPORTED, err);
     const size_t sb = gp.stages.size() * sizeof(svk::GemmStage);
     const size_t aoff = align16(sb);
-    const size_t total = aoff + gp.ablob.size();
+    const size_t total = aoff + gp.ublob.size();
     for (auto& st : gp.stages)
         if (svk::gemm_smem_bytes(st) > 227 * 1024) return fail(SV_ERR_UNSUPPORTED, "tensor-core stage too wide");
     SV_CUDA(h->gemm.ensure(total));
     SV_CUDA(h->status.ensure(sizeof(int)));
     h->gemm_host.assign(total, 0);
     std::memcpy(h->gemm_host.data(), gp.stages.data(), sb);
-    std::memcpy(h->gemm_host.data() + aoff, gp.ablob.data(), gp.ablob.size());
+    std::memcpy(h->gemm_host.data() + aoff, gp.ublob.data(), gp.ublob.size());
     SV_CUDA(cudaMemcpyAsync(h->gemm.p, h->gemm_host.data(), total, cudaMemcpyHostToDevice, h->stream));
     SV_CUDA(cudaMemsetAsync(h->status.p, 0, sizeof(int), h->stream));
     for (size_t i = 0; i < gp.stages.size(); ++i) {

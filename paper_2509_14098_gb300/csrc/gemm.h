@@ -9,25 +9,37 @@
 
 namespace svk {
 
-// One fused stage.  A tile = 2^ncol_bits columns (fixed global bits); a column = the
-// 2^keff amplitudes whose local bits vary, i.e. 2^(keff+1) interleaved floats (the K
-// dimension).  K is streamed in chunks of 32 floats = 16 amplitudes: chunk c fixes
-// the local bits 4..keff-1 to c; inside a chunk the 4 lowest local bits and the column
-// bits vary ("var" bits, ascending physical position).
+// One fused stage applied as D = X * Ut^T per tile:
+//   X  (the MMA's A operand, M = 128): 128 state columns of the tile, one per row; a
+//      column is the 2^keff amplitudes whose local bits vary, i.e. K = 2^(keff+1)
+//      interleaved (re, im) floats;
+//   Ut (the B operand, N = 2^(keff+1) rows): the real embedding of the stage's fused
+//      unitary, row n = output float n of a column;
+//   D  (M x N FP32 in tensor memory): the updated columns.
+// A tile fixes the global bits; its columns are indexed by the 7 column bits (the
+// lowest non-local bits).  K is processed in chunks of 128 bytes per row (32 TF32 or
+// 64 BF16 elements = 2^camp_bits amplitudes): chunk c fixes the local bits above
+// camp_bits to c.  Both operands use the 128-byte-swizzled K-major layout (rows of
+// 128 bytes, 8-row groups of 1024 bytes, 16-byte units XORed with the row index).
 struct GemmStage {
     uint32_t keff;          // local qubits (6 or 7)
-    uint32_t nacc;          // 128-row accumulators = 2^(keff+1) / 128
-    uint32_t nchunk;        // K chunks = 2^(keff+1) / 32
-    uint32_t ncol_bits;     // log2(columns per tile), 4..7
+    uint32_t N;             // 2^(keff+1)
+    uint32_t nchunk;        // K chunks
+    uint32_t camp_bits;     // log2 amplitudes per K chunk (4 TF32, 5 BF16)
     uint32_t n_glob;        // tile-index bits
-    uint32_t nvar;          // 4 + ncol_bits
-    uint32_t a_chunk_bytes; // bytes of one A chunk (hi then lo)
+    uint32_t resident;      // 1: every B chunk stays in shared memory for the whole launch
+    uint32_t b_chunk_bytes; // one B chunk: hi block then lo block (N x 128 bytes each)
+    uint32_t nvar;          // camp_bits + ncol_bits chunk-varying bits
+    uint32_t ncol_bits;     // log2 columns per tile: 7, fewer only for states with n < keff + 7
+                            // (the MMA rows beyond the columns are zero and never stored)
     uint32_t pad;
-    uint64_t a_off;         // byte offset of this stage's A chunks in the A blob
+    uint64_t b_off;         // byte offset of this stage's B chunks in the blob
     uint8_t glob_pos[kMaxQ];
-    uint8_t var_role[12];   // 0..3: bit j of the chunk's amplitude index; 8 + c: column bit c
-    uint64_t var_phys[12];  // 1 << physical position
-    uint64_t hi_local[4];   // physical value of local bits 4..keff-1 (chunk index bits)
+    uint8_t local_pos[8];   // physical positions of the local bits, ascending
+    uint8_t col_pos[8];     // physical positions of the column bits, ascending
+    uint8_t var_role[12];   // chunk-varying bits in ascending physical order: 0..4 = bit of
+                            // the amplitude index inside the chunk, 8 + c = column bit c
+    uint8_t var_pos[12];    // their physical positions
 };
 
 }  // namespace svk
@@ -36,7 +48,7 @@ namespace svh {
 struct Plan;
 struct GemmProgram {
     std::vector<svk::GemmStage> stages;
-    std::vector<uint8_t> ablob;
+    std::vector<uint8_t> ublob;   // B chunks of every stage (1024-byte aligned)
     bool identity_map = true;
 };
 // prec: 1 = TF32x3, 2 = BF16x3.  Returns "" or an error.

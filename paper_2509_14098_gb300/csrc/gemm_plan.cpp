@@ -7,7 +7,7 @@
 // interleaved (re, im) floats: Ut[2i+a][2j+b] = Re U_ij if a == b, Im U_ij if (a, b) =
 // (1, 0), -Im U_ij if (a, b) = (0, 1).  Ut is split as Ut ~ hi + lo with both halves
 // rounded to nearest (TF32: hi = rn(x), lo = rn(x - hi); BF16 likewise) and stored per
-// K-chunk of 32 columns in the tensor cores' canonical no-swizzle K-major layout.
+// K chunk of 128 bytes per row in the tensor cores' 128-byte-swizzled K-major layout.
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -86,48 +86,55 @@ static float from_bf16(uint16_t h) {
     return x;
 }
 
+// 128-byte-swizzled K-major position of byte b of row r inside one operand block
+static size_t sw128(uint32_t r, uint32_t b) {
+    return (size_t)(r >> 3) * 1024 + (r & 7) * 128 + ((((b >> 4) ^ (r & 7)) & 7) << 4) + (b & 15);
+}
+
 std::string plan_gemm(const Plan& P, const double* params, int prec, GemmProgram* out) {
     out->stages.clear();
-    out->ablob.clear();
+    out->ublob.clear();
     const int n = P.n;
+    const bool tf32 = prec == 1;
     for (size_t s = 0; s < P.top.local.size(); ++s) {
         uint64_t local = P.top.local[s];
         int k = __builtin_popcountll(local);
-        // widen to at least 6 local qubits (an M = 128 accumulator) with identity qubits
+        // widen to at least 6 local qubits (N = 128) with identity qubits
         for (int b = 0; b < n && k < 6; ++b)
             if (!((local >> b) & 1)) { local |= 1ull << b; ++k; }
         if (k < 6 || k > 7) return "tensor-core stages need 6 or 7 local qubits (k in 5..7, n >= 6)";
-        if (n - k < 4) return "tensor-core stages need at least 16 columns (n >= k + 4)";
+        if (n - k < 1) return "tensor-core stages need at least one column bit (n > k)";
         svk::GemmStage st;
         std::memset(&st, 0, sizeof(st));
         int lp[8], nl = 0;
         for (int b = 0; b < n; ++b)
             if ((local >> b) & 1) lp[nl++] = b;
         st.keff = (uint32_t)k;
-        st.nacc = (uint32_t)((2u << k) / 128);
-        st.nchunk = (uint32_t)((2u << k) / 32);
+        st.N = 2u << k;
+        st.camp_bits = tf32 ? 4u : 5u;
+        st.nchunk = (uint32_t)((1u << k) >> st.camp_bits);
         const int ncb = std::min(7, n - k);
         st.ncol_bits = (uint32_t)ncb;
-        int cp[7], nc = 0, ng = 0;
+        for (int j = 0; j < k; ++j) st.local_pos[j] = (uint8_t)lp[j];
+        int nc = 0, ng = 0;
         for (int b = 0; b < n; ++b) {
             if ((local >> b) & 1) continue;
-            if (nc < ncb) cp[nc++] = b;
+            if (nc < ncb) st.col_pos[nc++] = (uint8_t)b;
             else st.glob_pos[ng++] = (uint8_t)b;
         }
         st.n_glob = (uint32_t)ng;
-        // chunk-varying bits (local 0..3, column bits) sorted by physical position
-        int var[11], role[11], nv = 0;
-        for (int j = 0; j < 4; ++j) { var[nv] = lp[j]; role[nv] = j; ++nv; }
-        for (int c = 0; c < ncb; ++c) { var[nv] = cp[c]; role[nv] = 8 + c; ++nv; }
+        // chunk-varying bits (low local bits, column bits) in ascending physical order
+        int var[12], role[12], nv = 0;
+        for (uint32_t j = 0; j < st.camp_bits; ++j) { var[nv] = lp[j]; role[nv] = (int)j; ++nv; }
+        for (int c = 0; c < ncb; ++c) { var[nv] = st.col_pos[c]; role[nv] = 8 + c; ++nv; }
         for (int a = 0; a < nv; ++a)
             for (int b2 = a + 1; b2 < nv; ++b2)
                 if (var[b2] < var[a]) { std::swap(var[a], var[b2]); std::swap(role[a], role[b2]); }
         st.nvar = (uint32_t)nv;
         for (int a = 0; a < nv; ++a) {
-            st.var_phys[a] = 1ull << var[a];
+            st.var_pos[a] = (uint8_t)var[a];
             st.var_role[a] = (uint8_t)role[a];
         }
-        for (int j = 4; j < k; ++j) st.hi_local[j - 4] = 1ull << lp[j];
         // fused unitary over the local qubits (index bit j <-> lp[j])
         const int D = 1 << k;
         int lidx[64];
@@ -172,35 +179,38 @@ std::string plan_gemm(const Plan& P, const double* params, int prec, GemmProgram
                 }
             }
         }
-        // real embedding, split, canonical chunks
-        const int M = 2 * D;   // rows = cols of Ut
-        st.a_off = (uint64_t)out->ablob.size();
-        const bool tf32 = prec == 1;
-        const size_t chunk_bytes = tf32 ? (size_t)M * 128 * 2 : (size_t)M * 64 * 2;
-        st.a_chunk_bytes = (uint32_t)chunk_bytes;
-        out->ablob.resize(out->ablob.size() + chunk_bytes * st.nchunk, 0);
-        uint8_t* base = out->ablob.data() + st.a_off;
-        for (int m = 0; m < M; ++m) {
-            const int i = m >> 1, a = m & 1;
-            for (int kk = 0; kk < M; ++kk) {
-                const int j = kk >> 1, b = kk & 1;
+        // Real embedding Ut[n][kk] (n = 2i + a output float, kk = 2j + b input float),
+        // split into rounded hi / lo halves, one 128-byte K chunk per row per block.
+        const uint32_t Nn = st.N;
+        const size_t block = (size_t)Nn * 128;
+        st.b_chunk_bytes = (uint32_t)(2 * block);
+        // B stays in shared memory when it fits beside the two A slots (k = 6)
+        st.resident = ((size_t)st.nchunk * st.b_chunk_bytes + 2 * 32768 <= 192 * 1024) ? 1u : 0u;
+        st.b_off = (uint64_t)((out->ublob.size() + 1023) & ~(size_t)1023);
+        out->ublob.resize(st.b_off + (size_t)st.nchunk * st.b_chunk_bytes, 0);
+        uint8_t* base = out->ublob.data() + st.b_off;
+        const uint32_t kc = tf32 ? 32u : 64u;   // K elements per chunk
+        for (uint32_t r = 0; r < Nn; ++r) {
+            const int i = (int)(r >> 1), a = (int)(r & 1);
+            for (uint32_t kk = 0; kk < Nn; ++kk) {
+                const int j = (int)(kk >> 1), b = (int)(kk & 1);
                 const cd u = U[(size_t)j * D + i];
                 const double v = (a == b) ? u.real() : (a == 1 ? u.imag() : -u.imag());
                 const float x = (float)v;
-                const int c = kk / 32, kl = kk % 32;
-                uint8_t* ch = base + (size_t)c * chunk_bytes;
+                uint8_t* ch = base + (size_t)(kk / kc) * st.b_chunk_bytes;
+                const uint32_t kl = kk % kc;
                 if (tf32) {
                     float hi, lo;
                     split_tf32(x, &hi, &lo);
-                    const size_t off = (size_t)(m / 8) * 1024 + (kl / 4) * 128 + (m % 8) * 16 + (kl % 4) * 4;
+                    const size_t off = sw128(r, kl * 4);
                     std::memcpy(ch + off, &hi, 4);
-                    std::memcpy(ch + chunk_bytes / 2 + off, &lo, 4);
+                    std::memcpy(ch + block + off, &lo, 4);
                 } else {
                     const uint16_t hi = to_bf16(x);
                     const uint16_t lo = to_bf16(x - from_bf16(hi));
-                    const size_t off = (size_t)(m / 8) * 512 + (kl / 8) * 128 + (m % 8) * 16 + (kl % 8) * 2;
+                    const size_t off = sw128(r, kl * 2);
                     std::memcpy(ch + off, &hi, 2);
-                    std::memcpy(ch + chunk_bytes / 2 + off, &lo, 2);
+                    std::memcpy(ch + block + off, &lo, 2);
                 }
             }
         }
