@@ -1,10 +1,13 @@
 """Split-precision tensor-core stages (tcgen05) against the complex128 oracle.
 
 Each partition (no exemptions, fusion width k) is one dense unitary applied as a GEMM
-with three tensor-core products (hi*hi + hi*lo + lo*hi) accumulated in FP32.
-Bounds: TF32x3 keeps ~21 significant bits per product, so it must meet the complex64
-state tolerance 2e-5; BF16x3 keeps ~16 bits (relative rounding ~2^-17 per element and
-product), so its error grows with the number of fused stages: bound 2e-5 per stage.
+with three tensor-core products (hi*hi + lo*hi + hi*lo) accumulated in FP32 in tensor
+memory.  Bound: the split keeps ~21 (TF32x3) or ~16 (BF16x3) significant bits per
+product, but each output element of a fused stage is accumulated over K = 2^(k+1)
+terms in about 3 K / 8 tensor-core accumulation steps whose FP32 additions carry no
+IEEE rounding guarantee, i.e. up to ~3 (K / 8) 2^-23 relative per stage (~1e-5 at
+K = 256).  The tolerance is therefore 2e-5 per fused stage, accumulated over the stages,
+for both precisions.
 """
 import numpy as np
 import pytest
@@ -44,7 +47,7 @@ def test_brickwork_gemm(sv, k, prec):
     ref = S.simulate(circ, None, psi0)
     err = float(np.linalg.norm(got - ref))
     print(f"brick16 k={k} prec={prec} stages={nst} err={err:.3e}")
-    bound = 2e-5 if prec == 1 else 2e-5 * nst
+    bound = 2e-5 * nst
     assert err <= bound, (err, bound)
 
 
@@ -60,7 +63,7 @@ def test_random_circuits_gemm(sv, seed, prec):
     ref = S.simulate(circ, None, psi0)
     err = float(np.linalg.norm(got - ref))
     print(f"random n={n} k={k} prec={prec} stages={nst} err={err:.3e}")
-    bound = 2e-5 if prec == 1 else 2e-5 * nst
+    bound = 2e-5 * nst
     assert err <= bound, (err, bound)
 
 
@@ -80,3 +83,22 @@ def test_gemm_errors(sv):
     assert e.value.status == N.SV_ERR_UNSUPPORTED
     with pytest.raises(sv.SvError):
         sv.Plan(circ, 8, gemm=True)
+
+
+@pytest.mark.parametrize("k", [5, 6, 7])
+@pytest.mark.parametrize("prec", [1, 2])
+def test_brick20_vs_complex128(sv, k, prec):
+    """A wider state (many tiles per stage, k = 7 streams its B operand) against the
+    complex128 CUDA-core run of the same circuit and input."""
+    n = 20
+    circ = C.brickwork(n, 24, 3)
+    psi0 = C.random_state(n, 7)
+    ref = sv.StateVector(n, sv.SV_C128)
+    ref.set_host(psi0)
+    ref.run(sv.Plan(circ, 11))
+    r = ref.get_host()
+    got, nst = _run(sv, circ, k, prec, psi0.astype(np.complex64))
+    err = float(np.linalg.norm(got - r))
+    print(f"brick20 k={k} prec={prec} stages={nst} err={err:.3e}")
+    bound = 2e-5 * nst
+    assert err <= bound, (err, bound)
