@@ -517,7 +517,7 @@ def main_ours(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "qft30_roundtrip", "n_qubits": n, "L": L, "gates": len(circ.gates),
                        "state": "complex64, i.i.d. N(0,1) re/im (seeded torch Philox), normalised",
-                       "l2": "inputs larger than L2 (8 GiB state)", "parallelism": f"replicas x{world}"},
+                       "l2": f"inputs larger than L2 ({(1 << n) * 8 / 2**30:g} GiB state)", "parallelism": f"replicas x{world}"},
             "roofline": roofline,
             "hbm_passes": passes, "stages": len(stages), "achieved_gbs_whole_circuit": whole_gbs,
             "partition_ms": partition_ms, "norm_last_step": norms[-1],

@@ -102,7 +102,8 @@ __global__ void __launch_bounds__(kT, 1)
     const uint32_t N = st.N, nchunk = st.nchunk, cb = st.camp_bits, nvar = st.nvar;
     const uint32_t ncols = 1u << st.ncol_bits;
     const uint32_t namp = 1u << nvar;                 // amplitudes per chunk
-    const uint32_t rounds = namp > (uint32_t)kT ? namp / kT : 1u;
+    const uint32_t npair = namp >> 1;                 // 16-byte pairs (physical bit 0 is var bit 0)
+    const uint32_t rounds = npair > (uint32_t)kT ? npair / kT : 1u;
     const bool resident = st.resident != 0;
     const uint32_t bcb = st.b_chunk_bytes;
 
@@ -116,8 +117,9 @@ __global__ void __launch_bounds__(kT, 1)
         return resident ? sbase + c * bcb : sbase + s * (kASlot + bcb) + kASlot;
     };
 
-    // tables: local index -> physical bits; producer mapping (var bit v of the chunk
-    // amplitude t = tid + 512 r: bits v < 9 from tid, bits v >= 9 from r)
+    // tables: local index -> physical bits; producer mapping: a thread loads amplitude
+    // pairs (var bit 0 is always physical bit 0, so a pair is 16 contiguous bytes); var
+    // bit v >= 1 of pair tp = tid + 512 r comes from tid bit v - 1 (v <= 9) or r bit v - 10
     for (uint32_t i = tid; i < (1u << st.keff); i += kT) {
         uint64_t p = 0;
         for (uint32_t j = 0; j < st.keff; ++j)
@@ -126,8 +128,8 @@ __global__ void __launch_bounds__(kT, 1)
     }
     uint64_t p_tid = 0;
     uint32_t jm_tid = 0;
-    for (uint32_t v = 0; v < nvar && v < (uint32_t)kLogT; ++v)
-        if ((tid >> v) & 1) {
+    for (uint32_t v = 1; v < nvar && v <= (uint32_t)kLogT; ++v)
+        if ((tid >> (v - 1)) & 1) {
             p_tid |= 1ull << st.var_pos[v];
             const uint32_t r = st.var_role[v];
             jm_tid |= 1u << r;   // role j < 8: amplitude bit j; role 8 + c: column bit c (bit 8 + c)
@@ -135,8 +137,8 @@ __global__ void __launch_bounds__(kT, 1)
     if (tid < rounds) {
         uint64_t p = 0;
         uint32_t jm = 0;
-        for (uint32_t v = kLogT; v < nvar; ++v)
-            if ((tid >> (v - kLogT)) & 1) {
+        for (uint32_t v = kLogT + 1; v < nvar; ++v)
+            if ((tid >> (v - kLogT - 1)) & 1) {
                 p |= 1ull << st.var_pos[v];
                 const uint32_t r = st.var_role[v];
                 jm |= 1u << r;
@@ -145,6 +147,8 @@ __global__ void __launch_bounds__(kT, 1)
         s_rsoff[tid] = a_offset<PREC>(jm & 0xFFu, jm >> 8);
     }
     const uint32_t soff_tid = a_offset<PREC>(jm_tid & 0xFFu, jm_tid >> 8);
+    const uint32_t jm_b0 = 1u << st.var_role[0];                  // the pair's second amplitude
+    const uint32_t soff_b0 = a_offset<PREC>(jm_b0 & 0xFFu, jm_b0 >> 8);
     // epilogue: this thread's column (TMEM lane) and the quarter of N its warp reads
     const uint32_t m_ep = 32u * (warp & 3u) + lane;
     uint64_t cpart = 0;
@@ -207,9 +211,17 @@ __global__ void __launch_bounds__(kT, 1)
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             if (ok && m_ep < ncols) {
                 const uint64_t pc = pbase | cpart;
+                if (st.local_pos[0] == 0) {   // local index pairs (2i, 2i + 1) are adjacent: 16-byte stores
 #pragma unroll
-                for (int q = 0; q < 16; ++q)
-                    psi[pc | s_ltab[(n0 >> 1) + q]] = make_float2(__uint_as_float(r[2 * q]), __uint_as_float(r[2 * q + 1]));
+                    for (int q = 0; q < 8; ++q)
+                        *reinterpret_cast<float4*>(psi + (pc | s_ltab[(n0 >> 1) + 2 * q])) =
+                            make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                                        __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q)
+                        psi[pc | s_ltab[(n0 >> 1) + q]] = make_float2(__uint_as_float(r[2 * q]), __uint_as_float(r[2 * q + 1]));
+                }
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -220,7 +232,7 @@ __global__ void __launch_bounds__(kT, 1)
     // Every per-amplitude offset is a per-thread constant.  Three register sets form a
     // ring: while chunk g is split, stored and multiplied, chunks g + 1 and g + 2 are in
     // flight (their loads were issued one and two steps earlier).
-    constexpr int RMAX = PREC == 1 ? 4 : 8;
+    constexpr int RMAX = PREC == 1 ? 2 : 4;   // amplitude pairs per thread and chunk
     const uint64_t my_tiles = (uint64_t)blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const uint64_t total = my_tiles * nchunk;
     uint64_t gmask = 0, pstep = 0, base = 0;
@@ -233,15 +245,15 @@ __global__ void __launch_bounds__(kT, 1)
     uint32_t vmask = 0;
 #pragma unroll
     for (int r = 0; r < RMAX; ++r)
-        if ((uint32_t)r < rounds && tid + (uint32_t)r * kT < namp) vmask |= 1u << r;
-    auto load_chunk = [&](uint64_t cb0, float2 (&v)[RMAX]) {
+        if ((uint32_t)r < rounds && tid + (uint32_t)r * kT < npair) vmask |= 1u << r;
+    auto load_chunk = [&](uint64_t cb0, float4 (&v)[RMAX]) {
         const uint64_t b = cb0 | p_tid;
 #pragma unroll
         for (int r = 0; r < RMAX; ++r)
-            if ((vmask >> r) & 1) v[r] = psi[b | s_roff[r]];
+            if ((vmask >> r) & 1) v[r] = *reinterpret_cast<const float4*>(psi + (b | s_roff[r]));
     };
     auto next_tile = [&](uint64_t b) -> uint64_t { return ((b | ~gmask) + pstep) & gmask; };
-    float2 va[RMAX], vb[RMAX], vc3[RMAX];
+    float4 va[RMAX], vb[RMAX], vc3[RMAX];
     // lookahead position: the chunk two steps ahead of the current one
     uint32_t cl = 0;
     uint64_t bl = base;
@@ -261,7 +273,7 @@ __global__ void __launch_bounds__(kT, 1)
     // One chunk step: load chunk g + 2 into vl, split / store chunk g from vc, issue its
     // MMAs, then advance (g, t, c, base).  Returns false when a bounded wait gave up
     // (uniformly across the CTA).
-    auto step = [&](float2 (&vc)[RMAX], float2 (&vl)[RMAX]) -> bool {
+    auto step = [&](float4 (&vc)[RMAX], float4 (&vl)[RMAX]) -> bool {
         const uint32_t slot = (uint32_t)(g & 1u), ab = (uint32_t)(t & 1u);
         uint32_t cn = c + 1;
         uint64_t bn = base;
@@ -285,16 +297,21 @@ __global__ void __launch_bounds__(kT, 1)
         for (int r = 0; r < RMAX; ++r) {
             if (!((vmask >> r) & 1)) continue;
             const uint32_t so = soff_tid ^ s_rsoff[r];
-            if (PREC == 1) {
-                const float hr = rn_tf32(vc[r].x), hi_ = rn_tf32(vc[r].y);
-                *reinterpret_cast<float2*>(aH + so) = make_float2(hr, hi_);
-                *reinterpret_cast<float2*>(aL + so) = make_float2(rn_tf32(vc[r].x - hr), rn_tf32(vc[r].y - hi_));
-            } else {
-                const __nv_bfloat162 h2 = __floats2bfloat162_rn(vc[r].x, vc[r].y);
-                const float2 hf = __bfloat1622float2(h2);
-                const __nv_bfloat162 l2 = __floats2bfloat162_rn(vc[r].x - hf.x, vc[r].y - hf.y);
-                *reinterpret_cast<__nv_bfloat162*>(aH + so) = h2;
-                *reinterpret_cast<__nv_bfloat162*>(aL + so) = l2;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {   // the pair's two amplitudes
+                const float re = h ? vc[r].z : vc[r].x, im = h ? vc[r].w : vc[r].y;
+                const uint32_t o2 = h ? so ^ soff_b0 : so;
+                if (PREC == 1) {
+                    const float hr = rn_tf32(re), hi_ = rn_tf32(im);
+                    *reinterpret_cast<float2*>(aH + o2) = make_float2(hr, hi_);
+                    *reinterpret_cast<float2*>(aL + o2) = make_float2(rn_tf32(re - hr), rn_tf32(im - hi_));
+                } else {
+                    const __nv_bfloat162 h2 = __floats2bfloat162_rn(re, im);
+                    const float2 hf = __bfloat1622float2(h2);
+                    const __nv_bfloat162 l2 = __floats2bfloat162_rn(re - hf.x, im - hf.y);
+                    *reinterpret_cast<__nv_bfloat162*>(aH + o2) = h2;
+                    *reinterpret_cast<__nv_bfloat162*>(aL + o2) = l2;
+                }
             }
         }
         if (!resident) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
