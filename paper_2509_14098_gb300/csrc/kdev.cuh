@@ -336,13 +336,55 @@ __device__ __forceinline__ DevOp<Real> load_op(const DevOp<Real>* p) {
     return o;
 }
 
+// A real dense op's folded pair phases (F_PAIRS): the target's |1> amplitude of pair k
+// is multiplied by w0 * prod over the other register bits i set in k of e^{i angle_i}
+// (w0 = the op's twiddle, or 1).  The eight products come from a product tree.
+template <typename Real, int R, int NV, int J>
+__device__ __forceinline__ void pair_phases(typename RegT<Real>::type (&a)[NV][1 << R], const DevOp<Real>& o,
+                                            const OpCtx<Real>& x) {
+    using C = typename CT<Real>::C;
+    using Ang = typename AngT<Real>::type;
+    constexpr int NO = R - 1;   // other register bits
+    C w0;
+    if (o.flags & F_TW) {
+        w0 = phase_factor<Real>(o, x);
+    } else {
+        w0.x = 1;
+        w0.y = 0;
+    }
+    C ph[1 << NO];
+    ph[0] = w0;
+#pragma unroll
+    for (int i = 0; i < NO; ++i) {
+        Ang ang;
+        memcpy(&ang, &o.m[1 + 2 * i], sizeof(ang));
+        const C p = expi(ang);
+#pragma unroll
+        for (int c = 0; c < (1 << i); ++c) ph[c | (1 << i)] = cmul(ph[c], p);
+    }
+#pragma unroll
+    for (int k = 0; k < (1 << R); ++k) {
+        if (k & (1 << J)) continue;
+        constexpr int LOW = (1 << J) - 1;
+        const int c = (k & LOW) | ((k >> (J + 1)) << J);   // k without bit J
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            if constexpr (sizeof(Real) == 4) p_cmul(a[v][k | (1 << J)], ph[c].x, ph[c].y, -ph[c].y);
+            else a[v][k | (1 << J)] = cmul(a[v][k | (1 << J)], ph[c]);
+        }
+    }
+}
+
 template <typename Real, int R, int NV, int TYPE, bool CTRL, int J>
 __device__ __forceinline__ void dense_case(typename RegT<Real>::type (&a)[NV][1 << R], const DevOp<Real>& o,
                                            const OpCtx<Real>& x) {
     using C = typename CT<Real>::C;
     if constexpr (J < R) {
         if ((x.fix & o.ctrl_fix) != o.ctrl_fix) return;   // control on a thread / global bit
-        if (o.flags & F_TW) {
+        if constexpr (TYPE == OP_UR && !CTRL && R >= 2 && R <= 4) {
+            if (o.flags & F_PAIRS) pair_phases<Real, R, NV, J>(a, o, x);
+        }
+        if ((o.flags & (F_TW | F_PAIRS)) == F_TW) {
             const C w = phase_factor<Real>(o, x);
 #pragma unroll
             for (int v = 0; v < NV; ++v) {

@@ -51,6 +51,7 @@ class Lowerer {
     double gphase_ = 0.0;
     int regidx_[64];
     svk::Group* grp_ = nullptr;
+    int grp_R_ = 0;   // register bits of the current group
     uint32_t stage_slots_ = 0;
     uint32_t slot_base_ = 0;
 
@@ -81,7 +82,8 @@ class Lowerer {
     // register partner become PHASE2 ops; the rest (a constant and single-bit terms on
     // non-register bits) is either emitted as a PHASE1 op or, when fuse is set,
     // returned for the dense op to apply as its twiddle.
-    void flush_bit(int t, bool fuse, double* cangle_out, std::vector<svk::Term>* terms_out);
+    void flush_bit(int t, bool fuse, double* cangle_out, std::vector<svk::Term>* terms_out,
+                   std::map<int, double>* pairs_out = nullptr);
     void flush_all();
     std::string gate(const GateRec& g, const PGate& pg);
     std::string stage(int s);
@@ -97,7 +99,8 @@ void Lowerer::emit_grad_z(int bit, int param) {
 
 // Apply every pending term that involves physical bit t (a register bit of the
 // current group) — right before a dense gate on t.
-void Lowerer::flush_bit(int t, bool fuse, double* cangle_out, std::vector<svk::Term>* terms_out) {
+void Lowerer::flush_bit(int t, bool fuse, double* cangle_out, std::vector<svk::Term>* terms_out,
+                        std::map<int, double>* pairs_out) {
     const uint64_t tb = 1ull << t;
     const int jt = regidx_[t];
     double cangle = 0.0;
@@ -125,6 +128,10 @@ void Lowerer::flush_bit(int t, bool fuse, double* cangle_out, std::vector<svk::T
             }
         }
         it = pending_.erase(it);
+    }
+    if (pairs_out) {   // the dense op applies them (register bit -> angle)
+        *pairs_out = pair;
+        pair.clear();
     }
     for (auto& kv : pair) {   // diagonal: order among the phases is free
         int a = jt, b = kv.first;
@@ -259,7 +266,12 @@ std::string Lowerer::gate(const GateRec& g, const PGate& pg) {
     const bool fuse = !kind_is_controlled(g.kind) && !((bwd_ || bind_) && g.param >= 0);
     double tw_angle = 0.0;
     std::vector<svk::Term> tw_terms;
-    flush_bit(t, fuse, &tw_angle, &tw_terms);
+    // a real 2x2 (H, RY) also takes the pair phases on its target and another register
+    // bit, when its group's other register bits fit the op's three spare slots
+    const bool real_op = g.kind == K_H || g.kind == K_RY;
+    const bool pair_fuse = fuse && real_op && grp_R_ <= 4;
+    std::map<int, double> pairs;
+    flush_bit(t, fuse, &tw_angle, &tw_terms, pair_fuse ? &pairs : nullptr);
     double m[8];
     uint8_t type = svk::OP_U;
     switch (g.kind) {
@@ -307,6 +319,14 @@ std::string Lowerer::gate(const GateRec& g, const PGate& pg) {
     }
     svk::Op& o = new_op(type, jt);
     std::memcpy(o.m, m, sizeof(m));
+    if (!pairs.empty()) {
+        if (type != svk::OP_UR) return "internal: pair phases on a complex dense op";
+        o.has_pairs = 1;
+        for (auto& kv : pairs) {
+            const int idx = kv.first < jt ? kv.first : kv.first - 1;   // rank among the other bits
+            o.pair_ang[idx] += kv.second;
+        }
+    }
     if (bind_ && g.param >= 0) {
         o.bparam1 = (uint32_t)g.param + 1;
         o.bkind = (uint8_t)((g.kind == K_RX ? svk::BK_RX : g.kind == K_RY ? svk::BK_RY : svk::BK_RZ) |
@@ -373,6 +393,7 @@ std::string Lowerer::stage(int s) {
         std::memset(&G, 0, sizeof(G));
         G.op_off = (uint32_t)out_->ops.size();
         grp_ = &G;
+        grp_R_ = R;
         for (int b = 0; b < 64; ++b) regidx_[b] = -1;
         int nr = 0, nt = 0;
         for (int b = 0; b < T; ++b) {
@@ -479,6 +500,14 @@ static void pack_real(const Program& p, int n, Packed* out) {
                 d.ctrl_fix = o.ctrl_fix;
                 d.slot = o.slot;
                 for (int i = 0; i < 8; ++i) d.m[i] = (Real)o.m[i];
+                if (o.has_pairs) {   // angles in the imaginary slots OP_UR ignores
+                    d.flags |= svk::F_PAIRS;
+                    for (int i = 0; i < 3; ++i) {
+                        const typename svk::AngT<Real>::type a = dev_angle<Real>(o.pair_ang[i]);
+                        static_assert(sizeof(a) == sizeof(Real), "angle slot size");
+                        std::memcpy(&d.m[1 + 2 * i], &a, sizeof(a));
+                    }
+                }
                 if (o.bparam1) {
                     d.flags |= svk::F_BIND;
                     d.term_off = o.bparam1 - 1;

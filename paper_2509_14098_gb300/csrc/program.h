@@ -60,6 +60,9 @@ struct Op {
     double m[8];            // row-major 2x2 (re, im) pairs; PHASE ops use m[0], m[1]
     double tw_angle;        // dense op twiddle constant (has_tw)
     uint8_t bkind;          // bound dense op: BK_RX / BK_RY / BK_RZ, | BK_DAGGER for the adjoint
+    uint8_t has_pairs;      // real dense op: pair phases folded in (pair_ang)
+    double pair_ang[3];     // phase on the target's |1> half when the i-th other register bit
+                            // (ascending, skipping j) is set; 0 for bits without a phase
 };
 
 struct Term {               // phase angle added when every bit of mask is set
@@ -74,6 +77,9 @@ enum OpFlag : uint8_t {
                             // give the angle; a dense op's constant is a mask-0 term)
     F_BIND = 8,             // dense op whose matrix the kernel forms from a parameter:
                             // term_off = parameter index, u = BK_* kind (| BK_DAGGER)
+    F_PAIRS = 32,           // real dense op (OP_UR) preceded by phases on its target's |1> half
+                            // that depend on the other register bits: the angles (device angle
+                            // type) sit in m[1], m[3], m[5], the imaginary slots OP_UR ignores
 };
 
 // Parametric rotations whose matrix is formed on the device (batched programs are
