@@ -381,10 +381,7 @@ __device__ __forceinline__ void dense_case(typename RegT<Real>::type (&a)[NV][1 
     using C = typename CT<Real>::C;
     if constexpr (J < R) {
         if ((x.fix & o.ctrl_fix) != o.ctrl_fix) return;   // control on a thread / global bit
-        if constexpr (TYPE == OP_UR && !CTRL && R >= 2 && R <= 4) {
-            if (o.flags & F_PAIRS) pair_phases<Real, R, NV, J>(a, o, x);
-        }
-        if ((o.flags & (F_TW | F_PAIRS)) == F_TW) {
+        if (o.flags & F_TW) {
             const C w = phase_factor<Real>(o, x);
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
@@ -403,6 +400,21 @@ __device__ __forceinline__ void dense_case(typename RegT<Real>::type (&a)[NV][1 
                 else if constexpr (TYPE == OP_UR) dense_ur<R, J, CTRL, C, Real>(a[v], o.m, o.ctrl_reg);
                 else dense_u<R, J, CTRL, C, Real>(a[v], o.m, o.ctrl_reg);
             }
+        }
+    }
+}
+
+// real dense op with folded pair phases (its own dispatch codes, so the plain dense
+// bodies stay as they are)
+template <typename Real, int R, int NV, int J>
+__device__ __forceinline__ void urp_case(typename RegT<Real>::type (&a)[NV][1 << R], const DevOp<Real>& o,
+                                         const OpCtx<Real>& x) {
+    if constexpr (J < R && R >= 2 && R <= 4) {
+        pair_phases<Real, R, NV, J>(a, o, x);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            if constexpr (sizeof(Real) == 4) pd_ur<R, J, false>(a[v], o.m, 0u);
+            else dense_ur<R, J, false, typename CT<Real>::C, Real>(a[v], o.m, 0u);
         }
     }
 }
@@ -456,6 +468,10 @@ __device__ __forceinline__ void apply_op(typename RegT<Real>::type (&a)[NV][1 <<
         SVK_DENSE_CASES(OP_UR, true, 15)
         SVK_DENSE_CASES(OP_X, false, 20)
         SVK_DENSE_CASES(OP_X, true, 25)
+        case C_URP + 0: urp_case<Real, R, NV, 0>(a, o, x); break;
+        case C_URP + 1: urp_case<Real, R, NV, 1>(a, o, x); break;
+        case C_URP + 2: urp_case<Real, R, NV, 2>(a, o, x); break;
+        case C_URP + 3: urp_case<Real, R, NV, 3>(a, o, x); break;
         case C_PHASE1 + 0: phase1_case<Real, R, NV, 0>(a, o, x); break;
         case C_PHASE1 + 1: phase1_case<Real, R, NV, 1>(a, o, x); break;
         case C_PHASE1 + 2: phase1_case<Real, R, NV, 2>(a, o, x); break;

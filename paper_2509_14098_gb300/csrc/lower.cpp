@@ -573,6 +573,7 @@ static void pack_real(const Program& p, int n, Packed* out) {
                     case svk::OP_U: case svk::OP_UR: case svk::OP_X: {
                         const uint32_t ctrl = (o.ctrl_reg != 0) ? 1u : 0u;
                         d.code = svk::C_DENSE + ((uint32_t)o.type * 2 + ctrl) * 5 + o.j;
+                        if (o.has_pairs) d.code = svk::C_URP + o.j;   // uncontrolled OP_UR only
                         break;
                     }
                     case svk::OP_PHASE1: d.code = svk::C_PHASE1 + o.j; break;

@@ -112,6 +112,7 @@ enum : uint32_t {
     C_PHASE0 = 45,
     C_GRAD = 46,            // + (kind * 5 + j), kind 0 = X, 1 = Y, 2 = Z on a register bit
     C_GRADZ_FIX = 61,       // Z on a non-register bit
+    C_URP = 62,             // + j: real dense op with folded pair phases (F_PAIRS, uncontrolled)
 };
 SVK_HD uint32_t pair_index(int j, int u) {   // j < u < 5: (0,1..4) -> 0..3, (1,2..4) -> 4..6, (2,3..4) -> 7..8, (3,4) -> 9
     return (uint32_t)(j == 0 ? u - 1 : j == 1 ? u + 2 : j == 2 ? u + 4 : 9);
