@@ -7,6 +7,10 @@
 
 #include "program.h"
 
+#ifndef SVK_PACKED_U
+#define SVK_PACKED_U 1   // complex 2x2 bodies in packed FP32x2 arithmetic (0: scalar FP32)
+#endif
+
 namespace svk {
 
 template <typename Real> struct CT;
@@ -283,8 +287,39 @@ __device__ __forceinline__ void pd_ur(u64 (&a)[1 << R], const float (&m)[8], uin
         p_ur(a[k], a[k | (1 << J)], m0, m2, m4, m6);
     }
 }
+#if SVK_PACKED_U
+// complex 2x2 on a pair with packed FP32x2 arithmetic, in place: y0 = m00 x0 + m01 x1,
+// y1 = m10 x0 + m11 x1, each complex product as (mr, mr) * x + (-mi, mi) * swap(x) (the
+// same FMA order as p_u, so the same rounding)
+__device__ __forceinline__ void p_u2(u64& x0, u64& x1, const u64 (&mr)[4], const u64 (&mi)[4]) {
+    asm volatile("{\n\t.reg .b64 s0, s1, t0, t1;\n\t.reg .f32 a, b, c, d;\n\t"
+                 "mov.b64 {a, b}, %0;\n\tmov.b64 s0, {b, a};\n\t"
+                 "mov.b64 {c, d}, %1;\n\tmov.b64 s1, {d, c};\n\t"
+                 "mul.rn.f32x2 t0, %2, %0;\n\tfma.rn.f32x2 t0, %6, s0, t0;\n\t"
+                 "fma.rn.f32x2 t0, %3, %1, t0;\n\tfma.rn.f32x2 t0, %7, s1, t0;\n\t"
+                 "mul.rn.f32x2 t1, %4, %0;\n\tfma.rn.f32x2 t1, %8, s0, t1;\n\t"
+                 "fma.rn.f32x2 t1, %5, %1, t1;\n\tfma.rn.f32x2 t1, %9, s1, t1;\n\t"
+                 "mov.b64 %0, t0;\n\tmov.b64 %1, t1;\n\t}"
+                 : "+l"(x0), "+l"(x1)
+                 : "l"(mr[0]), "l"(mr[1]), "l"(mr[2]), "l"(mr[3]), "l"(mi[0]), "l"(mi[1]), "l"(mi[2]), "l"(mi[3]));
+}
+#endif
 template <int R, int J, bool CTRL>
 __device__ __forceinline__ void pd_u(u64 (&a)[1 << R], const float (&m)[8], uint32_t creg) {
+#if SVK_PACKED_U
+    u64 mr[4], mi[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        mr[e] = pack2(m[2 * e], m[2 * e]);
+        mi[e] = pack2(-m[2 * e + 1], m[2 * e + 1]);
+    }
+#pragma unroll
+    for (int k = 0; k < (1 << R); ++k) {
+        if (k & (1 << J)) continue;
+        if (CTRL && (k & creg) != creg) continue;
+        p_u2(a[k], a[k | (1 << J)], mr, mi);
+    }
+#else
     const float n[4] = {-m[1], -m[3], -m[5], -m[7]};
 #pragma unroll
     for (int k = 0; k < (1 << R); ++k) {
@@ -292,6 +327,7 @@ __device__ __forceinline__ void pd_u(u64 (&a)[1 << R], const float (&m)[8], uint
         if (CTRL && (k & creg) != creg) continue;
         p_u(a[k], a[k | (1 << J)], m, n);
     }
+#endif
 }
 template <int R, int J, bool CTRL>
 __device__ __forceinline__ void pd_x(u64 (&a)[1 << R], uint32_t creg) {
@@ -445,6 +481,14 @@ __device__ __forceinline__ void phase2_case(typename RegT<Real>::type (&a)[NV][1
     }
 }
 
+// complex dense ops (OP_U) only in kernels built with CPLX (stages without them run a
+// smaller interpreter)
+#define SVK_CDENSE_CASES(CTRL, BASE)                                                        \
+    case BASE + 0: if constexpr (CPLX) dense_case<Real, R, NV, OP_U, CTRL, 0>(a, o, x); break; \
+    case BASE + 1: if constexpr (CPLX) dense_case<Real, R, NV, OP_U, CTRL, 1>(a, o, x); break; \
+    case BASE + 2: if constexpr (CPLX) dense_case<Real, R, NV, OP_U, CTRL, 2>(a, o, x); break; \
+    case BASE + 3: if constexpr (CPLX) dense_case<Real, R, NV, OP_U, CTRL, 3>(a, o, x); break; \
+    case BASE + 4: if constexpr (CPLX) dense_case<Real, R, NV, OP_U, CTRL, 4>(a, o, x); break;
 #define SVK_DENSE_CASES(TYPE, CTRL, BASE)                                                   \
     case BASE + 0: dense_case<Real, R, NV, TYPE, CTRL, 0>(a, o, x); break;                 \
     case BASE + 1: dense_case<Real, R, NV, TYPE, CTRL, 1>(a, o, x); break;                 \
@@ -458,12 +502,12 @@ __device__ __forceinline__ void phase2_case(typename RegT<Real>::type (&a)[NV][1
 
 // Apply one (non-gradient) op to NV register arrays (forward: psi; adjoint: psi and
 // lambda), with one dispatch and one phase evaluation.
-template <typename Real, int R, int NV>
+template <typename Real, int R, int NV, bool CPLX = true>
 __device__ __forceinline__ void apply_op(typename RegT<Real>::type (&a)[NV][1 << R], const DevOp<Real>& o,
                                          const OpCtx<Real>& x) {
     switch (o.code) {
-        SVK_DENSE_CASES(OP_U, false, 0)
-        SVK_DENSE_CASES(OP_U, true, 5)
+        SVK_CDENSE_CASES(false, 0)
+        SVK_CDENSE_CASES(true, 5)
         SVK_DENSE_CASES(OP_UR, false, 10)
         SVK_DENSE_CASES(OP_UR, true, 15)
         SVK_DENSE_CASES(OP_X, false, 20)
@@ -498,6 +542,7 @@ __device__ __forceinline__ void apply_op(typename RegT<Real>::type (&a)[NV][1 <<
     }
 }
 #undef SVK_DENSE_CASES
+#undef SVK_CDENSE_CASES
 #undef SVK_PHASE2_CASE
 
 // Stage the stage's register groups, ops and phase slots into shared memory.

@@ -583,6 +583,7 @@ static void pack_real(const Program& p, int n, Packed* out) {
                     case svk::OP_GRAD_Y: d.code = svk::C_GRAD + 1 * 5 + o.j; break;
                     default: d.code = o.u ? svk::C_GRADZ_FIX : svk::C_GRAD + 2 * 5 + o.j; break;
                 }
+                if (d.code < svk::C_DENSE + 10) st.has_complex = 1;   // OP_U codes
                 ops.push_back(d);
             }
         }

@@ -163,7 +163,7 @@ struct Stage {
     uint32_t op_off, n_ops; // this stage's ops (groups index relative to op_off)
     uint32_t phase_off, n_phase;  // phase slots of this stage
     uint32_t thr_off;       // unused
-    uint32_t pad;
+    uint32_t has_complex;   // any complex dense op (OP_U) in this stage
     uint8_t glob_pos[kMaxQ];  // physical positions of the global bits (ascending)
     uint8_t tile_pos[kMaxT];  // physical positions of the tile bits (ascending)
     uint8_t pad2[2];

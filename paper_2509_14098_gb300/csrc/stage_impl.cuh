@@ -47,7 +47,7 @@ namespace svk {
 // the global bits: base(t + G) = ((base(t) | ~gmask) + pdep(G)) & gmask.  Gradient
 // partial sums accumulate per CTA in FP64 (per warp, fixed order) and are written once.
 // ---------------------------------------------------------------------------
-template <typename Real, int R, int MAXT, int NV, int NB>
+template <typename Real, int R, int MAXT, int NV, int NB, bool CPLX>
 __global__ void __launch_bounds__(MAXT, (MAXT >= 512 ? 1 : (NV == 1 ? SVK_MINB_FWD : SVK_MINB_BWD)))
     k_stage(typename CT<Real>::C* __restrict__ psi, typename CT<Real>::C* __restrict__ lam,
             const Stage* __restrict__ stp, const Group* __restrict__ groups,
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT >= 512 ? 1 : (NV == 1 ? SVK_MINB_F
                         if ((uint32_t)off < nthr) v += __shfl_xor_sync(wmask, v, off);
                     if (lane == 0) gsm[o.slot * nw + warp] += v;
                 } else {
-                    apply_op<Real, R, NV>(a, o, x);
+                    apply_op<Real, R, NV, CPLX>(a, o, x);
                 }
             }
             store_regs<A, C, R>(a[0], cur0, soff, sr, pairs);
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT >= 512 ? 1 : (NV == 1 ? SVK_MINB_F
 // ---------------------------------------------------------------------------
 // launch wrappers
 // ---------------------------------------------------------------------------
-template <typename Real, int R, int MAXT, int NV, int NB>
+template <typename Real, int R, int MAXT, int NV, int NB, bool CPLX>
 static cudaError_t try_launch(const StageLaunch& L, const Stage& hst, cudaStream_t s, uint32_t* grid_out,
                               int min_per_sm, bool* launched) {
     using C = typename CT<Real>::C;
@@ -260,7 +260,7 @@ static cudaError_t try_launch(const StageLaunch& L, const Stage& hst, cudaStream
     if (smem > 227 * 1024) return cudaSuccess;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_stage<Real, R, MAXT, NV, NB>,
+        cudaError_t e = cudaFuncSetAttribute(k_stage<Real, R, MAXT, NV, NB, CPLX>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         if (e != cudaSuccess) return e;
         configured = true;
@@ -270,12 +270,12 @@ static cudaError_t try_launch(const StageLaunch& L, const Stage& hst, cudaStream
     int per_sm = 0, dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage<Real, R, MAXT, NV, NB>, nthr, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage<Real, R, MAXT, NV, NB, CPLX>, nthr, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < min_per_sm || per_sm < 1) return cudaSuccess;
     const uint64_t grid = std::min<uint64_t>(ntiles, (uint64_t)per_sm * (uint64_t)nsm);
     if (grid_out) *grid_out = (uint32_t)grid;
-    k_stage<Real, R, MAXT, NV, NB><<<(unsigned)grid, nthr, smem, s>>>(
+    k_stage<Real, R, MAXT, NV, NB, CPLX><<<(unsigned)grid, nthr, smem, s>>>(
         (C*)L.psi, (C*)L.lam, L.stage, L.groups, (const DevOp<Real>*)L.ops, (const DevTerm<Real>*)L.terms,
         (const PhaseSlot<Real>*)L.slots, L.partial);
     *launched = true;
@@ -284,23 +284,31 @@ static cudaError_t try_launch(const StageLaunch& L, const Stage& hst, cudaStream
 
 // adjoint: double-buffered tiles while that still leaves >= 2 CTAs per SM, else single-
 // buffered; forward: single-buffered (occupancy hides the loads, see SVK_MINB_FWD)
-template <typename Real, int R, int MAXT, int NV>
+template <typename Real, int R, int MAXT, int NV, bool CPLX>
 static cudaError_t launch_RT(const StageLaunch& L, const Stage& hst, cudaStream_t s, uint32_t* grid_out) {
     bool ok = false;
     cudaError_t e = cudaSuccess;
     if constexpr (NV == 2) {
-        e = try_launch<Real, R, MAXT, NV, 2>(L, hst, s, grid_out, 2, &ok);
+        e = try_launch<Real, R, MAXT, NV, 2, CPLX>(L, hst, s, grid_out, 2, &ok);
         if (e != cudaSuccess || ok) return e;
     }
-    e = try_launch<Real, R, MAXT, NV, 1>(L, hst, s, grid_out, 1, &ok);
+    e = try_launch<Real, R, MAXT, NV, 1, CPLX>(L, hst, s, grid_out, 1, &ok);
     if (e != cudaSuccess) return e;
     return ok ? cudaSuccess : cudaErrorInvalidConfiguration;
 }
 // 256-thread bound unless the tile needs 512 threads
 template <typename Real, int R, int NV>
 cudaError_t launch_R(const StageLaunch& L, const Stage& hst, cudaStream_t s, uint32_t* grid_out) {
-    if ((hst.T - R) <= 8) return launch_RT<Real, R, 256, NV>(L, hst, s, grid_out);
-    if ((hst.T - R) == 9) return launch_RT<Real, R, 512, NV>(L, hst, s, grid_out);
+    // complex64 forward stages without complex dense ops run an interpreter without them
+    if constexpr (sizeof(Real) == 4 && NV == 1) {
+        if (!hst.has_complex) {
+            if ((hst.T - R) <= 8) return launch_RT<Real, R, 256, NV, false>(L, hst, s, grid_out);
+            if ((hst.T - R) == 9) return launch_RT<Real, R, 512, NV, false>(L, hst, s, grid_out);
+            return cudaErrorInvalidConfiguration;
+        }
+    }
+    if ((hst.T - R) <= 8) return launch_RT<Real, R, 256, NV, true>(L, hst, s, grid_out);
+    if ((hst.T - R) == 9) return launch_RT<Real, R, 512, NV, true>(L, hst, s, grid_out);
     return cudaErrorInvalidConfiguration;
 }
 
