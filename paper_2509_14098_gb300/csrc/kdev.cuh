@@ -445,7 +445,7 @@ __device__ __forceinline__ void dense_case(typename RegT<Real>::type (&a)[NV][1 
 template <typename Real, int R, int NV, int J>
 __device__ __forceinline__ void urp_case(typename RegT<Real>::type (&a)[NV][1 << R], const DevOp<Real>& o,
                                          const OpCtx<Real>& x) {
-    if constexpr (J < R && R >= 2 && R <= 4) {
+    if constexpr (J < R && R >= 2 && R <= 4 && NV == 1) {   // forward programs only
         pair_phases<Real, R, NV, J>(a, o, x);
 #pragma unroll
         for (int v = 0; v < NV; ++v) {

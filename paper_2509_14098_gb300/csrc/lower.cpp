@@ -269,7 +269,7 @@ std::string Lowerer::gate(const GateRec& g, const PGate& pg) {
     // a real 2x2 (H, RY) also takes the pair phases on its target and another register
     // bit, when its group's other register bits fit the op's three spare slots
     const bool real_op = g.kind == K_H || g.kind == K_RY;
-    const bool pair_fuse = fuse && real_op && grp_R_ <= 4;
+    const bool pair_fuse = fuse && real_op && grp_R_ <= 4 && !bwd_;   // forward programs only
     std::map<int, double> pairs;
     flush_bit(t, fuse, &tw_angle, &tw_terms, pair_fuse ? &pairs : nullptr);
     double m[8];
