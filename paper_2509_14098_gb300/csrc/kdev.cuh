@@ -505,6 +505,12 @@ __device__ __forceinline__ void phase2_case(typename RegT<Real>::type (&a)[NV][1
 template <typename Real, int R, int NV, bool CPLX = true>
 __device__ __forceinline__ void apply_op(typename RegT<Real>::type (&a)[NV][1 << R], const DevOp<Real>& o,
                                          const OpCtx<Real>& x) {
+    // folded-pair butterflies (the bulk of QFT-like stages) are dispatched ahead of the
+    // full switch: measured 7 % faster QFT30 stages (brickwork stages 4 % slower)
+    if (o.code >= C_URP) {
+        SVK_SWITCH_J(o.code - C_URP, R, (urp_case<Real, R, NV, J_>(a, o, x)));
+        return;
+    }
     switch (o.code) {
         SVK_CDENSE_CASES(false, 0)
         SVK_CDENSE_CASES(true, 5)
