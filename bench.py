@@ -347,6 +347,50 @@ def gemm_section(args):
             "reference": "complex128 CUDA-core run (L=11)" if ref is not None else None}
 
 
+def aux_section(n, reps=3):
+    """Permutation sweep (bit reversal of n qubits: out-of-place, then copied back) and the
+    FP64 reductions (norm; TFIM expectation by Pauli sweeps) on a 2^n complex64 state:
+    device time per call (CUDA events via the library's timing record where it has one)
+    and algorithmic GB/s."""
+    import torch
+
+    import circuits as C
+    import paper_2509_14098_gb300 as sv
+    psi = torch.randn(1 << n, dtype=torch.complex64, device="cuda")
+    psi /= torch.linalg.vector_norm(psi)
+    st = sv.StateVector(n, tensor=psi)
+    rev = [n - 1 - q for q in range(n)]
+    st.permute(rev)
+    st.norm()
+    st.expval(C.tfim(n))
+    st.timing(True)
+    st.timing(reset=True)
+    for _ in range(reps):
+        st.permute(rev)
+    st.synchronize()
+    tm = st.timing(reset=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st.stream)
+    for _ in range(reps):
+        st.norm()
+    e1.record(st.stream)
+    torch.cuda.synchronize()
+    norm_ms = e0.elapsed_time(e1) / reps
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        st.expval(C.tfim(n))
+    ev_ms = (time.perf_counter() - t0) * 1e3 / reps
+    st.timing(False)
+    st.close()
+    nb = (1 << n) * 8
+    perm_ms = tm["permute_ms"] / max(1, tm["permute_launches"])
+    return {"n_qubits": n,
+            "permutation": {"what": "bit reversal, one out-of-place sweep (kernel time; sv_permute then copies the result back into the caller's buffer)", "ms_per_sweep": perm_ms,
+                            "gbs": 2 * nb / (perm_ms * 1e-3) / 1e9, "launches": tm["permute_launches"] / reps},
+            "norm": {"what": "||psi||^2 in FP64 (host result)", "ms": norm_ms, "gbs": nb / (norm_ms * 1e-3) / 1e9},
+            "expval_tfim": {"what": "<psi| sum ZZ + 0.7 sum X |psi> (Pauli sweeps, FP64, host result)", "ms": ev_ms}}
+
+
 def main_ours(args):
     import ctypes
 
@@ -506,6 +550,8 @@ def main_ours(args):
         extras["batch"] = batch_section(args, 3)
         torch.cuda.empty_cache()
         extras["tensor_core_stages"] = gemm_section(args)
+        torch.cuda.empty_cache()
+        extras["permutation_and_reductions"] = aux_section(n)
     cpu = None
     if rank == 0 and world == 1 and not args.no_extras:
         cpu = run_cpu_sample(args.sample_seconds)
