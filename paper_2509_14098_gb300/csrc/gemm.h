@@ -32,7 +32,7 @@ struct GemmStage {
     uint32_t nvar;          // camp_bits + ncol_bits chunk-varying bits
     uint32_t ncol_bits;     // log2 columns per tile: 7, fewer only for states with n < keff + 7
                             // (the MMA rows beyond the columns are zero and never stored)
-    uint32_t pad;
+    uint32_t nslot;         // operand ring depth (A slots, with their B chunks when streamed)
     uint64_t b_off;         // byte offset of this stage's B chunks in the blob
     uint8_t glob_pos[kMaxQ];
     uint8_t local_pos[8];   // physical positions of the local bits, ascending

@@ -186,6 +186,10 @@ std::string plan_gemm(const Plan& P, const double* params, int prec, GemmProgram
         st.b_chunk_bytes = (uint32_t)(2 * block);
         // B stays in shared memory when it fits beside the two A slots (k = 6)
         st.resident = ((size_t)st.nchunk * st.b_chunk_bytes + 2 * 32768 <= 192 * 1024) ? 1u : 0u;
+        // ring depth: three slots when they fit in 224 KiB with the resident B, else two
+        const size_t slot = 32768 + (st.resident ? 0 : (size_t)st.b_chunk_bytes);
+        const size_t fixed = 1024 + (st.resident ? (size_t)st.nchunk * st.b_chunk_bytes : 0);
+        st.nslot = (fixed + 3 * slot <= 224 * 1024) ? 3u : 2u;
         st.b_off = (uint64_t)((out->ublob.size() + 1023) & ~(size_t)1023);
         out->ublob.resize(st.b_off + (size_t)st.nchunk * st.b_chunk_bytes, 0);
         uint8_t* base = out->ublob.data() + st.b_off;
