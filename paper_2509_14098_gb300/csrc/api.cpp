@@ -255,9 +255,11 @@ static sv_status do_permute(sv_handle h, const uint32_t* phys_of_qubit) {
 struct PauliPlan {
     std::vector<svk::PauliSweep> sweeps;
     std::vector<svk::PauliTerm> terms;
-    int R = 4;
 };
 
+// Split the observable into sweeps: each sweep's tile holds the L lowest physical bits
+// and the X / Y qubits of its terms; the diagonal terms go to sweep 0.  Within a sweep
+// the register bits are the tile qubits that carry X / Y most often.
 static sv_status plan_pauli(sv_handle h, const sv_observable* obs, const std::vector<int>& where,
                             PauliPlan* out) {
     const int n = (int)h->n;
@@ -278,64 +280,110 @@ static sv_status plan_pauli(sv_handle h, const sv_observable* obs, const std::ve
         }
         double fr = obs->coeff[t], fi = 0;   // coeff * i^ny
         for (int k = 0; k < (ny & 3); ++k) { double r = -fi, i2 = fr; fr = r; fi = i2; }
+        if (__builtin_popcountll(x & z) & 1) { fr = -fr; fi = -fi; }   // (-1)^{|x & z|}
         (x ? off : diag).push_back(Raw{x, z, fr, fi});
     }
-    const int c = std::min(4, n);
-    const int Tp = std::min(n, 12);
-    out->R = std::min(4, Tp);
+    const int T = std::min(n, 12);
+    const int R = std::min(h->eb == 8 ? 4 : 3, T);
+    const int L = std::min(4, T - R);
     std::vector<char> used(off.size(), 0);
     size_t left = off.size();
     bool first = true;
     while (first || left) {
-        uint64_t tile = (1ull << c) - 1;
+        uint64_t tile = (1ull << L) - 1;
         for (size_t i = 0; i < off.size(); ++i)
-            if (!used[i] && __builtin_popcountll(tile | off[i].x) <= Tp) tile |= off[i].x;
-        for (int p = 0; p < n && __builtin_popcountll(tile) < Tp; ++p) tile |= 1ull << p;
-        if (!first) {
-            bool any = false;
-            for (size_t i = 0; i < off.size(); ++i)
-                if (!used[i] && (off[i].x & ~tile) == 0) any = true;
-            if (!any) return fail(SV_ERR_UNSUPPORTED, "a Pauli term has X/Y on more qubits than a tile holds");
-        }
+            if (!used[i] && __builtin_popcountll(tile | off[i].x) <= T) tile |= off[i].x;
+        for (int p = 0; p < n && __builtin_popcountll(tile) < T; ++p) tile |= 1ull << p;
+        std::vector<size_t> mine;
+        for (size_t i = 0; i < off.size(); ++i)
+            if (!used[i] && (off[i].x & ~tile) == 0) mine.push_back(i);
+        if (!first && mine.empty())
+            return fail(SV_ERR_UNSUPPORTED, "a Pauli term has X/Y on more qubits than a tile holds");
+        // register bits: the non-low tile qubits with the most X / Y among this sweep's terms
+        std::vector<int> cand;
+        for (int p = L; p < n; ++p)
+            if ((tile >> p) & 1) cand.push_back(p);
+        std::vector<int> cnt(n, 0);
+        for (size_t i : mine)
+            for (uint64_t m = off[i].x; m; m &= m - 1) cnt[__builtin_ctzll(m)]++;
+        std::vector<int> byc = cand;
+        std::stable_sort(byc.begin(), byc.end(), [&](int u, int v) { return cnt[u] > cnt[v]; });
+        std::vector<int> reg(byc.begin(), byc.begin() + R);
+        std::sort(reg.begin(), reg.end());
+        std::vector<int> pos;
+        for (int p = 0; p < L; ++p) pos.push_back(p);
+        for (int p : reg) pos.push_back(p);
+        for (int p : cand)
+            if (std::find(reg.begin(), reg.end(), p) == reg.end()) pos.push_back(p);
         svk::PauliSweep sw;
         std::memset(&sw, 0, sizeof(sw));
-        sw.T = (uint32_t)Tp;
-        int nt = 0, ng = 0;
+        sw.T = (uint32_t)T;
+        sw.R = (uint32_t)R;
+        sw.L = (uint32_t)L;
         int tidx[64];
-        for (int p = 0; p < n; ++p) {
-            if ((tile >> p) & 1) {
-                tidx[p] = nt;
-                sw.tile_pos[nt] = (uint8_t)p;
-                sw.ptile[nt] = 1ull << p;
-                sw.swbit[nt] = svk::swizzle(1u << nt, h->eb);
-                ++nt;
-            } else {
-                tidx[p] = -1;
-                sw.glob_pos[ng++] = (uint8_t)p;
-            }
+        for (int p = 0; p < 64; ++p) tidx[p] = -1;
+        for (int b = 0; b < T; ++b) {
+            tidx[pos[b]] = b;
+            sw.ptile[b] = 1ull << pos[b];
         }
+        int ng = 0;
+        for (int p = 0; p < n; ++p)
+            if (tidx[p] < 0) sw.glob_pos[ng++] = (uint8_t)p;
         sw.n_glob = (uint32_t)ng;
         sw.term_off = (uint32_t)out->terms.size();
-        auto add = [&](const Raw& r) {
+        const uint32_t regmask = ((1u << R) - 1u) << L;
+        auto add = [&](const Raw& r, uint32_t flags) {
             svk::PauliTerm pt;
             std::memset(&pt, 0, sizeof(pt));
             pt.zmask = r.z;
-            pt.xmask = r.x;
             for (uint64_t m = r.x; m; m &= m - 1) pt.xtile |= 1u << tidx[__builtin_ctzll(m)];
-            for (int j = 0; j < out->R; ++j)
-                if ((r.z >> sw.tile_pos[j]) & 1) pt.zreg |= 1u << j;
+            pt.xreg = (uint16_t)((pt.xtile & regmask) >> L);
+            for (int j = 0; j < R; ++j)
+                if ((r.z >> pos[L + j]) & 1) pt.zreg |= (uint16_t)(1u << j);
+            for (int k = 0; k < (1 << R); ++k)
+                if (__builtin_popcount((unsigned)k & pt.zreg) & 1) pt.smask |= 1u << k;
+            if (pt.xtile & ~regmask) flags |= svk::PT_SMEM;
+            if (r.fim == 0.0) flags |= svk::PT_REAL;
+            pt.flags = flags;
             pt.fre = r.fre;
             pt.fim = r.fim;
+            pt.fre32 = (float)r.fre;
+            pt.fim32 = (float)r.fim;
             out->terms.push_back(pt);
         };
-        if (first)
-            for (auto& r : diag) add(r);
-        for (size_t i = 0; i < off.size(); ++i)
-            if (!used[i] && (off[i].x & ~tile) == 0) {
-                add(off[i]);
-                used[i] = 1;
-                --left;
+        if (first) {
+            // diagonal terms: Z on tile bits only, on global bits only, on both; the
+            // first and last classes grouped by their register-bit Z mask (one
+            // 2^R-wide update per group)
+            std::vector<size_t> cls[3];
+            for (size_t i = 0; i < diag.size(); ++i) {
+                const uint64_t zt = diag[i].z & tile, zg = diag[i].z & ~tile;
+                cls[zg == 0 ? 0 : (zt == 0 ? 1 : 2)].push_back(i);
             }
+            auto zreg_of = [&](size_t i) {
+                uint32_t zr = 0;
+                for (int j = 0; j < R; ++j)
+                    if ((diag[i].z >> pos[L + j]) & 1) zr |= 1u << j;
+                return zr;
+            };
+            for (int c = 0; c < 3; ++c) {
+                auto& v = cls[c];
+                if (c != 1)
+                    std::stable_sort(v.begin(), v.end(), [&](size_t u, size_t w) { return zreg_of(u) < zreg_of(w); });
+                for (size_t j = 0; j < v.size(); ++j) {
+                    const bool flush = c != 1 && (j + 1 == v.size() || zreg_of(v[j + 1]) != zreg_of(v[j]));
+                    add(diag[v[j]], flush ? svk::PT_FLUSH : 0u);
+                }
+            }
+            sw.n_dstat = (uint32_t)cls[0].size();
+            sw.n_dglob = (uint32_t)cls[1].size();
+            sw.n_dmix = (uint32_t)cls[2].size();
+        }
+        for (size_t i : mine) {
+            add(off[i], 0u);
+            used[i] = 1;
+            --left;
+        }
         sw.n_terms = (uint32_t)(out->terms.size() - sw.term_off);
         out->sweeps.push_back(sw);
         first = false;
@@ -354,26 +402,30 @@ static sv_status run_pauli(sv_handle h, const PauliPlan& pp, void* lam) {
     std::memcpy(h->aux_host.data(), pp.sweeps.data(), pp.sweeps.size() * sizeof(svk::PauliSweep));
     std::memcpy(h->aux_host.data() + szs, pp.terms.data(), pp.terms.size() * sizeof(svk::PauliTerm));
     SV_CUDA(cudaMemcpyAsync(h->aux.p, h->aux_host.data(), szs + szt, cudaMemcpyHostToDevice, h->stream));
-    uint64_t total_blocks = 0;
-    for (auto& sw : pp.sweeps) total_blocks += 1ull << (n - (int)sw.T);
-    SV_CUDA(h->red.ensure((total_blocks + 16) * sizeof(double)));
+    uint64_t total_rows = 0;
+    for (auto& sw : pp.sweeps) {
+        const uint32_t g = svk::pauli_grid(h->eb, (int)sw.T, (int)sw.R, 1ull << (n - (int)sw.T));
+        if (!g) SV_CUDA(cudaGetLastError());
+        total_rows += g;
+    }
+    SV_CUDA(h->red.ensure((total_rows + 16) * sizeof(double)));
     double* part = (double*)h->red.p + 16;
     uint64_t off = 0;
     for (size_t i = 0; i < pp.sweeps.size(); ++i) {
-        const int T = (int)pp.sweeps[i].T;
-        const uint64_t nt = 1ull << (n - T);
+        const svk::PauliSweep& sw = pp.sweeps[i];
+        const uint64_t nt = 1ull << (n - (int)sw.T);
+        uint32_t grid = 0;
         cudaEvent_t t0 = tick(h);
-        SV_CUDA(svk::launch_pauli(h->eb, pp.R, h->psi, lam, i > 0,
-                                  (const svk::PauliSweep*)h->aux.p + i,
-                                  (const svk::PauliTerm*)((uint8_t*)h->aux.p + szs), part + off, T, nt,
+        SV_CUDA(svk::launch_pauli(h->eb, h->psi, lam, i > 0, sw, (const svk::PauliSweep*)h->aux.p + i,
+                                  (const svk::PauliTerm*)((uint8_t*)h->aux.p + szs), part + off, nt, &grid,
                                   h->stream));
         tock(h, t0, TK_OBS);
-        off += nt;
+        off += grid;
         h->info.reduction_sweeps += 1;
         h->info.kernel_launches += 1;
         h->info.hbm_bytes += (double)state_bytes(h) * (lam ? (i ? 3.0 : 2.0) : 1.0);
     }
-    SV_CUDA(svk::launch_reduce_rows(part, total_blocks, 1, (double*)h->red.p, h->stream));
+    SV_CUDA(svk::launch_reduce_rows(part, off, 1, (double*)h->red.p, h->stream));
     h->info.kernel_launches += 1;
     return SV_OK;
 }

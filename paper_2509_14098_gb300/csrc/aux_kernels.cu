@@ -77,196 +77,393 @@ cudaError_t launch_permute(int elem_bytes, const void* in, void* out, const Perm
 }
 
 // ---------------------------------------------------------------------------
-// Pauli sweep.  Thread holds 2^R consecutive tile elements (register bits = tile bits
-// 0..R-1); (P psi)_x = f * (-1)^{parity((x ^ xmask) & zmask)} psi_{x ^ xmask}.
+// Pauli sweep, (P psi)_x = f (-1)^{parity(x & zmask)} psi_{x ^ xmask} with f carrying
+// the coefficient, i^{#Y} and (-1)^{parity(xmask & zmask)}.  Persistent CTAs stage
+// their tiles in shared memory two at a time (the next tile's copy is in flight while
+// the current one is evaluated); a thread's 2^R register elements sit on the tile bits
+// the host chose for the sweep's X / Y qubits, so most partners are in registers, the
+// others are read from the staged tile.  lambda is written from registers: for each
+// element index the lanes of a warp cover 2^L-amplitude runs.
 // ---------------------------------------------------------------------------
-template <typename C, typename Real, int R, int XT>
-__device__ __forceinline__ void pauli_reg_partner(const C (&a)[1 << R], C (&o)[1 << R], C f, int par0,
-                                                  uint32_t zr) {
+__device__ __forceinline__ float fmaf_t(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmaf_t(double a, double b, double c) { return fma(a, b, c); }
+
+// one term, read as three 16-byte words
+// (complex64 sweeps read the FP32 copy of the coefficient: no FP64 conversion per term)
+template <typename Real>
+struct PTermR {
+    uint64_t zmask;
+    uint32_t xtile, flags, xreg, zreg, smask;
+    Real fre, fim;
+};
+template <typename Real>
+__device__ __forceinline__ PTermR<Real> load_term(const PauliTerm* __restrict__ t) {
+    const uint4* q = reinterpret_cast<const uint4*>(t);
+    const uint4 q0 = __ldg(q), q1 = __ldg(q + 1);
+    PTermR<Real> r;
+    r.zmask = (uint64_t)q0.x | ((uint64_t)q0.y << 32);
+    r.xtile = q0.z;
+    r.flags = q0.w;
+    r.xreg = q1.x & 0xFFFFu;
+    r.zreg = q1.x >> 16;
+    r.smask = q1.y;
+    if constexpr (sizeof(Real) == 4) {
+        r.fre = __uint_as_float(q1.z);
+        r.fim = __uint_as_float(q1.w);
+    } else {
+        const uint4 q2 = __ldg(q + 2);
+        r.fre = __hiloint2double((int)q2.y, (int)q2.x);
+        r.fim = __hiloint2double((int)q2.w, (int)q2.z);
+    }
+    return r;
+}
+
+// o[k] += f_k * p_k with f_k = +-(fr + i fi), the sign of element k from bit k of smask
+template <typename C, typename Real, bool REAL, bool SGN>
+__device__ __forceinline__ void pauli_acc(C& o, const C p, Real fr, Real fi, uint32_t smask, int k) {
+    const bool nk = SGN && ((smask >> k) & 1u);
+    const Real gr = nk ? -fr : fr;
+    if (REAL) {
+        o.x = fmaf_t(gr, p.x, o.x);
+        o.y = fmaf_t(gr, p.y, o.y);
+    } else {
+        const Real gi = nk ? -fi : fi;
+        o.x = fmaf_t(gr, p.x, fmaf_t(-gi, p.y, o.x));
+        o.y = fmaf_t(gr, p.y, fmaf_t(gi, p.x, o.y));
+    }
+}
+
+template <typename Real, int R, int XR, bool REAL, bool SGN>
+__device__ __forceinline__ void pauli_reg_v(const typename CT<Real>::C (&a)[1 << R], typename CT<Real>::C (&o)[1 << R],
+                                            Real fr, Real fi, uint32_t smask) {
 #pragma unroll
-    for (int k = 0; k < (1 << R); ++k) {
-        C v = cmul(a[k ^ XT], f);
-        if ((par0 ^ __popc(k & zr)) & 1) { v.x = -v.x; v.y = -v.y; }
-        o[k].x += v.x;
-        o[k].y += v.y;
+    for (int k = 0; k < (1 << R); ++k) pauli_acc<typename CT<Real>::C, Real, REAL, SGN>(o[k], a[k ^ XR], fr, fi, smask, k);
+}
+template <typename Real, int R, int XR>
+__device__ __forceinline__ void pauli_reg(const typename CT<Real>::C (&a)[1 << R], typename CT<Real>::C (&o)[1 << R],
+                                          Real fr, Real fi, uint32_t smask, bool real, bool sgn) {
+    if (real) {
+        if (sgn) pauli_reg_v<Real, R, XR, true, true>(a, o, fr, fi, smask);
+        else pauli_reg_v<Real, R, XR, true, false>(a, o, fr, fi, smask);
+    } else {
+        if (sgn) pauli_reg_v<Real, R, XR, false, true>(a, o, fr, fi, smask);
+        else pauli_reg_v<Real, R, XR, false, false>(a, o, fr, fi, smask);
+    }
+}
+template <typename Real, int R, bool REAL, bool SGN>
+__device__ __forceinline__ void pauli_smem_v(const typename CT<Real>::C* tb, uint32_t xi, int L,
+                                             typename CT<Real>::C (&o)[1 << R], Real fr, Real fi, uint32_t smask) {
+#pragma unroll
+    for (int k = 0; k < (1 << R); ++k)
+        pauli_acc<typename CT<Real>::C, Real, REAL, SGN>(o[k], tb[xi ^ ((uint32_t)k << L)], fr, fi, smask, k);
+}
+
+// Diagonal run [t0, t1): real weights summed per run of equal zreg; a run on register
+// bits is applied to the elements by its sign pattern (o[k] += +-w a[k]), the others
+// add to the element-independent weight wconst.
+template <typename Real, int R, bool TO_O>
+__device__ __forceinline__ void pauli_diag(const PauliTerm* __restrict__ tl, uint32_t t0, uint32_t t1, uint64_t fix,
+                                           typename CT<Real>::C (&o)[1 << R], const typename CT<Real>::C (&a)[1 << R],
+                                           Real (&w)[1 << R], Real& wconst) {
+    Real cacc = 0;
+    for (uint32_t ti = t0; ti < t1; ++ti) {
+        const PTermR<Real> pt = load_term<Real>(tl + ti);
+        cacc += (__popcll(fix & pt.zmask) & 1) ? -pt.fre : pt.fre;
+        if (pt.flags & PT_FLUSH) {
+            if (pt.zreg == 0) {
+                wconst += cacc;
+            } else {
+#pragma unroll
+                for (int k = 0; k < (1 << R); ++k) {
+                    const Real c = ((pt.smask >> k) & 1u) ? -cacc : cacc;
+                    if (TO_O) {
+                        o[k].x = fmaf_t(c, a[k].x, o[k].x);
+                        o[k].y = fmaf_t(c, a[k].y, o[k].y);
+                    } else {
+                        w[k] += c;
+                    }
+                }
+            }
+            cacc = 0;
+        }
     }
 }
 
 template <typename Real, int R>
-__global__ void __launch_bounds__(512) k_pauli(const typename CT<Real>::C* __restrict__ psi,
-                                               typename CT<Real>::C* __restrict__ lam, int accumulate,
-                                               const PauliSweep* __restrict__ sp,
-                                               const PauliTerm* __restrict__ terms,
-                                               double* __restrict__ partial) {
+__global__ void __launch_bounds__(sizeof(Real) == 4 ? 256 : 512, sizeof(Real) == 4 ? 2 : 1) k_pauli(
+    const typename CT<Real>::C* __restrict__ psi, typename CT<Real>::C* __restrict__ lam, int accumulate,
+    const PauliSweep* __restrict__ sp, const PauliTerm* __restrict__ terms, double* __restrict__ partial,
+    uint64_t ntiles) {
     using C = typename CT<Real>::C;
     constexpr int K = 1 << R;
+    constexpr int EPC = 16 / (int)sizeof(C);   // elements per 16-byte copy
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const PauliSweep& sw = *sp;
-    const int T = (int)sw.T;
-    const int TR = T - R;
-    C* tile = reinterpret_cast<C*>(smem_raw);
-    C* tout = tile + (1u << T);
-    double* wsum = reinterpret_cast<double*>(tout + (1u << T));
-    const uint32_t tid = threadIdx.x;
-    const uint64_t base = tile_base(blockIdx.x, sw.glob_pos);
-    tile_load<C, R>(tile, psi, base, sw.ptile, sw.swbit, TR, tid);
-    cp_async_commit_wait_all();
+    __shared__ PauliSweep s_sw;
+    __shared__ uint64_t s_jp[16];   // physical offset of the CTA's j-th copy round
+    __shared__ double s_wsum[16];
+    __shared__ Real s_gc[2];        // global-bit diagonal constant of the current / next tile
+    const uint32_t tid = threadIdx.x, nthr = blockDim.x;
+    for (uint32_t i = tid; i < sizeof(PauliSweep) / 4; i += nthr)
+        reinterpret_cast<uint32_t*>(&s_sw)[i] = reinterpret_cast<const uint32_t*>(sp)[i];
     __syncthreads();
-
-    uint64_t fix = base;
-    uint32_t soff = 0;
-    for (int i = 0; i < TR; ++i)
-        if ((tid >> i) & 1) {
-            fix |= sw.ptile[R + i];
-            soff ^= sw.swbit[R + i];
+    const PauliSweep& sw = s_sw;
+    const int T = (int)sw.T, L = (int)sw.L;
+    const uint32_t telems = 1u << T;
+    C* buf0 = reinterpret_cast<C*>(smem_raw);
+    C* buf1 = buf0 + telems;
+    Real* wtab = reinterpret_cast<Real*>(buf1 + telems);   // static diagonal, [k][thread]
+    auto phys = [&](uint32_t e) -> uint64_t {
+        uint64_t p = 0;
+        for (int b = 0; e; ++b, e >>= 1)
+            if (e & 1) p |= sw.ptile[b];
+        return p;
+    };
+    // copy rounds: chunk c = tid + j * nthr holds tile elements EPC c .. EPC c + EPC - 1
+    const uint32_t rounds = (telems / EPC) / nthr;
+    for (uint32_t j = tid; j < rounds; j += nthr) s_jp[j] = phys(j * nthr * EPC);
+    const uint64_t ld_tid = phys(tid * EPC);
+    // the thread's tile index (register bits zero) and its physical bits
+    const uint32_t te = (tid & ((1u << L) - 1u)) | ((tid >> L) << (L + R));
+    const uint64_t tphys = phys(te);
+    const PauliTerm* __restrict__ tl = terms + sw.term_off;
+    const uint32_t nterms = sw.n_terms, d0 = sw.n_dstat, d1 = d0 + sw.n_dglob, d2 = d1 + sw.n_dmix;
+    {   // diagonal terms on tile bits only: the same for every tile
+        Real w[K], wc = 0;
+        C dummy[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) w[k] = 0;
+        pauli_diag<Real, R, false>(tl, 0, d0, tphys, dummy, dummy, w, wc);
+#pragma unroll
+        for (int k = 0; k < K; ++k) wtab[k * nthr + tid] = w[k] + wc;
+    }
+    // tile bases: the tile index's bits deposited on the global bits; the next tile of
+    // this CTA by a masked add (carries run through the non-global bits set to one)
+    uint64_t gmask = 0, pstep = 0, bcur = 0;
+    for (uint32_t i = 0; i < sw.n_glob; ++i) {
+        const uint64_t b = 1ull << sw.glob_pos[i];
+        gmask |= b;
+        if ((gridDim.x >> i) & 1) pstep |= b;
+        if ((blockIdx.x >> i) & 1) bcur |= b;
+    }
+    auto next_base = [&](uint64_t b) -> uint64_t { return ((b | ~gmask) + pstep) & gmask; };
+    // diagonal terms on global bits only: one constant per tile, summed by warp 0 in a
+    // fixed order (lane-strided partial sums, then a shuffle tree read from lane 0)
+    auto gconst = [&](uint64_t base) -> Real {
+        Real v = 0;
+        for (uint32_t ti = d0 + (tid & 31); ti < d1; ti += 32) {
+            const PTermR<Real> pt = load_term<Real>(tl + ti);
+            const Real c = pt.fre;
+            v += (__popcll(base & pt.zmask) & 1) ? -c : c;
         }
-    uint32_t sr[R];
-#pragma unroll
-    for (int j = 0; j < R; ++j) sr[j] = sw.swbit[j];
-    const bool pairs = sizeof(C) == 8;   // tile bit 0 is register bit 0
-    C a[K], o[K];
-    load_regs<C, C, R>(a, tile, soff, sr, pairs);
-#pragma unroll
-    for (int k = 0; k < K; ++k) o[k].x = o[k].y = 0;
-    Real wd[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) wd[k] = 0;
-    Real wconst = 0;
-    for (uint32_t ti = 0; ti < sw.n_terms; ++ti) {
-        const PauliTerm& pt = terms[sw.term_off + ti];
-        const int par0 = (__popcll(fix & pt.zmask) ^ __popcll(pt.xmask & pt.zmask)) & 1;
-        const uint32_t zr = pt.zreg;
-        if (pt.xmask == 0) {   // diagonal: a real weight per element
-            const Real c = par0 ? -(Real)pt.fre : (Real)pt.fre;
-            if (zr == 0) {
-                wconst += c;
-            } else {
-#pragma unroll
-                for (int k = 0; k < K; ++k) wd[k] += (__popc(k & zr) & 1) ? -c : c;
-            }
-            continue;
-        }
-        const uint32_t xt = pt.xtile;
-        C f;
-        f.x = (Real)pt.fre;
-        f.y = (Real)pt.fim;
-        if (xt == 1) {
-            pauli_reg_partner<C, Real, R, 1>(a, o, f, par0, zr);
-        } else if (R > 1 && xt == 2) {
-            pauli_reg_partner<C, Real, R, (R > 1 ? 2 : 0)>(a, o, f, par0, zr);
-        } else if (R > 2 && xt == 4) {
-            pauli_reg_partner<C, Real, R, (R > 2 ? 4 : 0)>(a, o, f, par0, zr);
-        } else if (R > 3 && xt == 8) {
-            pauli_reg_partner<C, Real, R, (R > 3 ? 8 : 0)>(a, o, f, par0, zr);
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        return v;
+    };
+    auto issue = [&](uint64_t b, C* buf) {
+        b |= ld_tid;
+        for (uint32_t j = 0; j < rounds; ++j) cp_async16(buf + (tid + j * nthr) * EPC, psi + (b | s_jp[j]));
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    const bool has_gc = d1 > d0 && nthr >= 32;
+    // expectation partial over the CTA's tiles: complex64 sweeps sum per tile in FP32
+    // and across tiles with compensated (Kahan) FP32 sums, keeping the slow FP64
+    // pipe out of the tile loop; complex128 sweeps sum in FP64
+    Real esum = 0, ecomp = 0;
+    uint64_t tile = blockIdx.x;
+    uint64_t bnext = next_base(bcur);
+    if (has_gc && tid < 32) {
+        const Real v = gconst(bcur);
+        if (tid == 0) s_gc[0] = v;
+    }
+    if (tile < ntiles) issue(bcur, buf0);
+    for (uint32_t cur = 0; tile < ntiles; tile += gridDim.x, cur ^= 1u) {
+        const bool more = tile + gridDim.x < ntiles;
+        if (more) {
+            issue(bnext, cur ? buf0 : buf1);
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
         } else {
-            uint32_t sx = 0;
-            for (int b = 0; b < T; ++b)
-                if ((xt >> b) & 1) sx ^= sw.swbit[b];
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        }
+        __syncthreads();
+        const C* tb = cur ? buf1 : buf0;
+        const uint64_t fix = bcur | tphys;
+        C a[K], o[K];
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                C v = cmul(tile[reg_addr<C, R>(k, soff, sr) ^ sx], f);
-                if ((par0 ^ __popc(k & zr)) & 1) { v.x = -v.x; v.y = -v.y; }
-                o[k].x += v.x;
-                o[k].y += v.y;
+        for (int k = 0; k < K; ++k) {
+            a[k] = tb[te | ((uint32_t)k << L)];
+            o[k].x = o[k].y = 0;
+        }
+        Real wconst = 0;
+        if (d1 > d0) {
+            if (has_gc) {
+                wconst = s_gc[cur];
+            } else {   // fewer than 32 threads: every thread sums them
+                for (uint32_t ti = d0; ti < d1; ++ti) {
+                    const PTermR<Real> pt = load_term<Real>(tl + ti);
+                    wconst += (__popcll(bcur & pt.zmask) & 1) ? -pt.fre : pt.fre;
+                }
             }
         }
-    }
-    Real e = 0;
+        {
+            Real wnone[K];
+            pauli_diag<Real, R, true>(tl, d1, d2, fix, o, a, wnone, wconst);
+        }
+        for (uint32_t ti = d2; ti < nterms; ++ti) {
+            const PTermR<Real> pt = load_term<Real>(tl + ti);
+            const bool neg = __popcll(fix & pt.zmask) & 1;
+            const Real fr = neg ? -pt.fre : pt.fre, fi = neg ? -pt.fim : pt.fim;
+            const bool real = (pt.flags & PT_REAL) != 0, sgn = pt.zreg != 0;
+            if (pt.flags & PT_SMEM) {
+                const uint32_t xi = te ^ pt.xtile;
+                if (real) {
+                    if (sgn) pauli_smem_v<Real, R, true, true>(tb, xi, L, o, fr, fi, pt.smask);
+                    else pauli_smem_v<Real, R, true, false>(tb, xi, L, o, fr, fi, pt.smask);
+                } else {
+                    if (sgn) pauli_smem_v<Real, R, false, true>(tb, xi, L, o, fr, fi, pt.smask);
+                    else pauli_smem_v<Real, R, false, false>(tb, xi, L, o, fr, fi, pt.smask);
+                }
+                continue;
+            }
+            switch (pt.xreg) {
+#define SVK_PAULI_XR(X) \
+    case X:             \
+        if constexpr ((X) < K) pauli_reg<Real, R, ((X) < K ? (X) : 0)>(a, o, fr, fi, pt.smask, real, sgn); \
+        break;
+                SVK_PAULI_XR(1) SVK_PAULI_XR(2) SVK_PAULI_XR(3) SVK_PAULI_XR(4) SVK_PAULI_XR(5)
+                SVK_PAULI_XR(6) SVK_PAULI_XR(7) SVK_PAULI_XR(8) SVK_PAULI_XR(9) SVK_PAULI_XR(10)
+                SVK_PAULI_XR(11) SVK_PAULI_XR(12) SVK_PAULI_XR(13) SVK_PAULI_XR(14) SVK_PAULI_XR(15)
+#undef SVK_PAULI_XR
+                default: break;
+            }
+        }
+        Real e = 0;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const Real w = wd[k] + wconst;
-        o[k].x += w * a[k].x;
-        o[k].y += w * a[k].y;
-        e += a[k].x * o[k].x + a[k].y * o[k].y;
+        for (int k = 0; k < K; ++k) {
+            const Real w = wconst + wtab[k * nthr + tid];
+            o[k].x = fmaf_t(w, a[k].x, o[k].x);
+            o[k].y = fmaf_t(w, a[k].y, o[k].y);
+            e = fmaf_t(a[k].x, o[k].x, fmaf_t(a[k].y, o[k].y, e));
+        }
+        {
+            const Real y = e - ecomp, t = esum + y;
+            ecomp = (t - esum) - y;
+            esum = t;
+        }
+        if (lam != nullptr) {
+            uint64_t preg[R];
+#pragma unroll
+            for (int j = 0; j < R; ++j) preg[j] = sw.ptile[L + j];
+            auto addr = [&](int k) -> uint64_t {
+                uint64_t p = fix;
+#pragma unroll
+                for (int j = 0; j < R; ++j)
+                    if ((k >> j) & 1) p |= preg[j];
+                return p;
+            };
+            if (accumulate) {
+                C g[K];
+#pragma unroll
+                for (int k = 0; k < K; ++k) g[k] = lam[addr(k)];
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    o[k].x += g[k].x;
+                    o[k].y += g[k].y;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < K; ++k) lam[addr(k)] = o[k];
+        }
+        if (has_gc && more && tid < 32) {   // the next tile's constant, published by the barrier below
+            const Real v = gconst(bnext);
+            if (tid == 0) s_gc[cur ^ 1u] = v;
+        }
+        __syncthreads();   // the buffer is refilled two tiles on
+        bcur = bnext;
+        bnext = next_base(bnext);
     }
-    // expectation partial: FP32 over the thread's 2^R elements, FP64 above, fixed order
-    double ev = (double)e;
-    const uint32_t wmask = blockDim.x >= 32 ? 0xffffffffu : ((1u << blockDim.x) - 1u);
+    // CTA partial: thread sums in FP64, fixed-order warp and CTA reductions
+    double eacc = (double)esum - (double)ecomp;
     for (int off = 16; off > 0; off >>= 1)
-        if ((uint32_t)off < blockDim.x) ev += __shfl_xor_sync(wmask, ev, off);
-    if (lam != nullptr) store_regs<C, C, R>(o, tout, soff, sr, pairs);
-    if ((tid & 31) == 0) wsum[tid >> 5] = ev;
+        if ((uint32_t)off < nthr) eacc += __shfl_xor_sync(nthr >= 32 ? 0xffffffffu : ((1u << nthr) - 1u), eacc, off);
+    if ((tid & 31) == 0) s_wsum[tid >> 5] = eacc;
     __syncthreads();
     if (tid == 0) {
         double s = 0;
-        for (uint32_t w = 0; w < (blockDim.x + 31) / 32; ++w) s += wsum[w];
+        for (uint32_t w = 0; w < (nthr + 31) / 32; ++w) s += s_wsum[w];
         partial[blockIdx.x] = s;
-    }
-    if (lam != nullptr) {
-        constexpr int APC = 16 / (int)sizeof(C);
-        constexpr int LA = APC == 2 ? 1 : 0;
-        constexpr int NCH = K / APC;
-        uint64_t ptid = 0;
-        uint32_t stid = 0;
-        for (int b = 0; b < TR; ++b)
-            if ((tid >> b) & 1) {
-                ptid ^= sw.ptile[b + LA];
-                stid ^= sw.swbit[b + LA];
-            }
-#pragma unroll
-        for (int i = 0; i < NCH; ++i) {
-            uint64_t pi = 0;
-            uint32_t si = 0;
-#pragma unroll
-            for (int b = 0; (1 << b) < NCH; ++b)
-                if ((i >> b) & 1) {
-                    pi ^= sw.ptile[TR + LA + b];
-                    si ^= sw.swbit[TR + LA + b];
-                }
-            float4 v = *reinterpret_cast<const float4*>(tout + (stid ^ si));
-            float4* gp = reinterpret_cast<float4*>(lam + (base | (ptid ^ pi)));
-            if (accumulate) {
-                if (sizeof(C) == 8) {
-                    const float4 g = *gp;
-                    v.x += g.x; v.y += g.y; v.z += g.z; v.w += g.w;
-                } else {
-                    double2 vd = *reinterpret_cast<double2*>(&v);
-                    const double2 g = *reinterpret_cast<const double2*>(gp);
-                    vd.x += g.x; vd.y += g.y;
-                    v = *reinterpret_cast<float4*>(&vd);
-                }
-            }
-            *gp = v;
-        }
     }
 }
 
 template <typename Real, int R>
-static cudaError_t launch_pauli_R(const void* psi, void* lam, bool acc, const PauliSweep* d_sweep,
-                                  const PauliTerm* d_terms, double* partial, int T, uint64_t ntiles,
-                                  cudaStream_t s) {
-    using C = typename CT<Real>::C;
-    const uint32_t nthr = 1u << (T - R);
-    const size_t smem = ((size_t)sizeof(C) << (T + 1)) + ((nthr + 31) / 32) * sizeof(double);
-    static bool cfg = false;
-    if (!cfg) {
-        cudaError_t e = cudaFuncSetAttribute(k_pauli<Real, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        if (e != cudaSuccess) return e;
-        cfg = true;
+struct PauliCfg {
+    // two tile buffers and the static-diagonal table
+    static size_t smem(int T) { return ((size_t)sizeof(typename CT<Real>::C) << (T + 1)) + ((size_t)sizeof(Real) << T); }
+    static uint32_t grid(int T, uint64_t ntiles) {
+        static int per_sm[13] = {0};
+        static int nsm = 0;
+        if (!nsm) {
+            int dev = 0, m = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, dev);
+            // the widest tile's two buffers (the kernel's static shared memory comes on top)
+            if (cudaFuncSetAttribute(k_pauli<Real, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem(12)) !=
+                cudaSuccess)
+                return 0;
+            nsm = m;
+        }
+        if (!per_sm[T]) {
+            int nb = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pauli<Real, R>, 1 << (T - R), smem(T));
+            per_sm[T] = nb > 0 ? nb : 1;
+        }
+        const uint64_t g = (uint64_t)nsm * (uint64_t)per_sm[T];
+        return (uint32_t)(ntiles < g ? ntiles : g);
     }
-    k_pauli<Real, R><<<(unsigned)ntiles, nthr, smem, s>>>((const C*)psi, (C*)lam, acc ? 1 : 0, d_sweep,
-                                                          d_terms, partial);
+};
+
+template <typename Real, int R>
+static cudaError_t launch_pauli_R(const void* psi, void* lam, bool acc, const PauliSweep& hsw,
+                                  const PauliSweep* d_sweep, const PauliTerm* d_terms, double* partial,
+                                  uint64_t ntiles, uint32_t* grid_out, cudaStream_t s) {
+    using C = typename CT<Real>::C;
+    const int T = (int)hsw.T;
+    const uint32_t grid = PauliCfg<Real, R>::grid(T, ntiles);
+    *grid_out = grid;
+    if (grid == 0) return ntiles ? cudaGetLastError() : cudaSuccess;
+    k_pauli<Real, R><<<grid, 1u << (T - R), PauliCfg<Real, R>::smem(T), s>>>(
+        (const C*)psi, (C*)lam, acc ? 1 : 0, d_sweep, d_terms, partial, ntiles);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pauli(int elem_bytes, int R, const void* psi, void* lam, bool accumulate,
-                         const PauliSweep* d_sweep, const PauliTerm* d_terms, double* partial, int T,
-                         uint64_t ntiles, cudaStream_t s) {
-    if (elem_bytes == 8) {
-        switch (R) {
-            case 1: return launch_pauli_R<float, 1>(psi, lam, accumulate, d_sweep, d_terms, partial, T, ntiles, s);
-            case 2: return launch_pauli_R<float, 2>(psi, lam, accumulate, d_sweep, d_terms, partial, T, ntiles, s);
-            case 3: return launch_pauli_R<float, 3>(psi, lam, accumulate, d_sweep, d_terms, partial, T, ntiles, s);
-            case 4: return launch_pauli_R<float, 4>(psi, lam, accumulate, d_sweep, d_terms, partial, T, ntiles, s);
-        }
-    } else {
-        switch (R) {
-            case 1: return launch_pauli_R<double, 1>(psi, lam, accumulate, d_sweep, d_terms, partial, T, ntiles, s);
-            case 2: return launch_pauli_R<double, 2>(psi, lam, accumulate, d_sweep, d_terms, partial, T, ntiles, s);
-            case 3: return launch_pauli_R<double, 3>(psi, lam, accumulate, d_sweep, d_terms, partial, T, ntiles, s);
-            case 4: return launch_pauli_R<double, 4>(psi, lam, accumulate, d_sweep, d_terms, partial, T, ntiles, s);
-        }
+uint32_t pauli_grid(int elem_bytes, int T, int R, uint64_t ntiles) {
+#define SVK_PG(RR) \
+    case RR: return elem_bytes == 8 ? PauliCfg<float, RR>::grid(T, ntiles) : PauliCfg<double, RR>::grid(T, ntiles);
+    switch (R) {
+        SVK_PG(1) SVK_PG(2) SVK_PG(3)
+        case 4: return elem_bytes == 8 ? PauliCfg<float, 4>::grid(T, ntiles) : 0;
     }
+#undef SVK_PG
+    return 0;
+}
+
+cudaError_t launch_pauli(int elem_bytes, const void* psi, void* lam, bool accumulate, const PauliSweep& hsw,
+                         const PauliSweep* d_sweep, const PauliTerm* d_terms, double* partial,
+                         uint64_t ntiles, uint32_t* grid_out, cudaStream_t s) {
+    if (hsw.T < hsw.R || hsw.T > 12 || hsw.T - hsw.R > (elem_bytes == 8 ? 8u : 9u) || hsw.L + hsw.R > hsw.T)
+        return cudaErrorInvalidValue;
+#define SVK_PL(RR)                                                                                           \
+    case RR:                                                                                                 \
+        return elem_bytes == 8                                                                               \
+                   ? launch_pauli_R<float, RR>(psi, lam, accumulate, hsw, d_sweep, d_terms, partial, ntiles, \
+                                               grid_out, s)                                                  \
+                   : launch_pauli_R<double, RR>(psi, lam, accumulate, hsw, d_sweep, d_terms, partial, ntiles, \
+                                                grid_out, s);
+    switch (hsw.R) {
+        SVK_PL(1) SVK_PL(2) SVK_PL(3)
+        case 4:   // complex128 sweeps use at most 3 register bits
+            if (elem_bytes != 8) return cudaErrorInvalidValue;
+            return launch_pauli_R<float, 4>(psi, lam, accumulate, hsw, d_sweep, d_terms, partial, ntiles, grid_out, s);
+    }
+#undef SVK_PL
     return cudaErrorInvalidValue;
 }
 

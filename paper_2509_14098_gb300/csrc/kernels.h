@@ -39,27 +39,45 @@ struct PermDesc {
 cudaError_t launch_permute(int elem_bytes, const void* in, void* out, const PermDesc* d_desc, int T,
                            uint64_t ntiles, cudaStream_t s);
 
-// Pauli-sum sweep.  Terms act on the tile of the sweep; diagonal terms (xmask 0) are
-// evaluated once, in sweep 0.
-struct PauliTerm {
-    uint64_t zmask;        // physical bits carrying Z or Y
-    uint64_t xmask;        // physical bits carrying X or Y
-    uint32_t xtile;        // xmask as a tile-element mask
-    uint32_t zreg;         // zmask restricted to the register bits (tile bits 0..R-1) as a k mask
-    double fre, fim;       // coeff * i^{#Y}
-};
+// Pauli-sum sweep.  A tile fixes the global bits; its T bits are laid out as
+//   tile bits [0, L)       the L lowest physical bits    (thread bits 0..L-1)
+//   tile bits [L, L + R)   register bits                 (element k of a thread)
+//   tile bits [L + R, T)   the remaining tile bits       (thread bits L..)
+// so a thread holds 2^R elements and, for each of them, the lanes of a warp cover
+// 2^L-amplitude runs of consecutive addresses.  Terms act on the tile of their sweep;
+// diagonal terms (no X / Y) are evaluated once, in sweep 0, ordered: Z on tile bits
+// only (n_dstat, folded into a per-thread table once per CTA), Z on global bits only
+// (n_dglob, one constant per tile), Z on both (n_dmix); then the X / Y terms.
 struct PauliSweep {
-    uint32_t T, n_glob, n_terms, term_off;
-    uint8_t glob_pos[kMaxQ];
-    uint8_t tile_pos[16];
-    uint64_t ptile[16];
-    uint32_t swbit[16];
+    uint32_t T, R, L, n_glob;
+    uint32_t n_terms, term_off, n_dstat, n_dglob;
+    uint32_t n_dmix, pad0, pad1, pad2;
+    uint64_t ptile[16];           // physical value of tile bit b
+    uint8_t glob_pos[kMaxQ];      // physical positions of the global bits (ascending)
+};
+enum : uint32_t {
+    PT_SMEM = 1,    // partner outside the thread's registers: read from the staged tile
+    PT_FLUSH = 2,   // diagonal: last term of a run with the same zreg
+    PT_REAL = 4,    // fim == 0
+};
+struct PauliTerm {         // 48 bytes, read as three 16-byte words
+    uint64_t zmask;        // physical bits carrying Z or Y
+    uint32_t xtile;        // bits carrying X or Y as a tile-index mask (0: diagonal)
+    uint32_t flags;        // PT_*
+    uint16_t xreg;         // X / Y register bits, as a mask of the element index k
+    uint16_t zreg;         // Z / Y register bits, as a mask of k
+    uint32_t smask;        // bit k: parity of (k & zreg)
+    float fre32, fim32;    // the coefficient rounded to FP32 (complex64 sweeps)
+    double fre, fim;       // coeff * i^{#Y} * (-1)^{|xmask & zmask|}
 };
 // lam == nullptr: expectation value only.  accumulate: lam += O_sweep psi, else lam =.
-// partial[blockIdx] = sum over the tile of Re(conj(psi) * (O_sweep psi)).
-cudaError_t launch_pauli(int elem_bytes, int R, const void* psi, void* lam, bool accumulate,
-                         const PauliSweep* d_sweep, const PauliTerm* d_terms, double* partial, int T,
-                         uint64_t ntiles, cudaStream_t s);
+// Persistent: *grid_out CTAs each walk a fixed set of tiles and write one partial
+// partial[cta] = sum over its tiles of Re(conj(psi) * (O_sweep psi)).
+cudaError_t launch_pauli(int elem_bytes, const void* psi, void* lam, bool accumulate,
+                         const PauliSweep& hsw, const PauliSweep* d_sweep, const PauliTerm* d_terms,
+                         double* partial, uint64_t ntiles, uint32_t* grid_out, cudaStream_t s);
+// CTAs launch_pauli uses for a sweep with T tile bits and R register bits (its partials)
+uint32_t pauli_grid(int elem_bytes, int T, int R, uint64_t ntiles);
 
 // sum |psi|^2 per block into partial[]; returns the number of blocks used.
 cudaError_t launch_norm(int elem_bytes, const void* psi, uint64_t n_amp, double* partial,
