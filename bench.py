@@ -35,7 +35,7 @@ N_QUBITS, L_BUDGET = 30, 11
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--L", type=int, default=L_BUDGET)
@@ -43,8 +43,9 @@ def parse():
     ap.add_argument("--grad-n", type=int, default=28)
     ap.add_argument("--grad-L", type=int, default=12)
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, grad ratio, batch and CPU baseline")
-    ap.add_argument("--part", default="all", choices=["all", "batch", "gemm"],
-                    help="batch / gemm: only that section (for profiling)")
+    ap.add_argument("--part", default="all", choices=["all", "batch", "gemm", "aux"],
+                    help="batch / gemm / aux: only that section (for profiling)")
+    ap.add_argument("--aux-n", type=int, default=N_QUBITS, help="state width of the aux section")
     ap.add_argument("--gemm-n", type=int, default=32)
     ap.add_argument("--gemm-k", default="5,6,7")
     ap.add_argument("--gemm-prec", default="1,2", help="1 = TF32x3, 2 = BF16x3")
@@ -114,10 +115,17 @@ class Clocks:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+
+    def sampling(self):
+        """True once the sampler has written its first row (or cannot run)."""
+        if self.proc is None:
+            return True
+        self.f.flush()
+        return os.path.getsize(self.f.name) > 0
 
     def stop(self):
         if self.proc is None:
@@ -416,6 +424,11 @@ def main_ours(args):
         if rank == 0:
             print(json.dumps({"part": "gemm", "gemm": r}))
         return
+    if args.part == "aux":
+        r = aux_section(args.aux_n)
+        if rank == 0:
+            print(json.dumps({"part": "aux", "aux": r}))
+        return
     n, L = args.n, args.L
     circ = C.qft_roundtrip(n)
     gen = torch.Generator(device=dev)
@@ -445,6 +458,11 @@ def main_ours(args):
     barrier(pg)
     clocks = Clocks(local)
     clocks.start()
+    t_wait = time.perf_counter()
+    while not clocks.sampling() and time.perf_counter() - t_wait < 5.0:   # untimed: the sampler starts under load
+        step()
+    torch.cuda.synchronize()
+    barrier(pg)
     st.timing(True)
     st.timing(reset=True)
     e0 = torch.cuda.Event(enable_timing=True)

@@ -284,8 +284,8 @@ static sv_status plan_pauli(sv_handle h, const sv_observable* obs, const std::ve
         (x ? off : diag).push_back(Raw{x, z, fr, fi});
     }
     const int T = std::min(n, 12);
-    const int R = std::min(h->eb == 8 ? 4 : 3, T);
-    const int L = std::min(4, T - R);
+    const int L = std::min(4, T - 1);
+    const int R = std::min(h->eb == 8 ? 4 : 3, T - L);
     std::vector<char> used(off.size(), 0);
     size_t left = off.size();
     bool first = true;
@@ -344,6 +344,9 @@ static sv_status plan_pauli(sv_handle h, const sv_observable* obs, const std::ve
                 if (__builtin_popcount((unsigned)k & pt.zreg) & 1) pt.smask |= 1u << k;
             if (pt.xtile & ~regmask) flags |= svk::PT_SMEM;
             if (r.fim == 0.0) flags |= svk::PT_REAL;
+            uint64_t regphys = 0;
+            for (int j = 0; j < R; ++j) regphys |= 1ull << pos[L + j];
+            if ((r.z & ~regphys) == 0) flags |= svk::PT_NOZ;
             pt.flags = flags;
             pt.fre = r.fre;
             pt.fim = r.fim;
@@ -404,8 +407,11 @@ static sv_status run_pauli(sv_handle h, const PauliPlan& pp, void* lam) {
     SV_CUDA(cudaMemcpyAsync(h->aux.p, h->aux_host.data(), szs + szt, cudaMemcpyHostToDevice, h->stream));
     uint64_t total_rows = 0;
     for (auto& sw : pp.sweeps) {
-        const uint32_t g = svk::pauli_grid(h->eb, (int)sw.T, (int)sw.R, 1ull << (n - (int)sw.T));
-        if (!g) SV_CUDA(cudaGetLastError());
+        const uint32_t g = svk::pauli_grid(h->eb, sw, 1ull << (n - (int)sw.T));
+        if (!g) {
+            const cudaError_t e = cudaGetLastError();
+            SV_CUDA(e != cudaSuccess ? e : cudaErrorInvalidValue);
+        }
         total_rows += g;
     }
     SV_CUDA(h->red.ensure((total_rows + 16) * sizeof(double)));

@@ -150,12 +150,16 @@ __device__ __forceinline__ void pauli_reg(const typename CT<Real>::C (&a)[1 << R
         else pauli_reg_v<Real, R, XR, false, false>(a, o, fr, fi, smask);
     }
 }
-template <typename Real, int R, bool REAL, bool SGN>
+// partner of element k at tile index xi ^ (k << L); with no X / Y on the register bits
+// (XR0) the partners sit at compile-time offsets from tb + xi
+template <typename Real, int R, bool REAL, bool SGN, bool XR0>
 __device__ __forceinline__ void pauli_smem_v(const typename CT<Real>::C* tb, uint32_t xi, int L,
                                              typename CT<Real>::C (&o)[1 << R], Real fr, Real fi, uint32_t smask) {
+    const typename CT<Real>::C* pb = tb + xi;
 #pragma unroll
     for (int k = 0; k < (1 << R); ++k)
-        pauli_acc<typename CT<Real>::C, Real, REAL, SGN>(o[k], tb[xi ^ ((uint32_t)k << L)], fr, fi, smask, k);
+        pauli_acc<typename CT<Real>::C, Real, REAL, SGN>(o[k], XR0 ? pb[(uint32_t)k << L] : tb[xi ^ ((uint32_t)k << L)],
+                                                          fr, fi, smask, k);
 }
 
 // Diagonal run [t0, t1): real weights summed per run of equal zreg; a run on register
@@ -189,7 +193,9 @@ __device__ __forceinline__ void pauli_diag(const PauliTerm* __restrict__ tl, uin
     }
 }
 
-template <typename Real, int R>
+// L4: the tile's low part is 4 bits (every state of 5 or more qubits); otherwise L is
+// read from the sweep (tiny states, one register bit)
+template <typename Real, int R, bool L4>
 __global__ void __launch_bounds__(sizeof(Real) == 4 ? 256 : 512, sizeof(Real) == 4 ? 2 : 1) k_pauli(
     const typename CT<Real>::C* __restrict__ psi, typename CT<Real>::C* __restrict__ lam, int accumulate,
     const PauliSweep* __restrict__ sp, const PauliTerm* __restrict__ terms, double* __restrict__ partial,
@@ -207,11 +213,13 @@ __global__ void __launch_bounds__(sizeof(Real) == 4 ? 256 : 512, sizeof(Real) ==
         reinterpret_cast<uint32_t*>(&s_sw)[i] = reinterpret_cast<const uint32_t*>(sp)[i];
     __syncthreads();
     const PauliSweep& sw = s_sw;
-    const int T = (int)sw.T, L = (int)sw.L;
+    const int T = (int)sw.T, L = L4 ? 4 : (int)sw.L;
     const uint32_t telems = 1u << T;
     C* buf0 = reinterpret_cast<C*>(smem_raw);
     C* buf1 = buf0 + telems;
-    Real* wtab = reinterpret_cast<Real*>(buf1 + telems);   // static diagonal, [k][thread]
+    // static diagonal, [k][thread] with a fixed row stride (the widest CTA)
+    constexpr uint32_t WS = sizeof(Real) == 4 ? 256 : 512;
+    Real* wtab = reinterpret_cast<Real*>(buf1 + telems);
     auto phys = [&](uint32_t e) -> uint64_t {
         uint64_t p = 0;
         for (int b = 0; e; ++b, e >>= 1)
@@ -234,7 +242,7 @@ __global__ void __launch_bounds__(sizeof(Real) == 4 ? 256 : 512, sizeof(Real) ==
         for (int k = 0; k < K; ++k) w[k] = 0;
         pauli_diag<Real, R, false>(tl, 0, d0, tphys, dummy, dummy, w, wc);
 #pragma unroll
-        for (int k = 0; k < K; ++k) wtab[k * nthr + tid] = w[k] + wc;
+        for (int k = 0; k < K; ++k) wtab[k * WS + tid] = w[k] + wc;
     }
     // tile bases: the tile index's bits deposited on the global bits; the next tile of
     // this CTA by a masked add (carries run through the non-global bits set to one)
@@ -309,17 +317,22 @@ __global__ void __launch_bounds__(sizeof(Real) == 4 ? 256 : 512, sizeof(Real) ==
         }
         for (uint32_t ti = d2; ti < nterms; ++ti) {
             const PTermR<Real> pt = load_term<Real>(tl + ti);
-            const bool neg = __popcll(fix & pt.zmask) & 1;
+            const bool neg = !(pt.flags & PT_NOZ) && (__popcll(fix & pt.zmask) & 1);
             const Real fr = neg ? -pt.fre : pt.fre, fi = neg ? -pt.fim : pt.fim;
             const bool real = (pt.flags & PT_REAL) != 0, sgn = pt.zreg != 0;
             if (pt.flags & PT_SMEM) {
                 const uint32_t xi = te ^ pt.xtile;
-                if (real) {
-                    if (sgn) pauli_smem_v<Real, R, true, true>(tb, xi, L, o, fr, fi, pt.smask);
-                    else pauli_smem_v<Real, R, true, false>(tb, xi, L, o, fr, fi, pt.smask);
+                if (pt.xreg == 0) {
+                    if (real) {
+                        if (sgn) pauli_smem_v<Real, R, true, true, true>(tb, xi, L, o, fr, fi, pt.smask);
+                        else pauli_smem_v<Real, R, true, false, true>(tb, xi, L, o, fr, fi, pt.smask);
+                    } else {
+                        if (sgn) pauli_smem_v<Real, R, false, true, true>(tb, xi, L, o, fr, fi, pt.smask);
+                        else pauli_smem_v<Real, R, false, false, true>(tb, xi, L, o, fr, fi, pt.smask);
+                    }
                 } else {
-                    if (sgn) pauli_smem_v<Real, R, false, true>(tb, xi, L, o, fr, fi, pt.smask);
-                    else pauli_smem_v<Real, R, false, false>(tb, xi, L, o, fr, fi, pt.smask);
+                    if (real) pauli_smem_v<Real, R, true, true, false>(tb, xi, L, o, fr, fi, sgn ? pt.smask : 0u);
+                    else pauli_smem_v<Real, R, false, true, false>(tb, xi, L, o, fr, fi, sgn ? pt.smask : 0u);
                 }
                 continue;
             }
@@ -338,7 +351,7 @@ __global__ void __launch_bounds__(sizeof(Real) == 4 ? 256 : 512, sizeof(Real) ==
         Real e = 0;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            const Real w = wconst + wtab[k * nthr + tid];
+            const Real w = wconst + wtab[k * WS + tid];
             o[k].x = fmaf_t(w, a[k].x, o[k].x);
             o[k].y = fmaf_t(w, a[k].y, o[k].y);
             e = fmaf_t(a[k].x, o[k].x, fmaf_t(a[k].y, o[k].y, e));
@@ -393,10 +406,12 @@ __global__ void __launch_bounds__(sizeof(Real) == 4 ? 256 : 512, sizeof(Real) ==
     }
 }
 
-template <typename Real, int R>
+template <typename Real, int R, bool L4>
 struct PauliCfg {
     // two tile buffers and the static-diagonal table
-    static size_t smem(int T) { return ((size_t)sizeof(typename CT<Real>::C) << (T + 1)) + ((size_t)sizeof(Real) << T); }
+    static size_t smem(int T) {
+        return ((size_t)sizeof(typename CT<Real>::C) << (T + 1)) + (size_t)sizeof(Real) * (1u << R) * (sizeof(Real) == 4 ? 256 : 512);
+    }
     static uint32_t grid(int T, uint64_t ntiles) {
         static int per_sm[13] = {0};
         static int nsm = 0;
@@ -405,66 +420,69 @@ struct PauliCfg {
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, dev);
             // the widest tile's two buffers (the kernel's static shared memory comes on top)
-            if (cudaFuncSetAttribute(k_pauli<Real, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem(12)) !=
+            if (cudaFuncSetAttribute(k_pauli<Real, R, L4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem(12)) !=
                 cudaSuccess)
                 return 0;
             nsm = m;
         }
         if (!per_sm[T]) {
             int nb = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pauli<Real, R>, 1 << (T - R), smem(T));
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pauli<Real, R, L4>, 1 << (T - R), smem(T));
             per_sm[T] = nb > 0 ? nb : 1;
         }
         const uint64_t g = (uint64_t)nsm * (uint64_t)per_sm[T];
         return (uint32_t)(ntiles < g ? ntiles : g);
     }
+    static cudaError_t launch(const void* psi, void* lam, bool acc, const PauliSweep& hsw, const PauliSweep* d_sweep,
+                              const PauliTerm* d_terms, double* partial, uint64_t ntiles, uint32_t* grid_out,
+                              cudaStream_t s) {
+        using C = typename CT<Real>::C;
+        const int T = (int)hsw.T;
+        const uint32_t g = grid(T, ntiles);
+        *grid_out = g;
+        if (g == 0) return ntiles ? cudaGetLastError() : cudaSuccess;
+        k_pauli<Real, R, L4><<<g, 1u << (T - R), smem(T), s>>>((const C*)psi, (C*)lam, acc ? 1 : 0, d_sweep, d_terms,
+                                                                partial, ntiles);
+        return cudaGetLastError();
+    }
 };
 
-template <typename Real, int R>
-static cudaError_t launch_pauli_R(const void* psi, void* lam, bool acc, const PauliSweep& hsw,
-                                  const PauliSweep* d_sweep, const PauliTerm* d_terms, double* partial,
-                                  uint64_t ntiles, uint32_t* grid_out, cudaStream_t s) {
-    using C = typename CT<Real>::C;
-    const int T = (int)hsw.T;
-    const uint32_t grid = PauliCfg<Real, R>::grid(T, ntiles);
-    *grid_out = grid;
-    if (grid == 0) return ntiles ? cudaGetLastError() : cudaSuccess;
-    k_pauli<Real, R><<<grid, 1u << (T - R), PauliCfg<Real, R>::smem(T), s>>>(
-        (const C*)psi, (C*)lam, acc ? 1 : 0, d_sweep, d_terms, partial, ntiles);
-    return cudaGetLastError();
+// the kernel instance of a sweep: (R, L == 4) with R <= 4 (complex64) or 3 (complex128);
+// L < 4 only with one register bit
+template <typename Real, typename F>
+static auto pauli_dispatch(const PauliSweep& sw, F&& f) {
+    if (sw.L != 4) return f(PauliCfg<Real, 1, false>{});
+    switch (sw.R) {
+        case 1: return f(PauliCfg<Real, 1, true>{});
+        case 2: return f(PauliCfg<Real, 2, true>{});
+        default: return f(PauliCfg<Real, 3, true>{});
+        case 4:
+            if constexpr (sizeof(Real) == 4) return f(PauliCfg<Real, 4, true>{});
+            else return f(PauliCfg<Real, 3, true>{});
+    }
 }
 
-uint32_t pauli_grid(int elem_bytes, int T, int R, uint64_t ntiles) {
-#define SVK_PG(RR) \
-    case RR: return elem_bytes == 8 ? PauliCfg<float, RR>::grid(T, ntiles) : PauliCfg<double, RR>::grid(T, ntiles);
-    switch (R) {
-        SVK_PG(1) SVK_PG(2) SVK_PG(3)
-        case 4: return elem_bytes == 8 ? PauliCfg<float, 4>::grid(T, ntiles) : 0;
-    }
-#undef SVK_PG
-    return 0;
+static bool pauli_shape_ok(int elem_bytes, const PauliSweep& sw) {
+    const uint32_t rmax = elem_bytes == 8 ? 4u : 3u;
+    if (sw.R < 1 || sw.R > rmax || sw.T > 12 || sw.L + sw.R > sw.T) return false;
+    if (sw.T - sw.R > (elem_bytes == 8 ? 8u : 9u)) return false;
+    return sw.L == 4 || sw.R == 1;
+}
+
+uint32_t pauli_grid(int elem_bytes, const PauliSweep& sw, uint64_t ntiles) {
+    if (!pauli_shape_ok(elem_bytes, sw)) return 0;
+    auto f = [&](auto cfg) { return decltype(cfg)::grid((int)sw.T, ntiles); };
+    return elem_bytes == 8 ? pauli_dispatch<float>(sw, f) : pauli_dispatch<double>(sw, f);
 }
 
 cudaError_t launch_pauli(int elem_bytes, const void* psi, void* lam, bool accumulate, const PauliSweep& hsw,
                          const PauliSweep* d_sweep, const PauliTerm* d_terms, double* partial,
                          uint64_t ntiles, uint32_t* grid_out, cudaStream_t s) {
-    if (hsw.T < hsw.R || hsw.T > 12 || hsw.T - hsw.R > (elem_bytes == 8 ? 8u : 9u) || hsw.L + hsw.R > hsw.T)
-        return cudaErrorInvalidValue;
-#define SVK_PL(RR)                                                                                           \
-    case RR:                                                                                                 \
-        return elem_bytes == 8                                                                               \
-                   ? launch_pauli_R<float, RR>(psi, lam, accumulate, hsw, d_sweep, d_terms, partial, ntiles, \
-                                               grid_out, s)                                                  \
-                   : launch_pauli_R<double, RR>(psi, lam, accumulate, hsw, d_sweep, d_terms, partial, ntiles, \
-                                                grid_out, s);
-    switch (hsw.R) {
-        SVK_PL(1) SVK_PL(2) SVK_PL(3)
-        case 4:   // complex128 sweeps use at most 3 register bits
-            if (elem_bytes != 8) return cudaErrorInvalidValue;
-            return launch_pauli_R<float, 4>(psi, lam, accumulate, hsw, d_sweep, d_terms, partial, ntiles, grid_out, s);
-    }
-#undef SVK_PL
-    return cudaErrorInvalidValue;
+    if (!pauli_shape_ok(elem_bytes, hsw)) return cudaErrorInvalidValue;
+    auto f = [&](auto cfg) {
+        return decltype(cfg)::launch(psi, lam, accumulate, hsw, d_sweep, d_terms, partial, ntiles, grid_out, s);
+    };
+    return elem_bytes == 8 ? pauli_dispatch<float>(hsw, f) : pauli_dispatch<double>(hsw, f);
 }
 
 // ---------------------------------------------------------------------------

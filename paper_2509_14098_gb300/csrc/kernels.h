@@ -59,6 +59,7 @@ enum : uint32_t {
     PT_SMEM = 1,    // partner outside the thread's registers: read from the staged tile
     PT_FLUSH = 2,   // diagonal: last term of a run with the same zreg
     PT_REAL = 4,    // fim == 0
+    PT_NOZ = 8,     // no Z / Y outside the register bits: no per-thread sign
 };
 struct PauliTerm {         // 48 bytes, read as three 16-byte words
     uint64_t zmask;        // physical bits carrying Z or Y
@@ -76,8 +77,8 @@ struct PauliTerm {         // 48 bytes, read as three 16-byte words
 cudaError_t launch_pauli(int elem_bytes, const void* psi, void* lam, bool accumulate,
                          const PauliSweep& hsw, const PauliSweep* d_sweep, const PauliTerm* d_terms,
                          double* partial, uint64_t ntiles, uint32_t* grid_out, cudaStream_t s);
-// CTAs launch_pauli uses for a sweep with T tile bits and R register bits (its partials)
-uint32_t pauli_grid(int elem_bytes, int T, int R, uint64_t ntiles);
+// CTAs launch_pauli uses for a sweep (the rows of partials it writes); 0 on error
+uint32_t pauli_grid(int elem_bytes, const PauliSweep& sw, uint64_t ntiles);
 
 // sum |psi|^2 per block into partial[]; returns the number of blocks used.
 cudaError_t launch_norm(int elem_bytes, const void* psi, uint64_t n_amp, double* partial,
