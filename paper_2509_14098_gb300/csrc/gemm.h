@@ -40,6 +40,9 @@ struct GemmStage {
     uint8_t var_role[12];   // chunk-varying bits in ascending physical order: 0..4 = bit of
                             // the amplitude index inside the chunk, 8 + c = column bit c
     uint8_t var_pos[12];    // their physical positions
+    uint8_t pperm[12];      // producer bit i (thread bits 0..8, then round bits) -> chunk-varying bit
+                            // 1..nvar-1 (bit 0 is the 16-byte pair); the lane bits are chosen so a
+                            // warp's operand stores fall on distinct shared-memory banks
 };
 
 }  // namespace svk

@@ -114,8 +114,8 @@ __global__ void __launch_bounds__(kT, 1)
     };
 
     // tables: local index -> physical bits; producer mapping: a producer loads amplitude
-    // pairs (var bit 0 is always physical bit 0, so a pair is 16 contiguous bytes); var
-    // bit v >= 1 of pair tp = tid + 256 r comes from tid bit v - 1 (v <= 8) or r bit v - 9
+    // pairs (var bit 0 is always physical bit 0, so a pair is 16 contiguous bytes); producer
+    // bit i of pair tp = tid + kP r (tid bits, then round bits) is var bit pperm[i]
     for (uint32_t i = tid; i < (1u << st.keff); i += kT) {
         uint64_t p = 0;
         for (uint32_t j = 0; j < st.keff; ++j)
@@ -125,8 +125,9 @@ __global__ void __launch_bounds__(kT, 1)
     if (tid < rounds) {
         uint64_t p = 0;
         uint32_t jm = 0;
-        for (uint32_t v = kLogP + 1; v < nvar; ++v)
-            if ((tid >> (v - kLogP - 1)) & 1) {
+        for (uint32_t i = kLogP; i + 1 < nvar; ++i)
+            if ((tid >> (i - kLogP)) & 1) {
+                const uint32_t v = st.pperm[i];
                 p |= 1ull << st.var_pos[v];
                 jm |= 1u << st.var_role[v];
             }
@@ -199,12 +200,14 @@ __global__ void __launch_bounds__(kT, 1)
         constexpr int RMAX = PREC == 1 ? 2 : 4;   // amplitude pairs per thread and chunk
         uint64_t p_tid = 0;
         uint32_t jm_tid = 0;
-        for (uint32_t v = 1; v < nvar && v <= (uint32_t)kLogP; ++v)
-            if ((tid >> (v - 1)) & 1) {
+        for (uint32_t i = 0; i + 1 < nvar && i < (uint32_t)kLogP; ++i)
+            if ((tid >> i) & 1) {
+                const uint32_t v = st.pperm[i];
                 p_tid |= 1ull << st.var_pos[v];
                 jm_tid |= 1u << st.var_role[v];   // role j < 8: amplitude bit j; 8 + c: column bit c
             }
         const uint32_t soff_tid = a_offset<PREC>(jm_tid & 0xFFu, jm_tid >> 8);
+        const bool pair_amp = st.var_role[0] == 0;                    // pair = amplitudes 2i, 2i + 1 of one row
         const uint32_t jm_b0 = 1u << st.var_role[0];                  // the pair's second amplitude
         const uint32_t soff_b0 = a_offset<PREC>(jm_b0 & 0xFFu, jm_b0 >> 8);
         uint32_t vmask = 0;
@@ -248,6 +251,29 @@ __global__ void __launch_bounds__(kT, 1)
             for (int r = 0; r < RMAX; ++r) {
                 if (!((vmask >> r) & 1)) continue;
                 const uint32_t so = soff_tid ^ s_rsoff[r];
+                if (pair_amp) {   // the pair's amplitudes are adjacent in the operand row: one store each for hi, lo
+                    if (PREC == 1) {
+                        const float4 v = vc[r];
+                        const float4 hv = make_float4(rn_tf32(v.x), rn_tf32(v.y), rn_tf32(v.z), rn_tf32(v.w));
+                        *reinterpret_cast<float4*>(aH + so) = hv;
+                        *reinterpret_cast<float4*>(aL + so) = make_float4(rn_tf32(v.x - hv.x), rn_tf32(v.y - hv.y),
+                                                                          rn_tf32(v.z - hv.z), rn_tf32(v.w - hv.w));
+                    } else {
+                        const __nv_bfloat162 h0 = __floats2bfloat162_rn(vc[r].x, vc[r].y);
+                        const __nv_bfloat162 h1 = __floats2bfloat162_rn(vc[r].z, vc[r].w);
+                        const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
+                        const __nv_bfloat162 l0 = __floats2bfloat162_rn(vc[r].x - f0.x, vc[r].y - f0.y);
+                        const __nv_bfloat162 l1 = __floats2bfloat162_rn(vc[r].z - f1.x, vc[r].w - f1.y);
+                        uint2 hw, lw;
+                        memcpy(&hw.x, &h0, 4);
+                        memcpy(&hw.y, &h1, 4);
+                        memcpy(&lw.x, &l0, 4);
+                        memcpy(&lw.y, &l1, 4);
+                        *reinterpret_cast<uint2*>(aH + so) = hw;
+                        *reinterpret_cast<uint2*>(aL + so) = lw;
+                    }
+                    continue;
+                }
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {   // the pair's two amplitudes
                     const float re = h ? vc[r].z : vc[r].x, im = h ? vc[r].w : vc[r].y;

@@ -8,9 +8,12 @@
 // (1, 0), -Im U_ij if (a, b) = (0, 1).  Ut is split as Ut ~ hi + lo with both halves
 // rounded to nearest (TF32: hi = rn(x), lo = rn(x - hi); BF16 likewise) and stored per
 // K chunk of 128 bytes per row in the tensor cores' 128-byte-swizzled K-major layout.
+#include <algorithm>
 #include <cmath>
+#include <functional>
 #include <complex>
 #include <cstring>
+#include <vector>
 
 #include "gemm.h"
 #include "planner.h"
@@ -134,6 +137,48 @@ std::string plan_gemm(const Plan& P, const double* params, int prec, GemmProgram
         for (int a = 0; a < nv; ++a) {
             st.var_pos[a] = (uint8_t)var[a];
             st.var_role[a] = (uint8_t)role[a];
+        }
+        {
+            // Producer mapping.  A store writes g bytes (one amplitude, or both amplitudes of
+            // the pair when the pair bit is amplitude bit 0) at an offset XOR-linear in the
+            // chunk-varying bits; the 128 / g lanes that share a shared-memory wavefront are
+            // conflict-free when their 128-byte-slot images are independent.  The lane bits
+            // take, lowest physical position first, the bits that extend that rank; the rest
+            // follow in ascending order.
+            auto aoff = [&](uint32_t jj, uint32_t m) -> uint32_t {
+                const uint32_t rowo = (m >> 3) * 1024 + (m & 7) * 128;
+                return tf32 ? rowo + ((((jj >> 1) ^ m) & 7u) << 4) + ((jj & 1u) << 3)
+                            : rowo + ((((jj >> 2) ^ m) & 7u) << 4) + ((jj & 3u) << 2);
+            };
+            const bool pair_amp = role[0] == 0;
+            const int g = (tf32 ? 8 : 4) * (pair_amp ? 2 : 1);
+            const int lg = __builtin_ctz((unsigned)g);
+            const int nphase = 7 - lg;                  // lane bits sharing a wavefront
+            const uint32_t smask = (128u / (uint32_t)g) - 1u;
+            auto slot = [&](int v) -> uint32_t {
+                const int r = role[v];
+                const uint32_t jj = r < 8 ? 1u << r : 0u, m = r >= 8 ? 1u << (r - 8) : 0u;
+                return (aoff(jj, m) >> lg) & smask;
+            };
+            std::vector<int> left, perm;
+            for (int v = 1; v < nv; ++v) left.push_back(v);
+            std::vector<uint32_t> basis;   // reduced slot images of the chosen lane bits
+            auto reduce = [&](uint32_t x) {
+                for (uint32_t b : basis) x = std::min(x, x ^ b);
+                return x;
+            };
+            for (int lane = 0; lane < nphase; ++lane) {
+                size_t pick = left.size();
+                for (size_t i = 0; i < left.size(); ++i)
+                    if (reduce(slot(left[i])) != 0) { pick = i; break; }
+                if (pick == left.size()) break;
+                basis.push_back(reduce(slot(left[pick])));
+                std::sort(basis.begin(), basis.end(), std::greater<uint32_t>());
+                perm.push_back(left[pick]);
+                left.erase(left.begin() + (long)pick);
+            }
+            for (int v : left) perm.push_back(v);
+            for (size_t i = 0; i < perm.size(); ++i) st.pperm[i] = (uint8_t)perm[i];
         }
         // fused unitary over the local qubits (index bit j <-> lp[j])
         const int D = 1 << k;

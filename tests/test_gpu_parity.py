@@ -182,3 +182,59 @@ def test_errors_are_reported(sv):
     with pytest.raises(sv.SvError) as e:
         sv.StateVector(3).grad(sv.Plan(c, 2), np.array([0.1]), C.tfim(3))
     assert e.value.status == N.SV_ERR_UNSUPPORTED
+
+
+def _term_class_observable(n, seed):
+    """Pauli terms that reach every path of the sweep planner: diagonal terms on tile
+    bits only / global bits only / both, X and Y on the low (lane) bits, the register
+    bits, the upper tile bits and mixtures of them, Y with Z on register bits (complex
+    coefficients and per-element signs), and X outside the first tile (later sweeps)."""
+    def s(**f):
+        c = ["I"] * n
+        for q, p in f.items():
+            c[int(q[1:])] = p
+        return "".join(c)
+    terms = [(0.9, s(q0="X")), (0.4, s(q1="X", q2="X")), (0.7, s(q5="X")), (0.3, s(q5="X", q13="X")),
+             (0.6, s(q5="Y", q7="Z")), (0.5, s(q3="Y", q15="Y")), (0.2, s(q7="X", q9="Y", q11="Z")),
+             (0.35, s(q9="X")), (0.25, s(q11="X", q8="Z")), (0.45, s(q13="Y")), (0.15, s(q15="X", q0="Z")),
+             (1.0, s(q4="Z", q5="Z")), (0.8, s(q0="Z")), (0.65, s(q1="Z", q9="Z")),
+             (0.55, s(q8="Z", q10="Z")), (0.3, s(q12="Z", q14="Z", q10="Z")),
+             (0.75, s(q4="Z", q8="Z")), (0.2, s(q5="Z", q12="Z", q7="Z")),
+             (0.5, s(q8="X")), (0.4, s(q10="X", q12="Y")), (0.3, s(q14="X", q0="Z")), (0.1, s()),
+             ]
+    rng = np.random.default_rng(seed)
+    for _ in range(20):
+        k = int(rng.integers(1, 5))
+        qs = rng.choice(n, size=k, replace=False)
+        c = ["I"] * n
+        for q in qs:
+            c[q] = "XYZ"[int(rng.integers(0, 3))]
+        terms.append((float(rng.normal()), "".join(c)))
+    return C.Observable(n, terms)
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("seed", range(3))
+def test_expval_term_classes(sv, dtype, seed):
+    n = 16
+    psi = C.random_state(n, 40 + seed)
+    st = sv.StateVector(n, dtype)
+    st.set_host(psi)
+    obs = _term_class_observable(n, seed)
+    e_ref = O.expval(psi, obs)
+    tol = 1e-6 * max(1.0, abs(e_ref)) if dtype == 0 else 1e-11 * max(1.0, abs(e_ref))
+    assert abs(st.expval(obs) - e_ref) <= tol
+
+
+def test_grad_term_classes(sv):
+    """lambda = O psi over several accumulating sweeps, checked through the gradient."""
+    n = 14
+    c = C.hea(n, 2)
+    p = C.hea_params(c.n_params, 11)
+    obs = _term_class_observable(16, 0)
+    obs = C.Observable(n, [(cf, ps[:n]) for cf, ps in obs.terms])
+    st = sv.StateVector(n)
+    e, g = st.grad(sv.Plan(c, 9), p, obs)
+    assert abs(e - O.expval(S.simulate(c, p), obs)) <= 1e-6 * max(1.0, abs(e))
+    g_ps = GR.parameter_shift(c, p, obs)
+    assert np.linalg.norm(g - g_ps) <= 1e-4 * np.linalg.norm(g_ps)
