@@ -6,9 +6,10 @@
 // sm_103a, one CTA per SM, persistent over tiles, warp-specialised (the roles hand off
 // through mbarriers; no CTA-wide barrier in the main loop):
 //  - 16 producer warps gather each K chunk of a tile's state columns (16-byte amplitude
-//    pairs, warps covering contiguous >= 128-byte runs, the next chunk's loads in
-//    flight), split them into hi / lo halves and store them into a ring of operand slots
-//    in the 128-byte-swizzled K-major layout (A operand, M = 128 columns); when B (the
+//    pairs, lane bits chosen per stage for conflict-free operand stores, the next chunk's
+//    loads in flight and, when B stays resident, the chunk two beyond it prefetched into
+//    L2), split them into hi / lo halves and store them into a ring of operand slots in
+//    the 128-byte-swizzled K-major layout (A operand, M = 128 columns); when B (the
 //    stage's fused unitary, pre-split and pre-swizzled by the host) does not stay in
 //    shared memory for the whole launch (k = 7), they also copy its K chunk;
 //  - one thread issues the 3 x 4 tcgen05.mma of a chunk and commits them to the slot's
@@ -229,6 +230,24 @@ __global__ void __launch_bounds__(kT, 1)
                 bl = next_tile(bl);
             }
         };
+        // L2 prefetch two chunks beyond the register lookahead when B stays resident (the
+        // loads then hit L2; with B streamed through L2 every chunk, prefetching measured slower)
+        uint32_t cpf = cl;
+        uint64_t bpf = bl;
+        auto advance_pf = [&]() {
+            if (++cpf == nchunk) {
+                cpf = 0;
+                bpf = next_tile(bpf);
+            }
+        };
+        const uint32_t pfd = resident ? 2u : 0u;
+        for (uint32_t i = 0; i < pfd + 1; ++i) advance_pf();
+        auto prefetch_chunk = [&]() {
+            const uint64_t b = bpf | s_ltab[cpf << cb] | p_tid;
+#pragma unroll
+            for (int r = 0; r < RMAX; ++r)
+                if ((vmask >> r) & 1) asm volatile("prefetch.global.L2 [%0];" ::"l"(psi + (b | s_roff[r])));
+        };
         float4 va[RMAX], vb[RMAX];
         if (total) load_chunk(bl | s_ltab[cl << cb], va);
         advance_look();
@@ -238,6 +257,8 @@ __global__ void __launch_bounds__(kT, 1)
             const uint32_t slot = (uint32_t)(g % NS), use = (uint32_t)(g / NS);
             if (g + 1 < total) load_chunk(bl | s_ltab[cl << cb], vl);
             advance_look();
+            if (pfd && g + 1 + pfd < total) prefetch_chunk();
+            advance_pf();
             if (g >= NS && !wait(bar_empty[slot], (use - 1) & 1u)) return false;
             if (!resident) {
                 const uint8_t* src = ublob + st.b_off + (size_t)c * bcb;
