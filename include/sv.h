@@ -242,8 +242,15 @@ sv_status sv_run(sv_handle h, const sv_plan* plan, const double* params, sv_prec
  * this sweep).  phys_of_qubit: host array of n entries, a permutation. */
 sv_status sv_permute(sv_handle h, const uint32_t* phys_of_qubit);
 
-/* <psi|O|psi> for a Pauli sum, reduced in FP64 (FP32 partial sums over at most
- * 32 amplitudes).  Result written to *out (host); synchronises. */
+/* <psi|O|psi> for a Pauli sum (Sec. 4.2's observable, evaluated by Pauli sweeps:
+ * one read of psi per group of X/Y-carrying terms whose X/Y qubits fit one 12-qubit
+ * tile together with qubits 0..3; the diagonal terms join the first sweep).  Each
+ * term's X/Y factors must fit such a tile: for states of more than 12 qubits at most
+ * 8 X/Y factors outside qubits 0..3 (physical positions), else SV_ERR_UNSUPPORTED.  Reduction: complex64 states sum in FP32 over
+ * one thread's 16 amplitudes per tile, compensated FP32 across its tiles, FP64 across
+ * threads and CTAs in a fixed order; complex128 states sum in FP64.  Result written
+ * to *out (host); synchronises.  Errors: SV_ERR_ARG (width mismatch, null or invalid
+ * Pauli codes), SV_ERR_UNSUPPORTED, SV_ERR_CUDA. */
 sv_status sv_expval(sv_handle h, const sv_observable* obs, double* out);
 
 /* ||psi||^2 in FP64; synchronises. */
