@@ -526,45 +526,47 @@ def main_ours(args):
         extras["e2e"] = {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": (1 << n) * 8,
                          "d2h_bytes_per_step": (1 << n) * 8 + 8}
         del host_in, host_out
-        # adjoint gradient / forward ratio on the hardware-efficient ansatz
+        # adjoint gradient / forward ratio on the hardware-efficient ansatz (the
+        # differentiation workload's width, and 30 qubits)
         st.close()
         del st, psi
         torch.cuda.empty_cache()
-        gn = args.grad_n
-        hc = C.hea(gn, 10)
-        hp = C.hea_params(hc.n_params, 4)
-        hplan = sv.Plan(hc, args.grad_L)
-        g = sv.StateVector(gn)
-        obs = C.tfim(gn)
 
-        def fwd():
-            g.reset()
-            g.run(hplan, hp)
-            return g.expval(obs)
+        def grad_ratio(gn):
+            hc = C.hea(gn, 10)
+            hp = C.hea_params(hc.n_params, 4)
+            hplan = sv.Plan(hc, args.grad_L)
+            g = sv.StateVector(gn)
+            obs = C.tfim(gn)
 
-        def grad():
-            g.reset()
-            return g.grad(hplan, hp, obs)
+            def grad():
+                g.reset()
+                return g.grad(hplan, hp, obs)
 
-        fwd(); grad()
-        torch.cuda.synchronize()
-        g.timing(True); g.timing(reset=True)
-        t0 = time.perf_counter(); [g.run(hplan, hp) for _ in range(3)]; torch.cuda.synchronize()
-        t_fwd = (time.perf_counter() - t0) / 3
-        tf = g.timing(reset=True)
-        t0 = time.perf_counter(); [grad() for _ in range(3)]; torch.cuda.synchronize()
-        t_grad = (time.perf_counter() - t0) / 3
-        tg = g.timing(reset=True)
-        g.timing(False)
-        extras["grad_forward_ratio"] = {
-            "workload": f"hea{gn}x10 (560 params), TFIM open chain, L={args.grad_L}",
-            "ratio": (t_grad - t_fwd) / t_fwd, "grad_over_forward": t_grad / t_fwd,
-            "forward_ms": t_fwd * 1e3, "grad_ms": t_grad * 1e3,
-            "kernel_ms": {"forward_stages": tf["stage_ms"] / 3, "grad_forward_stages": tg["stage_ms"] / 3,
-                          "backward_stages": tg["backward_ms"] / 3, "lambda_and_expval": tg["observable_ms"] / 3},
-            "definition": "(time(sv_grad) - time(sv_run)) / time(sv_run): lambda formation + backward over forward",
-        }
-        g.close()
+            g.reset(); g.run(hplan, hp); g.expval(obs); grad()
+            torch.cuda.synchronize()
+            g.timing(True); g.timing(reset=True)
+            t0 = time.perf_counter(); [g.run(hplan, hp) for _ in range(3)]; torch.cuda.synchronize()
+            t_fwd = (time.perf_counter() - t0) / 3
+            tf = g.timing(reset=True)
+            t0 = time.perf_counter(); [grad() for _ in range(3)]; torch.cuda.synchronize()
+            t_grad = (time.perf_counter() - t0) / 3
+            tg = g.timing(reset=True)
+            g.timing(False)
+            g.close()
+            torch.cuda.empty_cache()
+            return {
+                "workload": f"hea{gn}x10 ({hc.n_params} params), TFIM open chain, L={args.grad_L}",
+                "ratio": (t_grad - t_fwd) / t_fwd, "grad_over_forward": t_grad / t_fwd,
+                "forward_ms": t_fwd * 1e3, "grad_ms": t_grad * 1e3,
+                "kernel_ms": {"forward_stages": tf["stage_ms"] / 3, "grad_forward_stages": tg["stage_ms"] / 3,
+                              "backward_stages": tg["backward_ms"] / 3, "lambda_and_expval": tg["observable_ms"] / 3},
+                "definition": "(time(sv_grad) - time(sv_run)) / time(sv_run): lambda formation + backward over forward",
+            }
+
+        extras["grad_forward_ratio"] = grad_ratio(args.grad_n)
+        if args.grad_n != N_QUBITS:
+            extras["grad_forward_ratio_30q"] = grad_ratio(N_QUBITS)
         extras["batch"] = batch_section(args, 3)
         torch.cuda.empty_cache()
         extras["tensor_core_stages"] = gemm_section(args)
