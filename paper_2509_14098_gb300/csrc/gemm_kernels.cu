@@ -11,7 +11,8 @@
 //    L2), split them into hi / lo halves and store them into a ring of operand slots in
 //    the 128-byte-swizzled K-major layout (A operand, M = 128 columns); when B (the
 //    stage's fused unitary, pre-split and pre-swizzled by the host) does not stay in
-//    shared memory for the whole launch (k = 7), they also copy its K chunk;
+//    shared memory for the whole launch (k = 7), one of them starts a bulk copy of its K
+//    chunk that completes on the slot's own transaction barrier;
 //  - one thread issues the 3 x 4 tcgen05.mma of a chunk and commits them to the slot's
 //    "empty" barrier, and after a tile's last chunk to the accumulator's "full" barrier;
 //  - 4 epilogue warps (one per 32-lane quarter of tensor memory) read a finished
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(kT, 1)
     __shared__ uint64_t s_ltab[128];                 // local index -> physical offset
     __shared__ uint64_t s_roff[32];                  // producer round -> physical offset
     __shared__ uint32_t s_rsoff[32];                 // producer round -> swizzled A offset part
-    __shared__ __align__(8) uint64_t bar_full[3], bar_empty[3], bar_accf[2], bar_acce[2], bar_fin;
+    __shared__ __align__(8) uint64_t bar_full[3], bar_empty[3], bar_accf[2], bar_acce[2], bar_fin, bar_bfull[3];
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int s_fail;
     static_assert(sizeof(GemmStage) % 4 == 0, "stage copy");
@@ -146,6 +147,7 @@ __global__ void __launch_bounds__(kT, 1)
         for (int i = 0; i < 3; ++i) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_full[i])), "r"(kP / 32));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_empty[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_bfull[i])));
         }
         for (int i = 0; i < 2; ++i) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_accf[i])));
@@ -248,6 +250,7 @@ __global__ void __launch_bounds__(kT, 1)
             for (int r = 0; r < RMAX; ++r)
                 if ((vmask >> r) & 1) asm volatile("prefetch.global.L2 [%0];" ::"l"(psi + (b | s_roff[r])));
         };
+        uint64_t nbulk = 0;   // B bulk copies issued (thread 0)
         float4 va[RMAX], vb[RMAX];
         if (total) load_chunk(bl | s_ltab[cl << cb], va);
         advance_look();
@@ -260,11 +263,13 @@ __global__ void __launch_bounds__(kT, 1)
             if (pfd && g + 1 + pfd < total) prefetch_chunk();
             advance_pf();
             if (g >= NS && !wait(bar_empty[slot], (use - 1) & 1u)) return false;
-            if (!resident) {
+            if (!resident && tid == 0) {   // B chunk: one bulk copy, completing on bar_bfull[slot]
                 const uint8_t* src = ublob + st.b_off + (size_t)c * bcb;
-                const uint32_t dst = b_chunk(c, slot);
-                for (uint32_t o = tid * 16; o < bcb; o += kP * 16) cp_async16g(dst + o, src + o);
-                asm volatile("cp.async.commit_group;\n" ::: "memory");
+                const uint32_t bar = smem_u32(&bar_bfull[slot]);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bcb) : "memory");
+                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                             ::"r"(b_chunk(c, slot)), "l"(src), "r"(bcb), "r"(bar) : "memory");
+                ++nbulk;
             }
             unsigned char* aH = gbase + (a_slot(slot) - sbase);
             unsigned char* aL = aH + kOpBlock;
@@ -312,7 +317,6 @@ __global__ void __launch_bounds__(kT, 1)
                     }
                 }
             }
-            if (!resident) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // visible to the tensor core
             __syncwarp();
             if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar_full[slot])) : "memory");
@@ -324,6 +328,18 @@ __global__ void __launch_bounds__(kT, 1)
             if (!step(va, vb)) break;
             if (g < total && !step(vb, va)) break;
         }
+        // bulk copies still in flight (a failed run): wait, bounded, for the last one of
+        // each slot before the CTA can exit
+        if (tid == 0)
+            for (uint64_t gg = nbulk > NS ? nbulk - NS : 0; gg < nbulk; ++gg) {
+                const uint32_t a = smem_u32(&bar_bfull[gg % NS]), par = (uint32_t)(gg / NS) & 1u;
+                uint32_t done = 0;
+                for (uint32_t it = 0; it < kWaitLimit && !done; ++it)
+                    asm volatile("{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\t"
+                                 "selp.u32 %0, 1, 0, q;\n\t}"
+                                 : "=r"(done) : "r"(a), "r"(par) : "memory");
+                if (!done) s_fail = 1;
+            }
     } else if (warp < kEpiWarp0 + 4) {
         // ------------------------------------------------------------ epilogue
         const uint32_t q = warp & 3u, m = 32u * q + lane;
@@ -380,7 +396,8 @@ __global__ void __launch_bounds__(kT, 1)
             bool ok = true;
             for (uint32_t c = 0; c < nchunk; ++c, ++g) {
                 const uint32_t slot = (uint32_t)(g % NS);
-                if (!wait(bar_full[slot], (uint32_t)(g / NS) & 1u)) {
+                if (!wait(bar_full[slot], (uint32_t)(g / NS) & 1u) ||
+                    (!resident && !wait(bar_bfull[slot], (uint32_t)(g / NS) & 1u))) {
                     ok = false;
                     break;
                 }
