@@ -7,8 +7,8 @@
 // through mbarriers; no CTA-wide barrier in the main loop):
 //  - 16 producer warps gather each K chunk of a tile's state columns (16-byte amplitude
 //    pairs, lane bits chosen per stage for conflict-free operand stores, the next chunk's
-//    loads in flight and, when B stays resident, the chunk two beyond it prefetched into
-//    L2), split them into hi / lo halves and store them into a ring of operand slots in
+//    loads in flight and the chunk two beyond it prefetched into L2 unless a BF16x3 stage
+//    streams B), split them into hi / lo halves and store them into a ring of operand slots in
 //    the 128-byte-swizzled K-major layout (A operand, M = 128 columns); when B (the
 //    stage's fused unitary, pre-split and pre-swizzled by the host) does not stay in
 //    shared memory for the whole launch (k = 7), one of them starts a bulk copy of its K
@@ -232,8 +232,8 @@ __global__ void __launch_bounds__(kT, 1)
                 bl = next_tile(bl);
             }
         };
-        // L2 prefetch two chunks beyond the register lookahead when B stays resident (the
-        // loads then hit L2; with B streamed through L2 every chunk, prefetching measured slower)
+        // L2 prefetch two chunks beyond the register lookahead (the loads then hit L2),
+        // except for BF16x3 stages whose B streams through L2 every chunk (measured slower)
         uint32_t cpf = cl;
         uint64_t bpf = bl;
         auto advance_pf = [&]() {
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(kT, 1)
                 bpf = next_tile(bpf);
             }
         };
-        const uint32_t pfd = resident ? 2u : 0u;
+        const uint32_t pfd = (resident || PREC == 1) ? 2u : 0u;
         for (uint32_t i = 0; i < pfd + 1; ++i) advance_pf();
         auto prefetch_chunk = [&]() {
             const uint64_t b = bpf | s_ltab[cpf << cb] | p_tid;
