@@ -253,6 +253,16 @@ sv_status sv_permute(sv_handle h, const uint32_t* phys_of_qubit);
  * Pauli codes), SV_ERR_UNSUPPORTED, SV_ERR_CUDA. */
 sv_status sv_expval(sv_handle h, const sv_observable* obs, double* out);
 
+/* The Pauli-sweep grouping sv_expval uses for obs on an n_qubits state of dtype, computed
+ * on the host (no GPU, no handle): *n_sweeps sweeps; tile_masks[i] = the qubits held in
+ * sweep i's shared-memory tile, reg_masks[i] = those of them held in registers (each
+ * thread's element index), n_terms[i] = the terms evaluated in sweep i (every diagonal
+ * term in sweep 0).  The arrays may be NULL (query *n_sweeps first); each must hold
+ * *n_sweeps entries.  Errors: SV_ERR_ARG, SV_ERR_UNSUPPORTED (a term's X/Y factors do
+ * not fit one tile). */
+sv_status sv_pauli_plan_info(uint32_t n_qubits, sv_dtype dtype, const sv_observable* obs, uint32_t* n_sweeps,
+                             uint64_t* tile_masks, uint64_t* reg_masks, uint32_t* n_terms);
+
 /* ||psi||^2 in FP64; synchronises. */
 sv_status sv_norm(sv_handle h, double* out);
 

@@ -90,6 +90,8 @@ _SIGS = {
     "sv_partition_ex": ([ctypes.POINTER(sv_circuit), _u32, _u32, ctypes.POINTER(_vp)], ctypes.c_int),
     "sv_partition_gemm": ([ctypes.POINTER(sv_circuit), _u32, ctypes.POINTER(_vp)], ctypes.c_int),
     "sv_plan_stages": ([_vp, ctypes.POINTER(_u32), ctypes.POINTER(_u64), ctypes.POINTER(_u32)], ctypes.c_int),
+    "sv_pauli_plan_info": ([_u32, ctypes.c_int, ctypes.POINTER(sv_observable), ctypes.POINTER(_u32),
+                            ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u32)], ctypes.c_int),
     "sv_plan_order": ([_vp, ctypes.POINTER(_u32), ctypes.POINTER(_u32)], ctypes.c_int),
     "sv_plan_centrality": ([_vp, ctypes.POINTER(_u32), ctypes.POINTER(_u64), ctypes.POINTER(_u32)], ctypes.c_int),
     "sv_plan_destroy": ([_vp], ctypes.c_int),

@@ -260,10 +260,9 @@ struct PauliPlan {
 // Split the observable into sweeps: each sweep's tile holds the L lowest physical bits
 // and the X / Y qubits of its terms; the diagonal terms go to sweep 0.  Within a sweep
 // the register bits are the tile qubits that carry X / Y most often.
-static sv_status plan_pauli(sv_handle h, const sv_observable* obs, const std::vector<int>& where,
+static sv_status plan_pauli(int n, int eb, const sv_observable* obs, const std::vector<int>& where,
                             PauliPlan* out) {
-    const int n = (int)h->n;
-    if (!obs || obs->n_qubits != h->n || (obs->n_terms && (!obs->pauli || !obs->coeff)))
+    if (!obs || obs->n_qubits != (uint32_t)n || (obs->n_terms && (!obs->pauli || !obs->coeff)))
         return fail(SV_ERR_ARG, "bad observable");
     struct Raw { uint64_t x, z; double fre, fim; };
     std::vector<Raw> diag, off;
@@ -285,7 +284,7 @@ static sv_status plan_pauli(sv_handle h, const sv_observable* obs, const std::ve
     }
     const int T = std::min(n, 12);
     const int L = std::min(4, T - 1);
-    const int R = std::min(h->eb == 8 ? 4 : 3, T - L);
+    const int R = std::min(eb == 8 ? 4 : 3, T - L);
     std::vector<char> used(off.size(), 0);
     size_t left = off.size();
     bool first = true;
@@ -783,12 +782,37 @@ sv_status sv_expval(sv_handle h, const sv_observable* obs, double* out) {
     std::vector<int> ident(h->n);
     for (uint32_t q = 0; q < h->n; ++q) ident[q] = (int)q;
     PauliPlan pp;
-    sv_status s = plan_pauli(h, obs, ident, &pp);
+    sv_status s = plan_pauli((int)h->n, h->eb, obs, ident, &pp);
     if (s) return s;
     s = run_pauli(h, pp, nullptr);
     if (s) return s;
     SV_CUDA(cudaMemcpyAsync(out, h->red.p, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     SV_CUDA(cudaStreamSynchronize(h->stream));
+    return SV_OK;
+}
+
+sv_status sv_pauli_plan_info(uint32_t n_qubits, sv_dtype dtype, const sv_observable* obs, uint32_t* n_sweeps,
+                             uint64_t* tile_masks, uint64_t* reg_masks, uint32_t* n_terms) {
+    if (!obs || !n_sweeps) return fail(SV_ERR_ARG, "null argument");
+    if (n_qubits < 1 || n_qubits > 34) return fail(SV_ERR_ARG, "n_qubits must be in [1, 34]");
+    if (dtype != SV_C64 && dtype != SV_C128) return fail(SV_ERR_ARG, "bad dtype");
+    std::vector<int> ident(n_qubits);
+    for (uint32_t q = 0; q < n_qubits; ++q) ident[q] = (int)q;
+    PauliPlan pp;
+    sv_status s = plan_pauli((int)n_qubits, dtype == SV_C64 ? 8 : 16, obs, ident, &pp);
+    if (s) return s;
+    if ((tile_masks || reg_masks || n_terms) && *n_sweeps < pp.sweeps.size())
+        return fail(SV_ERR_ARG, "arrays too small");
+    *n_sweeps = (uint32_t)pp.sweeps.size();
+    for (size_t i = 0; i < pp.sweeps.size(); ++i) {
+        const svk::PauliSweep& sw = pp.sweeps[i];
+        uint64_t t = 0, r = 0;
+        for (uint32_t b = 0; b < sw.T; ++b) t |= sw.ptile[b];
+        for (uint32_t b = sw.L; b < sw.L + sw.R; ++b) r |= sw.ptile[b];
+        if (tile_masks) tile_masks[i] = t;
+        if (reg_masks) reg_masks[i] = r;
+        if (n_terms) n_terms[i] = sw.n_terms;
+    }
     return SV_OK;
 }
 
@@ -810,7 +834,7 @@ sv_status sv_grad(sv_handle h, const sv_plan* plan, const double* params, const 
     if (s) return s;
     // lambda = O psi in the forward program's final physical layout
     PauliPlan pp;
-    s = plan_pauli(h, obs, P.final_map, &pp);
+    s = plan_pauli((int)h->n, h->eb, obs, P.final_map, &pp);
     if (s) return s;
     SV_CUDA(h->scratch.ensure(state_bytes(h)));
     s = run_pauli(h, pp, h->scratch.p);
