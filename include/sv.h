@@ -206,6 +206,18 @@ sv_status sv_partition_ex(const sv_circuit* circuit, uint32_t L, uint32_t n_fixe
  * also run on the CUDA cores (SV_PREC_CUDACORE).  Errors as sv_partition. */
 sv_status sv_partition_gemm(const sv_circuit* circuit, uint32_t k, sv_plan** out);
 
+/* Layout of a tensor-core plan's stages for prec (SV_PREC_TF32X3 / SV_PREC_BF16X3),
+ * computed on the host (no GPU): keff[s] = local qubits of stage s's fused unitary (6
+ * or 7), resident[s] = 1 when its B operand stays in shared memory for the launch,
+ * nslot[s] = depth of its operand ring, lane_roles[6 s + i] = what producer lane bit i
+ * (i < 5) and the 16-byte pair bit (i = 5) select: 0..4 = a bit of the amplitude index
+ * inside a K chunk, 8 + c = column bit c (the operand row), 255 = none.  params as for
+ * sv_run (NULL when the circuit has none).  Arrays may be NULL; each holds *n_stages
+ * entries (lane_roles 6 *n_stages); query *n_stages first.  Errors: SV_ERR_ARG,
+ * SV_ERR_UNSUPPORTED (not a tensor-core plan, or a stage the kernel cannot hold). */
+sv_status sv_gemm_plan_info(const sv_plan* plan, const double* params, sv_prec prec, uint32_t* n_stages,
+                            uint32_t* keff, uint32_t* resident, uint32_t* nslot, uint8_t* lane_roles);
+
 /* Partition summary.  local_masks[s] = physical-bit mask of stage s's local set
  * (after SWAP relabelling); gate_counts[s] = gates in stage s.  Either array may be
  * NULL; each must hold n_stages entries (query n_stages first with both NULL). */

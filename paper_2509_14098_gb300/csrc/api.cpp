@@ -623,6 +623,32 @@ sv_status sv_partition_gemm(const sv_circuit* circuit, uint32_t k, sv_plan** out
     return build_plan(circuit, k, 0, out, true);
 }
 
+sv_status sv_gemm_plan_info(const sv_plan* plan, const double* params, sv_prec prec, uint32_t* n_stages,
+                            uint32_t* keff, uint32_t* resident, uint32_t* nslot, uint8_t* lane_roles) {
+    if (!plan || !n_stages) return fail(SV_ERR_ARG, "null argument");
+    if (prec != SV_PREC_TF32X3 && prec != SV_PREC_BF16X3) return fail(SV_ERR_ARG, "bad precision");
+    if (plan->plan.gemm_k == 0) return fail(SV_ERR_UNSUPPORTED, "tensor-core precision needs a plan from sv_partition_gemm");
+    if (plan->plan.n_params > 0 && !params) return fail(SV_ERR_ARG, "params is NULL");
+    svh::GemmProgram gp;
+    std::string err = svh::plan_gemm(plan->plan, params, prec == SV_PREC_TF32X3 ? 1 : 2, &gp);
+    if (!err.empty()) return fail(SV_ERR_UNSUPPORTED, err);
+    if ((keff || resident || nslot || lane_roles) && *n_stages < gp.stages.size())
+        return fail(SV_ERR_ARG, "arrays too small");
+    *n_stages = (uint32_t)gp.stages.size();
+    for (size_t i = 0; i < gp.stages.size(); ++i) {
+        const svk::GemmStage& st = gp.stages[i];
+        if (keff) keff[i] = st.keff;
+        if (resident) resident[i] = st.resident;
+        if (nslot) nslot[i] = st.nslot;
+        if (lane_roles) {
+            for (int l = 0; l < 5; ++l)   // producer lane bit l: chunk-varying bit pperm[l] (255: none)
+                lane_roles[i * 6 + l] = (uint32_t)l + 1 < st.nvar ? st.var_role[st.pperm[l]] : (uint8_t)255;
+            lane_roles[i * 6 + 5] = st.var_role[0];
+        }
+    }
+    return SV_OK;
+}
+
 sv_status sv_plan_stages(const sv_plan* plan, uint32_t* n_stages, uint64_t* local_masks,
                          uint32_t* gate_counts) {
     if (!plan || !n_stages) return fail(SV_ERR_ARG, "null argument");
