@@ -1,0 +1,236 @@
+// Host emulator of the packed forward program (test infrastructure).  Runs the
+// library's host planner (SWAP relabel, closeness-centrality partition, lowering into
+// register groups and micro-ops, packing) on a circuit and executes the packed device
+// program tile by tile, thread by thread, in double precision, following the op
+// semantics the kernels implement.  The test compares the result with the CPU oracle,
+// so the lowering is checked on the CPU.
+//
+//   stage_emu <in.bin> <out.bin>
+// in:  int32 n, L, n_fixed, n_params, n_gates, elem_bytes (8 | 16), rmax;
+//      n_params doubles; n_gates x (int32 kind, nq, q0, q1, param; double a0, a1, a2);
+//      2^n x (re, im) doubles
+// out: 2^n x (re, im) doubles in canonical qubit order; exit status 0, or 2 with a
+//      message on stderr when the planner rejects the circuit
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "planner.h"
+
+using namespace svh;
+using namespace svk;
+typedef std::complex<double> cd;
+
+static double ang(uint32_t k) { return (double)(int32_t)k * (2 * M_PI / 4294967296.0); }
+static double ang(double a) { return a; }
+static uint64_t deposit(uint64_t x, const uint8_t* pos, int n) {
+    uint64_t r = 0;
+    for (int i = 0; i < n; ++i)
+        if ((x >> i) & 1) r |= 1ull << pos[i];
+    return r;
+}
+
+template <typename Real>
+static void run_packed(const Program& prog, int n, std::vector<cd>& psi) {
+    Packed pk;
+    std::string err = pack(prog, n, sizeof(Real) == 8 ? 16 : 8, &pk);
+    if (!err.empty()) {
+        fprintf(stderr, "pack: %s\n", err.c_str());
+        exit(2);
+    }
+    const uint8_t* b = pk.blob.data();
+    const Stage* stages = (const Stage*)(b + pk.stage_off);
+    const Group* groups = (const Group*)(b + pk.group_off);
+    const DevOp<Real>* ops = (const DevOp<Real>*)(b + pk.op_off);
+    const DevTerm<Real>* terms = (const DevTerm<Real>*)(b + pk.term_off);
+    const PhaseSlot<Real>* slots = (const PhaseSlot<Real>*)(b + pk.slot_off);
+    for (size_t si = 0; si < pk.stages.size(); ++si) {
+        const Stage& st = stages[si];
+        const int R = (int)st.R, TR = (int)st.T - R;
+        for (uint64_t tile = 0; tile < (1ull << st.n_glob); ++tile) {
+            const uint64_t base = deposit(tile, st.glob_pos, (int)st.n_glob);
+            std::vector<double> wg(st.n_phase);   // per-tile angle of each phase slot
+            for (uint32_t p = 0; p < st.n_phase; ++p) {
+                const PhaseSlot<Real>& ps = slots[st.phase_off + p];
+                double a = ang(ps.cangle);
+                for (uint32_t i = 0; i < ps.n_glob; ++i)
+                    if (base & terms[ps.glob_off + i].mask) a += ang(terms[ps.glob_off + i].angle);
+                wg[p] = a;
+            }
+            for (uint32_t gi = 0; gi < st.n_groups; ++gi) {
+                const Group& G = groups[st.group_off + gi];
+                for (uint32_t tid = 0; tid < (1u << TR); ++tid) {
+                    uint64_t fix = base;
+                    for (int i = 0; i < TR; ++i)
+                        if ((tid >> i) & 1) fix |= 1ull << st.tile_pos[G.thr_pos[i]];
+                    std::vector<uint64_t> addr(1u << R);
+                    std::vector<cd> a(1u << R);
+                    for (int k = 0; k < (1 << R); ++k) {
+                        uint64_t x = fix;
+                        for (int j = 0; j < R; ++j)
+                            if ((k >> j) & 1) x |= 1ull << st.tile_pos[G.reg_pos[j]];
+                        addr[k] = x;
+                        a[k] = psi[x];
+                    }
+                    for (uint32_t oi = 0; oi < G.n_ops; ++oi) {
+                        const DevOp<Real>& o = ops[st.op_off + G.op_off + oi];
+                        cd M[4] = {cd(o.m[0], o.m[1]), cd(o.m[2], o.m[3]), cd(o.m[4], o.m[5]), cd(o.m[6], o.m[7])};
+                        if (o.type == OP_UR) {
+                            M[0] = o.m[0];
+                            M[1] = o.m[2];
+                            M[2] = o.m[4];
+                            M[3] = o.m[6];
+                        }
+                        // the op's phase factor: a phase slot (per-tile angle plus the thread
+                        // bits' part), or a constant with optional per-thread terms
+                        auto phase = [&]() {
+                            if (o.flags & F_SLOT) {
+                                double x = wg[o.slot];
+                                const PhaseSlot<Real>& ps = slots[st.phase_off + o.slot];
+                                for (int i = 0; i < TR; ++i)
+                                    if ((tid >> i) & 1) x += ang(ps.J[i]);
+                                return std::polar(1.0, x);
+                            }
+                            cd w = (o.flags & F_TW) ? cd(1, 0) : cd(o.m[0], o.m[1]);
+                            if (o.flags & F_TERMS) {
+                                double x = 0;
+                                for (uint32_t i = 0; i < o.n_terms; ++i) {
+                                    const uint64_t m = terms[o.term_off + i].mask;
+                                    if ((fix & m) == m) x += ang(terms[o.term_off + i].angle);
+                                }
+                                w *= std::polar(1.0, x);
+                            }
+                            return w;
+                        };
+                        if (o.type <= OP_X) {
+                            if ((fix & o.ctrl_fix) != o.ctrl_fix) continue;
+                            if (o.flags & F_PAIRS) {   // pair phases on the target's |1> half
+                                const cd w0 = (o.flags & F_TW) ? phase() : cd(1, 0);
+                                double pa[3];
+                                for (int i = 0; i < 3; ++i) {
+                                    typename AngT<Real>::type t;
+                                    memcpy(&t, &o.m[1 + 2 * i], sizeof(t));
+                                    pa[i] = ang(t);
+                                }
+                                for (int k = 0; k < (1 << R); ++k) {
+                                    if (!((k >> o.j) & 1)) continue;
+                                    const int kk = k & ~(1 << o.j);
+                                    const int c = (kk & ((1 << o.j) - 1)) | ((kk >> (o.j + 1)) << o.j);
+                                    double ph = 0;
+                                    for (int i = 0; i < R - 1; ++i)
+                                        if ((c >> i) & 1) ph += pa[i];
+                                    a[k] *= w0 * std::polar(1.0, ph);
+                                }
+                            } else if (o.flags & F_TW) {
+                                const cd w = phase();
+                                for (int k = 0; k < (1 << R); ++k)
+                                    if ((k >> o.j) & 1) a[k] *= w;
+                            }
+                            for (int k = 0; k < (1 << R); ++k) {
+                                if ((k >> o.j) & 1) continue;
+                                if ((k & (int)o.ctrl_reg) != (int)o.ctrl_reg) continue;
+                                const int k1 = k | (1 << o.j);
+                                const cd x0 = a[k], x1 = a[k1];
+                                if (o.type == OP_X) {
+                                    a[k] = x1;
+                                    a[k1] = x0;
+                                } else {
+                                    a[k] = M[0] * x0 + M[1] * x1;
+                                    a[k1] = M[2] * x0 + M[3] * x1;
+                                }
+                            }
+                        } else if (o.type == OP_PHASE1) {
+                            const cd w = phase();
+                            for (int k = 0; k < (1 << R); ++k)
+                                if ((k >> o.j) & 1) a[k] *= w;
+                        } else if (o.type == OP_PHASE2) {
+                            const cd w(o.m[0], o.m[1]);
+                            for (int k = 0; k < (1 << R); ++k)
+                                if (((k >> o.j) & 1) && ((k >> o.u) & 1)) a[k] *= w;
+                        } else if (o.type == OP_PHASE0) {
+                            const cd w = phase();
+                            for (int k = 0; k < (1 << R); ++k) a[k] *= w;
+                        } else {
+                            fprintf(stderr, "op type %d in a forward program\n", (int)o.type);
+                            exit(3);
+                        }
+                    }
+                    for (int k = 0; k < (1 << R); ++k) psi[addr[k]] = a[k];
+                }
+            }
+        }
+    }
+}
+
+template <typename T>
+static T rd(FILE* f) {
+    T v;
+    if (fread(&v, sizeof(T), 1, f) != 1) {
+        fprintf(stderr, "short input\n");
+        exit(1);
+    }
+    return v;
+}
+
+int main(int argc, char** argv) {
+    if (argc != 3) {
+        fprintf(stderr, "usage: stage_emu in.bin out.bin\n");
+        return 1;
+    }
+    FILE* f = fopen(argv[1], "rb");
+    if (!f) return 1;
+    const int n = rd<int32_t>(f), L = rd<int32_t>(f), nf = rd<int32_t>(f), np = rd<int32_t>(f);
+    const int ng = rd<int32_t>(f), eb = rd<int32_t>(f), rmax = rd<int32_t>(f);
+    std::vector<double> params(np);
+    for (auto& p : params) p = rd<double>(f);
+    Plan P;
+    P.n = n;
+    P.n_params = np;
+    P.L = L;
+    P.n_fixed = nf;
+    for (int i = 0; i < ng; ++i) {
+        GateRec g;
+        g.kind = rd<int32_t>(f);
+        g.nq = rd<int32_t>(f);
+        g.q[0] = rd<int32_t>(f);
+        g.q[1] = rd<int32_t>(f);
+        g.param = rd<int32_t>(f);
+        for (int k = 0; k < 3; ++k) g.angle[k] = rd<double>(f);
+        P.gates.push_back(g);
+    }
+    std::vector<cd> psi(1ull << n);
+    for (auto& x : psi) {
+        const double re = rd<double>(f), im = rd<double>(f);
+        x = cd(re, im);
+    }
+    fclose(f);
+    relabel(n, P.gates, &P.phys, &P.final_map);
+    const uint64_t fixed = nf ? ((1ull << nf) - 1) : 0;
+    std::string err = partition_core(n, P.phys, L, fixed, (1ull << n) - 1, &P.top, &P.cc);
+    if (!err.empty()) {
+        fprintf(stderr, "partition: %s\n", err.c_str());
+        return 2;
+    }
+    Program prog;
+    err = lower(P, np ? params.data() : nullptr, eb, rmax, false, &prog);
+    if (!err.empty()) {
+        fprintf(stderr, "lower: %s\n", err.c_str());
+        return 2;
+    }
+    if (eb == 8) run_packed<float>(prog, n, psi);
+    else run_packed<double>(prog, n, psi);
+    FILE* o = fopen(argv[2], "wb");
+    if (!o) return 1;
+    for (uint64_t y = 0; y < psi.size(); ++y) {   // physical -> canonical order
+        uint64_t x = 0;
+        for (int q = 0; q < n; ++q)
+            if ((y >> q) & 1) x |= 1ull << P.final_map[q];
+        const double v[2] = {psi[x].real(), psi[x].imag()};
+        fwrite(v, sizeof(double), 2, o);
+    }
+    fclose(o);
+    return 0;
+}

@@ -1,0 +1,103 @@
+"""The host planner's output executed on the CPU (no GPU): `tests/host_emu/stage_emu.cpp`
+runs the library's SWAP relabel, closeness-centrality partition, lowering (register
+groups, micro-ops, diagonal sinking, twiddles, phase slots, pair phases folded into
+real butterflies) and packing, then executes the packed forward program in double
+precision, tile by tile and thread by thread.  Its state must match the CPU oracle's
+gate-by-gate result: within 1e-10 for the complex128 packing (FP64 matrices and
+angles), within 2e-5 for the complex64 packing (FP32 matrices, 32-bit fixed-point
+phase turns)."""
+import os
+import struct
+import subprocess
+
+import numpy as np
+import pytest
+
+import circuits as C
+from oracle import statevector as S
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2509_14098_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def emu(tmp_path_factory):
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2509_14098_gb300 import _native as N
+    global GATE_CODES
+    GATE_CODES = N.GATE_CODES                       # the C ABI's gate kind codes
+    exe = str(tmp_path_factory.mktemp("emu") / "stage_emu")
+    cmd = ["g++", "-O2", "-std=c++17", "-I", CSRC, "-I", os.path.join(ROOT, "include"),
+           os.path.join(ROOT, "tests", "host_emu", "stage_emu.cpp"),
+           os.path.join(CSRC, "partition.cpp"), os.path.join(CSRC, "lower.cpp"), "-o", exe]
+    subprocess.run(cmd, check=True, capture_output=True)
+    return exe
+
+
+def run_emu(exe, tmp_path, circ, L, n_fixed, params, psi0, elem_bytes, rmax=4):
+    n = circ.n_qubits
+    params = [] if params is None else list(params)
+    buf = [struct.pack("<7i", n, L, n_fixed, len(params), len(circ.gates), elem_bytes, rmax)]
+    buf.append(struct.pack(f"<{len(params)}d", *params))
+    for g in circ.gates:
+        q = list(g.qubits) + [-1] * (2 - len(g.qubits))
+        a = list(g.angles) + [0.0] * (3 - len(g.angles))
+        buf.append(struct.pack("<5i3d", GATE_CODES[g.kind], len(g.qubits), q[0], q[1], g.param, *a))
+    buf.append(np.ascontiguousarray(psi0, dtype=np.complex128).tobytes())
+    fin, fout = tmp_path / "in.bin", tmp_path / "out.bin"
+    fin.write_bytes(b"".join(buf))
+    r = subprocess.run([exe, str(fin), str(fout)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    return np.frombuffer(fout.read_bytes(), dtype=np.complex128)
+
+
+TOL = {16: 1e-10, 8: 2e-5}
+GATE_CODES = {}
+
+
+@pytest.mark.parametrize("seed", range(16))
+@pytest.mark.parametrize("elem_bytes", [16, 8])
+def test_random_circuits(emu, tmp_path, seed, elem_bytes):
+    rng = np.random.default_rng(900 + seed)
+    n = int(rng.integers(2, 12))
+    L = int(rng.integers(1, n + 1))
+    n_fixed = int(rng.integers(0, min(4, L - 1) + 1)) if L > 1 else 0
+    circ = C.random_circuit(n, int(rng.integers(20, 160)), seed)
+    psi0 = C.random_state(n, seed)
+    got = run_emu(emu, tmp_path, circ, L, n_fixed, None, psi0, elem_bytes)
+    ref = S.simulate(circ, None, psi0)
+    assert np.linalg.norm(got - ref) <= TOL[elem_bytes]
+
+
+@pytest.mark.parametrize("elem_bytes", [16, 8])
+@pytest.mark.parametrize("n,L", [(10, 7), (12, 9), (11, 11)])
+def test_qft_roundtrip_pair_phases(emu, tmp_path, elem_bytes, n, L):
+    """QFT and its inverse: controlled phases between register bits fold into the
+    following real butterflies (pair phases); the rest become twiddles and slots."""
+    circ = C.qft_roundtrip(n)
+    psi0 = C.random_state(n, 3)
+    got = run_emu(emu, tmp_path, circ, L, min(4, L - 1), None, psi0, elem_bytes)
+    assert np.linalg.norm(got - psi0) <= TOL[elem_bytes]
+    half = C.Circuit(n, circ.gates[: len(circ.gates) // 2], 0)
+    got = run_emu(emu, tmp_path, half, L, min(4, L - 1), None, psi0, elem_bytes)
+    assert np.linalg.norm(got - S.simulate(half, None, psi0)) <= TOL[elem_bytes]
+
+
+@pytest.mark.parametrize("elem_bytes", [16, 8])
+@pytest.mark.parametrize("rmax", [2, 3, 4])
+def test_parametric_ansatz(emu, tmp_path, elem_bytes, rmax):
+    n = 9
+    circ = C.hea(n, 4)
+    p = C.hea_params(circ.n_params, 7)
+    psi0 = C.random_state(n, 7)
+    got = run_emu(emu, tmp_path, circ, 7, 3, p, psi0, elem_bytes, rmax)
+    assert np.linalg.norm(got - S.simulate(circ, p, psi0)) <= TOL[elem_bytes]
+
+
+@pytest.mark.parametrize("elem_bytes", [16, 8])
+def test_brickwork_config(emu, tmp_path, elem_bytes):
+    circ = C.brickwork(11, 10, 1)
+    psi0 = C.random_state(11, 1)
+    got = run_emu(emu, tmp_path, circ, 8, 4, None, psi0, elem_bytes)
+    assert np.linalg.norm(got - S.simulate(circ, None, psi0)) <= TOL[elem_bytes]
