@@ -5,12 +5,16 @@
 // semantics the kernels implement.  The test compares the result with the CPU oracle,
 // so the lowering is checked on the CPU.
 //
-//   stage_emu <in.bin> <out.bin>
+//   stage_emu fwd  <in.bin> <out.bin>     forward program
+//   stage_emu grad <in.bin> <out.bin>     forward, lambda = O psi, adjoint program
 // in:  int32 n, L, n_fixed, n_params, n_gates, elem_bytes (8 | 16), rmax;
 //      n_params doubles; n_gates x (int32 kind, nq, q0, q1, param; double a0, a1, a2);
-//      2^n x (re, im) doubles
-// out: 2^n x (re, im) doubles in canonical qubit order; exit status 0, or 2 with a
-//      message on stderr when the planner rejects the circuit
+//      2^n x (re, im) doubles (the input state);
+//      grad only: int32 n_terms; n_terms x (double coeff, n uint8 Pauli codes 0..3 = I X Y Z)
+// out: fwd:  2^n x (re, im) doubles in canonical qubit order;
+//      grad: double E, n_params doubles dE/dtheta, then the state after the adjoint
+//      program (the input state again) as 2^n x (re, im) doubles;
+//      exit status 0, or 2 with a message on stderr when the planner rejects the circuit
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -33,8 +37,11 @@ static uint64_t deposit(uint64_t x, const uint8_t* pos, int n) {
     return r;
 }
 
+// lam / slot_param / grad: adjoint programs carry lambda beside psi and accumulate
+// gradient ops (slot += Im <lam| P |psi>) into grad[slot_param[slot]]
 template <typename Real>
-static void run_packed(const Program& prog, int n, std::vector<cd>& psi) {
+static void run_packed(const Program& prog, int n, std::vector<cd>& psi, std::vector<cd>* lam = nullptr,
+                       std::vector<double>* grad = nullptr) {
     Packed pk;
     std::string err = pack(prog, n, sizeof(Real) == 8 ? 16 : 8, &pk);
     if (!err.empty()) {
@@ -66,17 +73,46 @@ static void run_packed(const Program& prog, int n, std::vector<cd>& psi) {
                     uint64_t fix = base;
                     for (int i = 0; i < TR; ++i)
                         if ((tid >> i) & 1) fix |= 1ull << st.tile_pos[G.thr_pos[i]];
+                    const int NV = lam ? 2 : 1;
                     std::vector<uint64_t> addr(1u << R);
-                    std::vector<cd> a(1u << R);
+                    std::vector<cd> av[2] = {std::vector<cd>(1u << R), std::vector<cd>(1u << R)};
                     for (int k = 0; k < (1 << R); ++k) {
                         uint64_t x = fix;
                         for (int j = 0; j < R; ++j)
                             if ((k >> j) & 1) x |= 1ull << st.tile_pos[G.reg_pos[j]];
                         addr[k] = x;
-                        a[k] = psi[x];
+                        av[0][k] = psi[x];
+                        if (lam) av[1][k] = (*lam)[x];
                     }
                     for (uint32_t oi = 0; oi < G.n_ops; ++oi) {
                         const DevOp<Real>& o = ops[st.op_off + G.op_off + oi];
+                        if (o.type >= OP_GRAD_X) {
+                            if (!lam) {
+                                fprintf(stderr, "gradient op in a forward program\n");
+                                exit(3);
+                            }
+                            const std::vector<cd>&ps = av[0], &la = av[1];
+                            double acc = 0;
+                            if (o.type == OP_GRAD_Z && o.u) {   // Z on the bit in ctrl_fix: one sign per thread
+                                for (int k = 0; k < (1 << R); ++k) acc += std::imag(std::conj(la[k]) * ps[k]);
+                                if (fix & o.ctrl_fix) acc = -acc;
+                            } else {
+                                for (int k = 0; k < (1 << R); ++k) {
+                                    if ((k >> o.j) & 1) continue;
+                                    const int k1 = k | (1 << o.j);
+                                    if (o.type == OP_GRAD_X)
+                                        acc += std::imag(std::conj(la[k]) * ps[k1] + std::conj(la[k1]) * ps[k]);
+                                    else if (o.type == OP_GRAD_Y)
+                                        acc += std::imag(std::conj(la[k]) * cd(0, -1) * ps[k1] + std::conj(la[k1]) * cd(0, 1) * ps[k]);
+                                    else
+                                        acc += std::imag(std::conj(la[k]) * ps[k] - std::conj(la[k1]) * ps[k1]);
+                                }
+                            }
+                            (*grad)[st.slot_off + o.slot] += acc;
+                            continue;
+                        }
+                        for (int v = 0; v < NV; ++v) {
+                        std::vector<cd>& a = av[v];
                         cd M[4] = {cd(o.m[0], o.m[1]), cd(o.m[2], o.m[3]), cd(o.m[4], o.m[5]), cd(o.m[6], o.m[7])};
                         if (o.type == OP_UR) {
                             M[0] = o.m[0];
@@ -154,11 +190,15 @@ static void run_packed(const Program& prog, int n, std::vector<cd>& psi) {
                             const cd w = phase();
                             for (int k = 0; k < (1 << R); ++k) a[k] *= w;
                         } else {
-                            fprintf(stderr, "op type %d in a forward program\n", (int)o.type);
+                            fprintf(stderr, "unknown op type %d\n", (int)o.type);
                             exit(3);
                         }
+                        }
                     }
-                    for (int k = 0; k < (1 << R); ++k) psi[addr[k]] = a[k];
+                    for (int k = 0; k < (1 << R); ++k) {
+                        psi[addr[k]] = av[0][k];
+                        if (lam) (*lam)[addr[k]] = av[1][k];
+                    }
                 }
             }
         }
@@ -176,11 +216,12 @@ static T rd(FILE* f) {
 }
 
 int main(int argc, char** argv) {
-    if (argc != 3) {
-        fprintf(stderr, "usage: stage_emu in.bin out.bin\n");
+    if (argc != 4 || (strcmp(argv[1], "fwd") != 0 && strcmp(argv[1], "grad") != 0)) {
+        fprintf(stderr, "usage: stage_emu fwd|grad in.bin out.bin\n");
         return 1;
     }
-    FILE* f = fopen(argv[1], "rb");
+    const bool want_grad = strcmp(argv[1], "grad") == 0;
+    FILE* f = fopen(argv[2], "rb");
     if (!f) return 1;
     const int n = rd<int32_t>(f), L = rd<int32_t>(f), nf = rd<int32_t>(f), np = rd<int32_t>(f);
     const int ng = rd<int32_t>(f), eb = rd<int32_t>(f), rmax = rd<int32_t>(f);
@@ -206,6 +247,17 @@ int main(int argc, char** argv) {
         const double re = rd<double>(f), im = rd<double>(f);
         x = cd(re, im);
     }
+    std::vector<double> coeff;
+    std::vector<std::vector<uint8_t>> pauli;
+    if (want_grad) {
+        const int nt = rd<int32_t>(f);
+        for (int t = 0; t < nt; ++t) {
+            coeff.push_back(rd<double>(f));
+            std::vector<uint8_t> c(n);
+            for (int q = 0; q < n; ++q) c[q] = rd<uint8_t>(f);
+            pauli.push_back(c);
+        }
+    }
     fclose(f);
     relabel(n, P.gates, &P.phys, &P.final_map);
     const uint64_t fixed = nf ? ((1ull << nf) - 1) : 0;
@@ -222,8 +274,49 @@ int main(int argc, char** argv) {
     }
     if (eb == 8) run_packed<float>(prog, n, psi);
     else run_packed<double>(prog, n, psi);
-    FILE* o = fopen(argv[2], "wb");
+    FILE* o = fopen(argv[3], "wb");
     if (!o) return 1;
+    if (want_grad) {
+        // lambda = O psi in the physical layout (qubit q sits at bit final_map[q]);
+        // (P psi)_x = f(x) psi_{x ^ xmask} for a Pauli string P
+        const uint64_t dim = psi.size();
+        std::vector<cd> lam(dim, 0.0);
+        for (size_t t = 0; t < pauli.size(); ++t) {
+            uint64_t xm = 0;
+            for (int q = 0; q < n; ++q)
+                if (pauli[t][q] == 1 || pauli[t][q] == 2) xm |= 1ull << P.final_map[q];
+            for (uint64_t x = 0; x < dim; ++x) {
+                const uint64_t y = x ^ xm;   // (P psi)_x = prod_q p_q(x_q <- y_q) psi_y
+                cd f = coeff[t];
+                for (int q = 0; q < n; ++q) {
+                    const int bx = (int)((x >> P.final_map[q]) & 1);
+                    if (pauli[t][q] == 2) f *= bx ? cd(0, 1) : cd(0, -1);   // Y|0> = i|1>, Y|1> = -i|0>
+                    else if (pauli[t][q] == 3 && bx) f = -f;
+                }
+                lam[x] += f * psi[y];
+            }
+        }
+        double E = 0;
+        for (uint64_t x = 0; x < dim; ++x) E += std::real(std::conj(psi[x]) * lam[x]);
+        Program bprog;
+        err = lower(P, np ? params.data() : nullptr, eb, rmax, true, &bprog);
+        if (!err.empty()) {
+            fprintf(stderr, "lower (adjoint): %s\n", err.c_str());
+            return 2;
+        }
+        std::vector<double> slots(bprog.slot_param.size(), 0.0), grad(np, 0.0);
+        if (eb == 8) run_packed<float>(bprog, n, psi, &lam, &slots);
+        else run_packed<double>(bprog, n, psi, &lam, &slots);
+        for (size_t i = 0; i < slots.size(); ++i) grad[bprog.slot_param[i]] += slots[i];
+        fwrite(&E, sizeof(double), 1, o);
+        fwrite(grad.data(), sizeof(double), grad.size(), o);
+        for (uint64_t x = 0; x < dim; ++x) {
+            const double v[2] = {psi[x].real(), psi[x].imag()};
+            fwrite(v, sizeof(double), 2, o);
+        }
+        fclose(o);
+        return 0;
+    }
     for (uint64_t y = 0; y < psi.size(); ++y) {   // physical -> canonical order
         uint64_t x = 0;
         for (int q = 0; q < n; ++q)

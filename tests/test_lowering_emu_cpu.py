@@ -1,10 +1,12 @@
 """The host planner's output executed on the CPU (no GPU): `tests/host_emu/stage_emu.cpp`
 runs the library's SWAP relabel, closeness-centrality partition, lowering (register
 groups, micro-ops, diagonal sinking, twiddles, phase slots, pair phases folded into
-real butterflies) and packing, then executes the packed forward program in double
-precision, tile by tile and thread by thread.  Its state must match the CPU oracle's
-gate-by-gate result: within 1e-10 for the complex128 packing (FP64 matrices and
-angles), within 2e-5 for the complex64 packing (FP32 matrices, 32-bit fixed-point
+real butterflies; adjoint programs with their gradient ops) and packing, then executes
+the packed programs in double precision, tile by tile and thread by thread.  The
+forward state must match the CPU oracle's gate-by-gate result, and the adjoint
+program's E and gradient the oracle's expectation value and parameter-shift gradient:
+within 1e-10 for the complex128 packing (FP64 matrices and angles), within the
+complex64 tolerances for the complex64 packing (FP32 matrices, 32-bit fixed-point
 phase turns)."""
 import os
 import struct
@@ -14,6 +16,8 @@ import numpy as np
 import pytest
 
 import circuits as C
+from oracle import gradients as GR
+from oracle import observables as O
 from oracle import statevector as S
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -35,7 +39,7 @@ def emu(tmp_path_factory):
     return exe
 
 
-def run_emu(exe, tmp_path, circ, L, n_fixed, params, psi0, elem_bytes, rmax=4):
+def run_emu(exe, tmp_path, circ, L, n_fixed, params, psi0, elem_bytes, rmax=4, obs=None):
     n = circ.n_qubits
     params = [] if params is None else list(params)
     buf = [struct.pack("<7i", n, L, n_fixed, len(params), len(circ.gates), elem_bytes, rmax)]
@@ -45,11 +49,20 @@ def run_emu(exe, tmp_path, circ, L, n_fixed, params, psi0, elem_bytes, rmax=4):
         a = list(g.angles) + [0.0] * (3 - len(g.angles))
         buf.append(struct.pack("<5i3d", GATE_CODES[g.kind], len(g.qubits), q[0], q[1], g.param, *a))
     buf.append(np.ascontiguousarray(psi0, dtype=np.complex128).tobytes())
+    if obs is not None:
+        buf.append(struct.pack("<i", len(obs.terms)))
+        for c, ps in obs.terms:
+            buf.append(struct.pack("<d", c) + bytes("IXYZ".index(ch) for ch in ps))
     fin, fout = tmp_path / "in.bin", tmp_path / "out.bin"
     fin.write_bytes(b"".join(buf))
-    r = subprocess.run([exe, str(fin), str(fout)], capture_output=True, text=True)
+    r = subprocess.run([exe, "grad" if obs is not None else "fwd", str(fin), str(fout)],
+                       capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
-    return np.frombuffer(fout.read_bytes(), dtype=np.complex128)
+    raw = fout.read_bytes()
+    if obs is None:
+        return np.frombuffer(raw, dtype=np.complex128)
+    vals = np.frombuffer(raw[: 8 * (1 + len(params))], dtype=np.float64)
+    return vals[0], vals[1:], np.frombuffer(raw[8 * (1 + len(params)):], dtype=np.complex128)
 
 
 TOL = {16: 1e-10, 8: 2e-5}
@@ -101,3 +114,56 @@ def test_brickwork_config(emu, tmp_path, elem_bytes):
     psi0 = C.random_state(11, 1)
     got = run_emu(emu, tmp_path, circ, 8, 4, None, psi0, elem_bytes)
     assert np.linalg.norm(got - S.simulate(circ, None, psi0)) <= TOL[elem_bytes]
+
+
+def _mixed_ansatz(n, layers, seed):
+    """Hardware-efficient layers (parametric RX / RY / RZ, CX / CZ) with fixed gates
+    sprinkled in, SWAPs among them (so the adjoint runs in a relabelled layout)."""
+    rng = np.random.default_rng(seed)
+    gates, p = [], 0
+    for _ in range(layers):
+        for q in range(n):
+            gates.append(C.Gate(("RX", "RY")[int(rng.integers(0, 2))], (q,), p)); p += 1
+            gates.append(C.Gate("RZ", (q,), p)); p += 1
+        for q in range(n - 1):
+            gates.append(C.Gate(("CX", "CZ")[int(rng.integers(0, 2))], (q, q + 1)))
+        for _ in range(3):
+            k = ("H", "T", "S", "CP", "U3", "SWAP")[int(rng.integers(0, 6))]
+            if k in ("CP", "SWAP"):
+                a, b = (int(x) for x in rng.choice(n, size=2, replace=False))
+                gates.append(C.Gate(k, (a, b), -1, (float(rng.uniform(-3, 3)),) if k == "CP" else ()))
+            elif k == "U3":
+                gates.append(C.Gate(k, (int(rng.integers(0, n)),), -1, tuple(float(x) for x in rng.uniform(-3, 3, 3))))
+            else:
+                gates.append(C.Gate(k, (int(rng.integers(0, n)),)))
+    return C.Circuit(n, gates, p)
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("elem_bytes", [16, 8])
+def test_adjoint_gradient(emu, tmp_path, seed, elem_bytes):
+    rng = np.random.default_rng(700 + seed)
+    n = int(rng.integers(6, 10))
+    L = int(rng.integers(5, n + 1))
+    circ = _mixed_ansatz(n, int(rng.integers(1, 4)), seed)
+    p = C.hea_params(circ.n_params, seed)
+    terms = list(C.tfim(n).terms)
+    for _ in range(6):
+        c = ["I"] * n
+        for q in rng.choice(n, size=int(rng.integers(1, 4)), replace=False):
+            c[q] = "XYZ"[int(rng.integers(0, 3))]
+        terms.append((float(rng.normal()), "".join(c)))
+    obs = C.Observable(n, terms)
+    psi0 = C.zero_state(n)
+    E, g, back = run_emu(emu, tmp_path, circ, L, min(4, L - 1), p, psi0, elem_bytes,
+                         4 if elem_bytes == 8 else 3, obs)
+    e_ref = O.expval(S.simulate(circ, p), obs)
+    g_ps = GR.parameter_shift(circ, p, obs)
+    if elem_bytes == 16:
+        assert abs(E - e_ref) <= 1e-10 * max(1.0, abs(e_ref))
+        assert np.linalg.norm(g - g_ps) <= 1e-9 * max(1.0, np.linalg.norm(g_ps))
+        assert np.linalg.norm(back - psi0) <= 1e-10
+    else:
+        assert abs(E - e_ref) <= 1e-6 * max(1.0, abs(e_ref))
+        assert np.linalg.norm(g - g_ps) <= 1e-4 * np.linalg.norm(g_ps)
+        assert np.linalg.norm(back - psi0) <= 1e-4
