@@ -7,6 +7,10 @@
 //
 //   stage_emu fwd  <in.bin> <out.bin>     forward program
 //   stage_emu grad <in.bin> <out.bin>     forward, lambda = O psi, adjoint program
+//   stage_emu bind <in.bin> <out.bin>     as grad, lowered the way batches are: the
+//                                         parametric rotations stay symbolic (bound
+//                                         dense ops) and their matrices are formed from
+//                                         the parameters after packing
 // in:  int32 n, L, n_fixed, n_params, n_gates, elem_bytes (8 | 16), rmax;
 //      n_params doubles; n_gates x (int32 kind, nq, q0, q1, param; double a0, a1, a2);
 //      2^n x (re, im) doubles (the input state);
@@ -39,14 +43,38 @@ static uint64_t deposit(uint64_t x, const uint8_t* pos, int n) {
 
 // lam / slot_param / grad: adjoint programs carry lambda beside psi and accumulate
 // gradient ops (slot += Im <lam| P |psi>) into grad[slot_param[slot]]
+// bound: the parameters of bound dense ops (F_BIND: term_off = parameter index, u = the
+// rotation kind, | BK_DAGGER for the adjoint, i.e. the angle negated), whose matrices
+// are written from the rotations' definitions, RX(t) = [[c, -i s], [-i s, c]],
+// RY(t) = [[c, -s], [s, c]], RZ(t) = diag(e^{-i t/2}, e^{i t/2}) with c = cos(t/2),
+// s = sin(t/2)
 template <typename Real>
 static void run_packed(const Program& prog, int n, std::vector<cd>& psi, std::vector<cd>* lam = nullptr,
-                       std::vector<double>* grad = nullptr) {
+                       std::vector<double>* grad = nullptr, const double* bound = nullptr) {
     Packed pk;
     std::string err = pack(prog, n, sizeof(Real) == 8 ? 16 : 8, &pk);
     if (!err.empty()) {
         fprintf(stderr, "pack: %s\n", err.c_str());
         exit(2);
+    }
+    if (bound) {
+        DevOp<Real>* bops = (DevOp<Real>*)(pk.blob.data() + pk.op_off);
+        for (size_t i = 0; i < pk.n_ops; ++i) {
+            DevOp<Real>& o = bops[i];
+            if (!(o.flags & F_BIND)) continue;
+            const double t = (o.u & BK_DAGGER) ? -bound[o.term_off] : bound[o.term_off];
+            const cd c(std::cos(0.5 * t), 0), is(0, std::sin(0.5 * t));
+            cd M[4];
+            switch (o.u & 3) {
+                case BK_RX: M[0] = c; M[1] = -is; M[2] = -is; M[3] = c; break;
+                case BK_RY: M[0] = c; M[1] = -std::sin(0.5 * t); M[2] = std::sin(0.5 * t); M[3] = c; break;
+                default: M[0] = c - is; M[1] = 0; M[2] = 0; M[3] = c + is; break;   // BK_RZ
+            }
+            for (int e = 0; e < 4; ++e) {
+                o.m[2 * e] = (Real)M[e].real();
+                o.m[2 * e + 1] = (Real)M[e].imag();
+            }
+        }
     }
     const uint8_t* b = pk.blob.data();
     const Stage* stages = (const Stage*)(b + pk.stage_off);
@@ -216,11 +244,12 @@ static T rd(FILE* f) {
 }
 
 int main(int argc, char** argv) {
-    if (argc != 4 || (strcmp(argv[1], "fwd") != 0 && strcmp(argv[1], "grad") != 0)) {
-        fprintf(stderr, "usage: stage_emu fwd|grad in.bin out.bin\n");
+    if (argc != 4 || (strcmp(argv[1], "fwd") != 0 && strcmp(argv[1], "grad") != 0 && strcmp(argv[1], "bind") != 0)) {
+        fprintf(stderr, "usage: stage_emu fwd|grad|bind in.bin out.bin\n");
         return 1;
     }
-    const bool want_grad = strcmp(argv[1], "grad") == 0;
+    const bool bind = strcmp(argv[1], "bind") == 0;
+    const bool want_grad = bind || strcmp(argv[1], "grad") == 0;
     FILE* f = fopen(argv[2], "rb");
     if (!f) return 1;
     const int n = rd<int32_t>(f), L = rd<int32_t>(f), nf = rd<int32_t>(f), np = rd<int32_t>(f);
@@ -260,6 +289,9 @@ int main(int argc, char** argv) {
     }
     fclose(f);
     relabel(n, P.gates, &P.phys, &P.final_map);
+    if (bind)   // a bound RZ is a dense op: its qubit must be local
+        for (size_t g = 0; g < P.gates.size(); ++g)
+            if (P.gates[g].kind == K_RZ && P.gates[g].param >= 0) P.phys[g].bound = true;
     const uint64_t fixed = nf ? ((1ull << nf) - 1) : 0;
     std::string err = partition_core(n, P.phys, L, fixed, (1ull << n) - 1, &P.top, &P.cc);
     if (!err.empty()) {
@@ -267,13 +299,15 @@ int main(int argc, char** argv) {
         return 2;
     }
     Program prog;
-    err = lower(P, np ? params.data() : nullptr, eb, rmax, false, &prog);
+    const double* lp = (np && !bind) ? params.data() : nullptr;   // bind: parameters stay symbolic
+    const double* bp = (np && bind) ? params.data() : nullptr;
+    err = lower(P, lp, eb, rmax, false, &prog, bind);
     if (!err.empty()) {
         fprintf(stderr, "lower: %s\n", err.c_str());
         return 2;
     }
-    if (eb == 8) run_packed<float>(prog, n, psi);
-    else run_packed<double>(prog, n, psi);
+    if (eb == 8) run_packed<float>(prog, n, psi, nullptr, nullptr, bp);
+    else run_packed<double>(prog, n, psi, nullptr, nullptr, bp);
     FILE* o = fopen(argv[3], "wb");
     if (!o) return 1;
     if (want_grad) {
@@ -299,14 +333,14 @@ int main(int argc, char** argv) {
         double E = 0;
         for (uint64_t x = 0; x < dim; ++x) E += std::real(std::conj(psi[x]) * lam[x]);
         Program bprog;
-        err = lower(P, np ? params.data() : nullptr, eb, rmax, true, &bprog);
+        err = lower(P, lp, eb, rmax, true, &bprog, bind);
         if (!err.empty()) {
             fprintf(stderr, "lower (adjoint): %s\n", err.c_str());
             return 2;
         }
         std::vector<double> slots(bprog.slot_param.size(), 0.0), grad(np, 0.0);
-        if (eb == 8) run_packed<float>(bprog, n, psi, &lam, &slots);
-        else run_packed<double>(bprog, n, psi, &lam, &slots);
+        if (eb == 8) run_packed<float>(bprog, n, psi, &lam, &slots, bp);
+        else run_packed<double>(bprog, n, psi, &lam, &slots, bp);
         for (size_t i = 0; i < slots.size(); ++i) grad[bprog.slot_param[i]] += slots[i];
         fwrite(&E, sizeof(double), 1, o);
         fwrite(grad.data(), sizeof(double), grad.size(), o);

@@ -39,7 +39,7 @@ def emu(tmp_path_factory):
     return exe
 
 
-def run_emu(exe, tmp_path, circ, L, n_fixed, params, psi0, elem_bytes, rmax=4, obs=None):
+def run_emu(exe, tmp_path, circ, L, n_fixed, params, psi0, elem_bytes, rmax=4, obs=None, bind=False):
     n = circ.n_qubits
     params = [] if params is None else list(params)
     buf = [struct.pack("<7i", n, L, n_fixed, len(params), len(circ.gates), elem_bytes, rmax)]
@@ -55,8 +55,8 @@ def run_emu(exe, tmp_path, circ, L, n_fixed, params, psi0, elem_bytes, rmax=4, o
             buf.append(struct.pack("<d", c) + bytes("IXYZ".index(ch) for ch in ps))
     fin, fout = tmp_path / "in.bin", tmp_path / "out.bin"
     fin.write_bytes(b"".join(buf))
-    r = subprocess.run([exe, "grad" if obs is not None else "fwd", str(fin), str(fout)],
-                       capture_output=True, text=True)
+    mode = "bind" if bind else ("grad" if obs is not None else "fwd")
+    r = subprocess.run([exe, mode, str(fin), str(fout)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
     raw = fout.read_bytes()
     if obs is None:
@@ -139,9 +139,12 @@ def _mixed_ansatz(n, layers, seed):
     return C.Circuit(n, gates, p)
 
 
+@pytest.mark.parametrize("bind", [False, True])
 @pytest.mark.parametrize("seed", range(4))
 @pytest.mark.parametrize("elem_bytes", [16, 8])
-def test_adjoint_gradient(emu, tmp_path, seed, elem_bytes):
+def test_adjoint_gradient(emu, tmp_path, seed, elem_bytes, bind):
+    """sv_grad's lowering (parameters bound at lowering) and the batched form's (bound
+    dense ops whose matrices are formed from the parameters after packing)."""
     rng = np.random.default_rng(700 + seed)
     n = int(rng.integers(6, 10))
     L = int(rng.integers(5, n + 1))
@@ -156,7 +159,7 @@ def test_adjoint_gradient(emu, tmp_path, seed, elem_bytes):
     obs = C.Observable(n, terms)
     psi0 = C.zero_state(n)
     E, g, back = run_emu(emu, tmp_path, circ, L, min(4, L - 1), p, psi0, elem_bytes,
-                         4 if elem_bytes == 8 else 3, obs)
+                         4 if elem_bytes == 8 else 3, obs, bind)
     e_ref = O.expval(S.simulate(circ, p), obs)
     g_ps = GR.parameter_shift(circ, p, obs)
     if elem_bytes == 16:
