@@ -11,6 +11,12 @@
 //                                         parametric rotations stay symbolic (bound
 //                                         dense ops) and their matrices are formed from
 //                                         the parameters after packing
+//   stage_emu gemm <in.bin> <out.bin>     tensor-core plan (header L = fusion width k,
+//                                         rmax = precision 1 TF32x3 / 2 BF16x3): each
+//                                         stage's B operand is decoded from the packed
+//                                         blob (hi + lo halves, 128-byte-swizzled rows)
+//                                         and applied to every state column in FP64;
+//                                         out: double n_stages, then the state
 // in:  int32 n, L, n_fixed, n_params, n_gates, elem_bytes (8 | 16), rmax;
 //      n_params doubles; n_gates x (int32 kind, nq, q0, q1, param; double a0, a1, a2);
 //      2^n x (re, im) doubles (the input state);
@@ -26,6 +32,7 @@
 #include <cstring>
 #include <vector>
 
+#include "gemm.h"
 #include "planner.h"
 
 using namespace svh;
@@ -233,6 +240,60 @@ static void run_packed(const Program& prog, int n, std::vector<cd>& psi, std::ve
     }
 }
 
+// Tensor-core stages: D = X Ut^T per column (X: the column's 2^keff local amplitudes as
+// interleaved (re, im) floats; Ut: the real embedding of the fused unitary, read back as
+// hi + lo from the 128-byte-swizzled K-major blob).
+static void run_gemm(const GemmProgram& gp, int prec, int n, std::vector<cd>& psi) {
+    auto sw = [](uint32_t r, uint32_t b) -> size_t {   // byte b of row r in an operand block
+        return (size_t)(r / 8) * 1024 + (r % 8) * 128 + ((((b / 16) ^ (r % 8)) % 8) * 16) + b % 16;
+    };
+    for (const GemmStage& st : gp.stages) {
+        const uint32_t N = st.N, kc = prec == 1 ? 32u : 64u;   // K elements per chunk
+        const size_t block = (size_t)N * 128;
+        const uint8_t* base = gp.ublob.data() + st.b_off;
+        std::vector<double> U((size_t)N * N);
+        for (uint32_t r = 0; r < N; ++r)
+            for (uint32_t kk = 0; kk < N; ++kk) {
+                const uint8_t* ch = base + (size_t)(kk / kc) * st.b_chunk_bytes;
+                const uint32_t kl = kk % kc;
+                double v = 0;
+                for (int half = 0; half < 2; ++half) {
+                    const uint8_t* q = ch + half * block;
+                    if (prec == 1) {
+                        float x;
+                        memcpy(&x, q + sw(r, kl * 4), 4);
+                        v += x;
+                    } else {
+                        uint16_t h;
+                        memcpy(&h, q + sw(r, kl * 2), 2);
+                        const uint32_t b = (uint32_t)h << 16;   // bfloat16: the top half of an FP32
+                        float x;
+                        memcpy(&x, &b, 4);
+                        v += x;
+                    }
+                }
+                U[(size_t)r * N + kk] = v;
+            }
+        const uint32_t D = 1u << st.keff;
+        std::vector<double> x(N), y(N);
+        for (uint64_t g = 0; g < (1ull << st.n_glob); ++g)
+            for (uint64_t c = 0; c < (1ull << st.ncol_bits); ++c) {
+                const uint64_t col = deposit(g, st.glob_pos, (int)st.n_glob) | deposit(c, st.col_pos, (int)st.ncol_bits);
+                for (uint32_t j = 0; j < D; ++j) {
+                    const cd a = psi[col | deposit(j, st.local_pos, (int)st.keff)];
+                    x[2 * j] = a.real();
+                    x[2 * j + 1] = a.imag();
+                }
+                for (uint32_t r = 0; r < N; ++r) {
+                    double acc = 0;
+                    for (uint32_t kk = 0; kk < N; ++kk) acc += U[(size_t)r * N + kk] * x[kk];
+                    y[r] = acc;
+                }
+                for (uint32_t j = 0; j < D; ++j) psi[col | deposit(j, st.local_pos, (int)st.keff)] = cd(y[2 * j], y[2 * j + 1]);
+            }
+    }
+}
+
 template <typename T>
 static T rd(FILE* f) {
     T v;
@@ -244,11 +305,13 @@ static T rd(FILE* f) {
 }
 
 int main(int argc, char** argv) {
-    if (argc != 4 || (strcmp(argv[1], "fwd") != 0 && strcmp(argv[1], "grad") != 0 && strcmp(argv[1], "bind") != 0)) {
-        fprintf(stderr, "usage: stage_emu fwd|grad|bind in.bin out.bin\n");
+    if (argc != 4 || (strcmp(argv[1], "fwd") != 0 && strcmp(argv[1], "grad") != 0 && strcmp(argv[1], "bind") != 0 &&
+                      strcmp(argv[1], "gemm") != 0)) {
+        fprintf(stderr, "usage: stage_emu fwd|grad|bind|gemm in.bin out.bin\n");
         return 1;
     }
     const bool bind = strcmp(argv[1], "bind") == 0;
+    const bool gemm = strcmp(argv[1], "gemm") == 0;
     const bool want_grad = bind || strcmp(argv[1], "grad") == 0;
     FILE* f = fopen(argv[2], "rb");
     if (!f) return 1;
@@ -292,11 +355,34 @@ int main(int argc, char** argv) {
     if (bind)   // a bound RZ is a dense op: its qubit must be local
         for (size_t g = 0; g < P.gates.size(); ++g)
             if (P.gates[g].kind == K_RZ && P.gates[g].param >= 0) P.phys[g].bound = true;
-    const uint64_t fixed = nf ? ((1ull << nf) - 1) : 0;
-    std::string err = partition_core(n, P.phys, L, fixed, (1ull << n) - 1, &P.top, &P.cc);
+    const uint64_t fixed = (nf && !gemm) ? ((1ull << nf) - 1) : 0;
+    std::string err = partition_core(n, P.phys, L, fixed, (1ull << n) - 1, &P.top, &P.cc, gemm);
     if (!err.empty()) {
         fprintf(stderr, "partition: %s\n", err.c_str());
         return 2;
+    }
+    if (gemm) {
+        P.gemm_k = L;
+        GemmProgram gp;
+        err = plan_gemm(P, np ? params.data() : nullptr, rmax, &gp);
+        if (!err.empty()) {
+            fprintf(stderr, "plan_gemm: %s\n", err.c_str());
+            return 2;
+        }
+        run_gemm(gp, rmax, n, psi);
+        FILE* o = fopen(argv[3], "wb");
+        if (!o) return 1;
+        const double nst = (double)gp.stages.size();
+        fwrite(&nst, sizeof(double), 1, o);
+        for (uint64_t y = 0; y < psi.size(); ++y) {   // physical -> canonical order
+            uint64_t x = 0;
+            for (int q = 0; q < n; ++q)
+                if ((y >> q) & 1) x |= 1ull << P.final_map[q];
+            const double v[2] = {psi[x].real(), psi[x].imag()};
+            fwrite(v, sizeof(double), 2, o);
+        }
+        fclose(o);
+        return 0;
     }
     Program prog;
     const double* lp = (np && !bind) ? params.data() : nullptr;   // bind: parameters stay symbolic

@@ -34,12 +34,13 @@ def emu(tmp_path_factory):
     exe = str(tmp_path_factory.mktemp("emu") / "stage_emu")
     cmd = ["g++", "-O2", "-std=c++17", "-I", CSRC, "-I", os.path.join(ROOT, "include"),
            os.path.join(ROOT, "tests", "host_emu", "stage_emu.cpp"),
-           os.path.join(CSRC, "partition.cpp"), os.path.join(CSRC, "lower.cpp"), "-o", exe]
+           os.path.join(CSRC, "partition.cpp"), os.path.join(CSRC, "lower.cpp"),
+           os.path.join(CSRC, "gemm_plan.cpp"), "-o", exe]
     subprocess.run(cmd, check=True, capture_output=True)
     return exe
 
 
-def run_emu(exe, tmp_path, circ, L, n_fixed, params, psi0, elem_bytes, rmax=4, obs=None, bind=False):
+def run_emu(exe, tmp_path, circ, L, n_fixed, params, psi0, elem_bytes, rmax=4, obs=None, bind=False, gemm=False):
     n = circ.n_qubits
     params = [] if params is None else list(params)
     buf = [struct.pack("<7i", n, L, n_fixed, len(params), len(circ.gates), elem_bytes, rmax)]
@@ -55,10 +56,12 @@ def run_emu(exe, tmp_path, circ, L, n_fixed, params, psi0, elem_bytes, rmax=4, o
             buf.append(struct.pack("<d", c) + bytes("IXYZ".index(ch) for ch in ps))
     fin, fout = tmp_path / "in.bin", tmp_path / "out.bin"
     fin.write_bytes(b"".join(buf))
-    mode = "bind" if bind else ("grad" if obs is not None else "fwd")
+    mode = "gemm" if gemm else ("bind" if bind else ("grad" if obs is not None else "fwd"))
     r = subprocess.run([exe, mode, str(fin), str(fout)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
     raw = fout.read_bytes()
+    if gemm:
+        return int(np.frombuffer(raw[:8], dtype=np.float64)[0]), np.frombuffer(raw[8:], dtype=np.complex128)
     if obs is None:
         return np.frombuffer(raw, dtype=np.complex128)
     vals = np.frombuffer(raw[: 8 * (1 + len(params))], dtype=np.float64)
@@ -170,3 +173,22 @@ def test_adjoint_gradient(emu, tmp_path, seed, elem_bytes, bind):
         assert abs(E - e_ref) <= 1e-6 * max(1.0, abs(e_ref))
         assert np.linalg.norm(g - g_ps) <= 1e-4 * np.linalg.norm(g_ps)
         assert np.linalg.norm(back - psi0) <= 1e-4
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("k", [5, 6, 7])
+@pytest.mark.parametrize("n,seed", [(8, 1), (11, 2), (14, 3)])
+def test_tensor_core_plan(emu, tmp_path, prec, k, n, seed):
+    """The tensor-core planner (strict partition, fused unitary, real embedding, hi / lo
+    split, 128-byte-swizzled B blob, local / column / global bit roles), decoded and
+    applied in FP64 (the state itself unsplit): only the split of the unitary remains,
+    about 2^-22 (TF32 pair) or 2^-17 (BF16 pair) relative per element, so 2e-7 (TF32x3)
+    and 2e-6 (BF16x3) per fused stage."""
+    if n < k + 1:
+        pytest.skip("narrower than the stage needs")
+    circ = C.brickwork(n, 10, seed)
+    psi0 = C.random_state(n, seed)
+    nst, got = run_emu(emu, tmp_path, circ, k, 0, None, psi0, 8, prec, gemm=True)
+    ref = S.simulate(circ, None, psi0)
+    assert nst >= 1
+    assert np.linalg.norm(got - ref) <= (2e-7 if prec == 1 else 2e-6) * nst
