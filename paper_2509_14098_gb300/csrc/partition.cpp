@@ -70,8 +70,14 @@ std::string partition_core(int nbits, const std::vector<PGate>& gates, int L, ui
 
     // --- Step A: DAG on bit positions (identical to the DAG on circuit wires,
     // because a SWAP touches both of its positions) and levels.
+    // A gate acts on at most two bits, so it has at most two predecessors (the last
+    // gate on each of its bits) and at most two successors (the next one on each).
     std::vector<int> last(nbits, -1);
-    std::vector<std::vector<int>> preds(G), succs(G);
+    struct Adj {
+        int n = 0;
+        int v[2];
+    };
+    std::vector<Adj> preds(G), succs(G);
     std::vector<uint32_t> level(G, 0);
     for (int i = 0; i < G; ++i) {
         int ps[2];
@@ -83,39 +89,49 @@ std::string partition_core(int nbits, const std::vector<PGate>& gates, int L, ui
         if (np == 2 && ps[0] > ps[1]) std::swap(ps[0], ps[1]);
         uint32_t lv = 0;
         for (int k = 0; k < np; ++k) {
-            preds[i].push_back(ps[k]);
-            succs[ps[k]].push_back(i);
+            preds[i].v[preds[i].n++] = ps[k];
+            succs[ps[k]].v[succs[ps[k]].n++] = i;
             lv = std::max(lv, level[ps[k]]);
         }
         level[i] = lv + 1;
         for (int k = 0; k < gates[i].nq; ++k) last[gates[i].p[k]] = i;
     }
 
-    // --- Step B backward: reachable sets and exact distance sums.
+    // --- Step B backward: reachable sets and exact distance sums.  The bitsets index
+    // gates by level order (pos), so a level band is a contiguous range of bits.  Every
+    // gate reachable from v has a level above l_v and levels 1..max all occur, so
+    //   dist(v) = sum over x in RN(v) of (l_x - l_v) = sum over l > l_v of |{x in RN(v): l_x >= l}|,
+    // each term a suffix count of the bitset from the first position of level l.
     const int W = (G + 63) / 64;
+    uint32_t max_level = 0;
+    for (int i = 0; i < G; ++i) max_level = std::max(max_level, level[i]);
+    std::vector<int> lstart(max_level + 2, 0), pos(G);   // lstart[l]: first position of level >= l
+    for (int i = 0; i < G; ++i) ++lstart[level[i] + 1];
+    for (uint32_t l = 1; l <= max_level + 1; ++l) lstart[l] += lstart[l - 1];
+    {
+        std::vector<int> next(lstart.begin(), lstart.end());   // counting sort by level
+        for (int i = 0; i < G; ++i) pos[i] = next[level[i]]++;
+    }
     std::vector<uint64_t> rn((size_t)G * (size_t)W, 0);
-    std::vector<uint32_t> reach(G, 0);
+    std::vector<uint32_t> reach(G, 0), cum(W + 1, 0);
     std::vector<uint64_t> dist(G, 0);
     for (int v = G - 1; v >= 0; --v) {
         uint64_t* r = &rn[(size_t)v * W];
-        for (int w : succs[v]) {
+        for (int e = 0; e < succs[v].n; ++e) {
+            const int w = succs[v].v[e];
             const uint64_t* rw = &rn[(size_t)w * W];
             for (int k = 0; k < W; ++k) r[k] |= rw[k];
-            r[w >> 6] |= 1ull << (w & 63);
+            r[pos[w] >> 6] |= 1ull << (pos[w] & 63);
         }
-        uint64_t sum_level = 0;
-        uint32_t cnt = 0;
-        for (int k = 0; k < W; ++k) {
-            uint64_t x = r[k];
-            while (x) {
-                int b = __builtin_ctzll(x);
-                x &= x - 1;
-                sum_level += level[k * 64 + b];
-                ++cnt;
-            }
+        cum[W] = 0;   // cum[k]: bits set in words k.. of r
+        for (int k = W - 1; k >= 0; --k) cum[k] = cum[k + 1] + (uint32_t)popc64(r[k]);
+        uint64_t d = 0;
+        for (uint32_t l = level[v] + 1; l <= max_level; ++l) {
+            const int a = lstart[l];
+            d += cum[(a >> 6) + 1] + (uint32_t)popc64(r[a >> 6] >> (a & 63));
         }
-        reach[v] = cnt;
-        dist[v] = sum_level - (uint64_t)cnt * level[v];
+        reach[v] = cum[0];
+        dist[v] = d;
     }
     if (ccout) {
         ccout->reach = reach;
@@ -135,32 +151,35 @@ std::string partition_core(int nbits, const std::vector<PGate>& gates, int L, ui
     std::vector<uint64_t> need(G);
     for (int i = 0; i < G; ++i) need[i] = need_mask(gates[i], strict);
     std::vector<char> done(G, 0);
-    auto ready = [&](int i) {
-        for (int p : preds[i])
-            if (!done[p]) return false;
-        return true;
+    std::vector<int> pending(G);   // predecessors not yet done: ready <=> 0
+    for (int i = 0; i < G; ++i) pending[i] = preds[i].n;
+    auto finish = [&](int i) {
+        done[i] = 1;
+        for (int e = 0; e < succs[i].n; ++e) --pending[succs[i].v[e]];
     };
     const int width = std::min(L, popc64(universe | fixed));
     int n_done = 0;
+    int first = 0;   // every gate below this index is done
     while (n_done < G) {
         uint64_t local = fixed;
         std::vector<uint32_t> stage;
         for (;;) {
-            bool changed = true;
-            while (changed) {
-                changed = false;
-                for (int i = 0; i < G; ++i) {
-                    if (!done[i] && (need[i] & ~local) == 0 && ready(i)) {
-                        done[i] = 1;
-                        ++n_done;
-                        stage.push_back((uint32_t)i);
-                        changed = true;
-                    }
+            // Absorb to the fixed point in gate order.  Gates are in topological order
+            // (predecessors have smaller indices) and the local set does not change
+            // while absorbing, so one pass reaches the fixed point: a gate skipped
+            // because a predecessor was not done stays blocked, since that predecessor
+            // was visited earlier in the same pass and could not be absorbed either.
+            for (int i = first; i < G; ++i) {
+                if (!done[i] && pending[i] == 0 && (need[i] & ~local) == 0) {
+                    finish(i);
+                    ++n_done;
+                    stage.push_back((uint32_t)i);
                 }
             }
+            while (first < G && done[first]) ++first;
             int best = -1;
-            for (int i = 0; i < G; ++i) {
-                if (done[i] || !ready(i)) continue;
+            for (int i = first; i < G; ++i) {
+                if (done[i] || pending[i] != 0) continue;
                 if (popc64(local | need[i]) > L) continue;
                 if (best < 0 || cc_greater(i, best)) best = i;
             }
