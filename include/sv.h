@@ -207,7 +207,8 @@ sv_status sv_partition_ex(const sv_circuit* circuit, uint32_t L, uint32_t n_fixe
 sv_status sv_partition_gemm(const sv_circuit* circuit, uint32_t k, sv_plan** out);
 
 /* Layout of a tensor-core plan's stages for prec (SV_PREC_TF32X3 / SV_PREC_BF16X3),
- * computed on the host (no GPU): keff[s] = local qubits of stage s's fused unitary (6
+ * computed on the host (no GPU; an introspection call with no counterpart in the paper,
+ * whose partitions are the fused stages of Sec. 4.2 run without exemptions): keff[s] = local qubits of stage s's fused unitary (6
  * or 7), resident[s] = 1 when its B operand stays in shared memory for the launch,
  * nslot[s] = depth of its operand ring, lane_roles[6 s + i] = what producer lane bit i
  * (i < 5) and the 16-byte pair bit (i = 5) select: 0..4 = a bit of the amplitude index
@@ -266,7 +267,8 @@ sv_status sv_permute(sv_handle h, const uint32_t* phys_of_qubit);
 sv_status sv_expval(sv_handle h, const sv_observable* obs, double* out);
 
 /* The Pauli-sweep grouping sv_expval uses for obs on an n_qubits state of dtype, computed
- * on the host (no GPU, no handle): *n_sweeps sweeps; tile_masks[i] = the qubits held in
+ * on the host (no GPU, no handle; an introspection call with no counterpart in the
+ * paper): *n_sweeps sweeps; tile_masks[i] = the qubits held in
  * sweep i's shared-memory tile, reg_masks[i] = those of them held in registers (each
  * thread's element index), n_terms[i] = the terms evaluated in sweep i (every diagonal
  * term in sweep 0).  The arrays may be NULL (query *n_sweeps first); each must hold
