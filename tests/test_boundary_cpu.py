@@ -70,6 +70,19 @@ def test_partition_bit_exact(sv, c, L, nf):
     assert r == size and d == dist and lv == level
 
 
+def test_partition_closeness_choice_golden(sv):
+    """The C++ partitioner on the hand-derived closeness-choice cases (Sec. 4.2)."""
+    import json
+    cases = json.load(open(os.path.join(ROOT, "tests", "golden", "cc_choice.json")))["cases"]
+    for case in cases:
+        c = C.Circuit(case["n_qubits"], [C.Gate(k, tuple(q)) for k, q in case["gates"]])
+        got, _, plan = _native_partition(sv, c, case["L"], 0)
+        want = [(sum(1 << b for b in s["local"]), s["gates"]) for s in case["stages"]]
+        assert got == want, case["name"]
+        r, d, lv = plan.centrality()
+        assert r == [len(x) for x in case["reach"]] and d == case["dist"] and lv == case["levels"]
+
+
 @pytest.mark.parametrize("seed", range(12))
 def test_partition_bit_exact_random(sv, seed):
     rng = np.random.default_rng(seed)

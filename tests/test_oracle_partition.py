@@ -1,8 +1,10 @@
 """Pins for the oracle partitioner: the paper's worked example, brute-force closeness
 on tiny DAGs, NetworkX's closeness, validator invariants, execution equivalence."""
+import inspect
 import itertools
 import json
 import os
+import types
 from fractions import Fraction
 
 import numpy as np
@@ -35,6 +37,49 @@ def test_ghz3_paper_example():
     d = gold["derived_not_printed"]
     assert size == d["reach_size"] and dist == d["dist"]
     assert cc == [Fraction(a, b) for a, b in d["cc_numerator_denominator"]]
+
+
+def _cc_cases():
+    return json.load(open(os.path.join(GOLD, "cc_choice.json")))["cases"]
+
+
+def _cc_circuit(case):
+    return C.Circuit(case["n_qubits"], [C.Gate(k, tuple(q)) for k, q in case["gates"]])
+
+
+def _stages_match(partition_fn, case):
+    stages, _ = partition_fn(_cc_circuit(case), case["L"])
+    return [(sorted(loc), ids) for loc, ids in stages] == [(s["local"], s["gates"]) for s in case["stages"]]
+
+
+@pytest.mark.parametrize("case", _cc_cases(), ids=lambda c: c["name"])
+def test_closeness_choice_golden(case):
+    """Hand-derived cases in which the highest-closeness choice (Sec. 4.2, step 3)
+    decides the partitions: levels, reachable sets, distance sums, exact closeness
+    and the stage lists."""
+    c = _cc_circuit(case)
+    _, succs, level = P.build_dag(c)
+    rn, dist = P.reach_and_dist(succs, level)
+    assert level == case["levels"]
+    assert [sorted(i for i in range(len(level)) if (r >> i) & 1) for r in rn] == case["reach"]
+    assert dist == case["dist"]
+    cc, _, _, _ = P.closeness(c)
+    assert cc == [Fraction(a, b) for a, b in case["cc"]]
+    assert _stages_match(P.partition, case)
+    assert P.validate(c, P.partition(c, case["L"])[0], case["L"])[0]
+
+
+def test_closeness_choice_golden_catches_planted_mistakes():
+    """The golden cases fail an oracle whose choice takes the lowest closeness first,
+    or breaks ties towards the higher gate index (mutations planted in a copy of the
+    oracle's source, on the CPU)."""
+    src = inspect.getsource(P)
+    assert src.count("cc[i] > cc[best]") == 1
+    cases = _cc_cases()
+    for mutated in ("cc[i] < cc[best]", "cc[i] >= cc[best]"):
+        mod = types.ModuleType("mutated_partition")
+        exec(compile(src.replace("cc[i] > cc[best]", mutated), "mutated_partition", "exec"), mod.__dict__)
+        assert not all(_stages_match(mod.partition, case) for case in cases), mutated
 
 
 def _brute_force_closeness(circuit):
