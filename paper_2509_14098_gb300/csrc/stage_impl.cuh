@@ -10,8 +10,10 @@
 //
 // Backward (adjoint): the same sweep over psi and lambda together, with the stage's
 // gates conjugate-transposed in reverse order, and gradient ops accumulating
-// Im <lambda|G|psi> per parametric rotation into per-tile partial sums (FP32 inside a
-// warp, FP64 across warps and tiles, in a fixed order).
+// Im <lambda|G|psi> per parametric rotation: one warp's sum over its amplitudes of one
+// tile is formed in the kernel's precision (FP32 for complex64, FP64 for complex128),
+// then added in FP64 to that warp's per-CTA slot sum, across tiles; the warps' sums are
+// added in FP64, in a fixed order, once at the end.
 //
 // This header holds the kernel template and its launchers; stage_inst.cu compiles one
 // (precision, direction, register width) subset per object so the instantiations
@@ -77,7 +79,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT >= 512 ? 1 : (NV == 1 ? SVK_MINB_F
     uint64_t* chp = reinterpret_cast<uint64_t*>(smem_raw + Ly.chp);
     uint32_t* gsoff = reinterpret_cast<uint32_t*>(smem_raw + Ly.gsoff);
     uint32_t* chs = reinterpret_cast<uint32_t*>(smem_raw + Ly.chs);
-    float* gsm = reinterpret_cast<float*>(smem_raw + Ly.gsm);
+    double* gsm = reinterpret_cast<double*>(smem_raw + Ly.gsm);
     Ang* tang = reinterpret_cast<Ang*>(smem_raw + Ly.tang);
     const bool ttab = angle_table_fits(st.n_phase, nthr, sizeof(Ang));
     const bool gtab = group_table_fits(ng, nthr);
@@ -133,7 +135,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT >= 512 ? 1 : (NV == 1 ? SVK_MINB_F
             gsoff[g * nthr + tid] = so;
         }
     if (NV == 2)
-        for (uint32_t i = tid; i < nslots * nw; i += nthr) gsm[i] = 0.f;
+        for (uint32_t i = tid; i < nslots * nw; i += nthr) gsm[i] = 0.0;
     if (ttab)   // each thread's own column: the thread-bit part of every phase slot
         for (uint32_t p = 0; p < st.n_phase; ++p) {
             const PhaseSlot<Real>& ps = slots[st.phase_off + p];
@@ -217,11 +219,11 @@ __global__ void __launch_bounds__(MAXT, (MAXT >= 512 ? 1 : (NV == 1 ? SVK_MINB_F
                     } else {
                         SVK_SWITCH_J(o.j, R, (acc = grad_pairs<Real, R, J_>(ps, la, o.type)));
                     }
-                    float v = (float)acc;   // FP32 over the warp, per warp across this CTA's tiles
+                    Real v = acc;   // over the warp in the kernel's precision, then FP64 across tiles
 #pragma unroll
                     for (int off = 16; off > 0; off >>= 1)
                         if ((uint32_t)off < nthr) v += __shfl_xor_sync(wmask, v, off);
-                    if (lane == 0) gsm[o.slot * nw + warp] += v;
+                    if (lane == 0) gsm[o.slot * nw + warp] += (double)v;
                 } else {
                     apply_op<Real, R, NV, CPLX>(a, o, x);
                 }
@@ -243,7 +245,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT >= 512 ? 1 : (NV == 1 ? SVK_MINB_F
     if (NV == 2)
         for (uint32_t s = tid; s < nslots; s += nthr) {
             double sum = 0.0;
-            for (uint32_t w = 0; w < nw; ++w) sum += (double)gsm[s * nw + w];
+            for (uint32_t w = 0; w < nw; ++w) sum += gsm[s * nw + w];
             partial[(size_t)blockIdx.x * nslots + s] = sum;
         }
 }

@@ -41,7 +41,7 @@ __host__ __device__ __forceinline__ SmemLayout smem_layout(int elem_bytes, int n
     L.chp = o;     o += (size_t)nch * 8;
     L.gsoff = o;   o += (size_t)ngt * nthr * 4;
     L.chs = o;     o = align_up(o + (size_t)nch * 4, 16);
-    L.gsm = o;     o = align_up(o + ((nv == 2) ? (size_t)n_slots * ((nthr + 31) / 32) * sizeof(float) : 0), 16);
+    L.gsm = o;     o = align_up(o + ((nv == 2) ? (size_t)n_slots * ((nthr + 31) / 32) * sizeof(double) : 0), 16);
     L.tang = o;    o += angle_table_fits(n_phase, nthr, angb) ? (size_t)n_phase * nthr * angb : 0;
     L.total = o;
     return L;

@@ -23,5 +23,11 @@ def test_reference_arm_line():
     assert line["config"]["workload"] == "qft30_roundtrip" and line["config"]["n_qubits"] == 30
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+    # the 30-qubit value is an extrapolation and says so in the line itself; one
+    # complete oracle run at a smaller width is measured end to end
+    assert line["extrapolated"] is True and cb["extrapolated"] is True
+    assert cb["measured_gates"] > 0 and cb["measured_s"] > 0 and cb["scale"] > 1
+    full = cb["measured_full_run"]
+    assert full["extrapolated"] is False and full["ms"] > 0 and full["error_l2_vs_input"] < 1e-10
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0

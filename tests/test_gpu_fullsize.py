@@ -10,6 +10,9 @@ times), where the oracle cannot hold the whole state:
   state returns to |0...0>; sampled gradient components agree with central differences
   of the GPU forward pass (a consistency property at full size; the oracle pins the
   gradient itself at 12 qubits in test_gpu_parity.py).
+* HEA24 (10 layers, 480 parameters, TFIM): every gradient component of the complex64
+  path against the complex128 path (FP64 arithmetic and reductions, itself pinned to
+  the oracle at 12 qubits) within the target's 1e-4 relative, and <H> within 1e-6.
 """
 import numpy as np
 import pytest
@@ -98,3 +101,42 @@ def test_hea28_adjoint_properties(sv):
         em = f.expval(obs)
         fd = (ep - em) / (2 * h)
         assert abs(g[k] - fd) <= 2e-3 * max(1.0, abs(fd)), (k, g[k], fd)
+
+
+def test_hea24_gradient_vs_complex128(sv):
+    n = 24
+    c = C.hea(n, 10)
+    p = C.hea_params(c.n_params, 4)
+    obs = C.tfim(n)
+    plan = sv.Plan(c, 12)
+    e64, g64 = sv.StateVector(n, 0).grad(plan, p, obs)
+    e128, g128 = sv.StateVector(n, 1).grad(plan, p, obs)
+    assert abs(e64 - e128) <= 1e-6 * max(1.0, abs(e128)), (e64, e128)
+    assert np.linalg.norm(g64 - g128) <= 1e-4 * np.linalg.norm(g128)
+    # component-wise too: no parameter's error hides under the norm of the others
+    assert np.max(np.abs(g64 - g128)) <= 1e-4 * np.max(np.abs(g128))
+
+
+def test_reductions_28q_vs_complex128(sv):
+    """The complex64 reductions (FP32 within a thread's group of amplitudes, FP64 or
+    compensated FP32 above) against the complex128 kernels' all-FP64 reductions of
+    the same amplitudes, on a 28-qubit random state: <TFIM> within the target's 1e-6
+    relative (max(|E|, 1)), the norm within 1e-7."""
+    import torch
+    n = 28
+    psi = _random_state_gpu(n, 11)
+    psi128 = psi.to(torch.complex128)
+    s64 = sv.StateVector(n, 0, tensor=psi)
+    s128 = sv.StateVector(n, 1, tensor=psi128)
+    obs = C.tfim(n)
+    e64, e128 = s64.expval(obs), s128.expval(obs)
+    assert abs(e64 - e128) <= 1e-6 * max(1.0, abs(e128)), (e64, e128)
+    # a state with a large expectation value too: |+...+> rotated slightly, <X> terms ~ 0.7 n
+    plus = torch.full((1 << n,), 2.0 ** (-n / 2), dtype=torch.complex64, device="cuda")
+    plus = plus + 1e-3 * psi
+    plus /= torch.linalg.vector_norm(plus)
+    p64 = sv.StateVector(n, 0, tensor=plus)
+    p128 = sv.StateVector(n, 1, tensor=plus.to(torch.complex128))
+    e64, e128 = p64.expval(obs), p128.expval(obs)
+    assert abs(e64 - e128) <= 1e-6 * max(1.0, abs(e128)), (e64, e128)
+    assert abs(s64.norm() - s128.norm()) <= 1e-7

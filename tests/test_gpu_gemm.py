@@ -2,12 +2,16 @@
 
 Each partition (no exemptions, fusion width k) is one dense unitary applied as a GEMM
 with three tensor-core products (hi*hi + lo*hi + hi*lo) accumulated in FP32 in tensor
-memory.  Bound: the split keeps ~21 (TF32x3) or ~16 (BF16x3) significant bits per
-product, but each output element of a fused stage is accumulated over K = 2^(k+1)
-terms in about 3 K / 8 tensor-core accumulation steps whose FP32 additions carry no
-IEEE rounding guarantee, i.e. up to ~3 (K / 8) 2^-23 relative per stage (~1e-5 at
-K = 256).  The tolerance is therefore 2e-5 per fused stage, accumulated over the stages,
-for both precisions.
+memory.  Error bound per fused stage, from the arithmetic: every output element sums
+K = 2^(k_eff + 1) real products (k_eff = max(k, 6): the MMA's N is at least 128) in at
+most 3 K / 8 tensor-core accumulation steps (K / 8 per product for TF32, K / 16 for
+BF16), whose FP32 additions carry no IEEE rounding guarantee: up to 2^-23 relative each,
+i.e. eps(K) = 3 (K / 8) 2^-23 per stage (5.7e-6 at K = 128, 1.1e-5 at K = 256).  The
+split itself keeps ~22 (TF32x3) or ~16 (BF16x3) significant bits per product; its error
+is independent between stages and measured well inside eps.  The state bound is the sum
+of eps over the plan's stages (`derived_bound`).  At 26 and 32 qubits (60-97 stages) the
+measured error is 5e-5 to 1e-4: the target's 2e-5 on the state is missed there, and the
+tests hold the derived bound instead of widening the target.
 """
 import numpy as np
 import pytest
@@ -29,12 +33,21 @@ def sv():
     return pkg
 
 
+def derived_bound(plan):
+    """Sum over the fused stages of eps(K) = 3 (K / 8) 2^-23, K = 2^(k_eff + 1)."""
+    total = 0.0
+    for mask, _ in plan.stages():
+        K = 2 ** (max(6, bin(mask).count("1")) + 1)
+        total += 3 * (K / 8) * 2.0 ** -23
+    return total
+
+
 def _run(sv, circ, k, prec, psi0):
     plan = sv.Plan(circ, k, gemm=True)
     st = sv.StateVector(circ.n_qubits)
     st.set_host(psi0)
     st.run(plan, None, prec)
-    return st.get_host().astype(np.complex128), len(plan.stages())
+    return st.get_host().astype(np.complex128), plan
 
 
 @pytest.mark.parametrize("k", [5, 6, 7])
@@ -43,11 +56,11 @@ def test_brickwork_gemm(sv, k, prec):
     n = 16
     circ = C.brickwork(n, 12, 3)
     psi0 = C.random_state(n, 3)
-    got, nst = _run(sv, circ, k, prec, psi0)
+    got, plan = _run(sv, circ, k, prec, psi0)
     ref = S.simulate(circ, None, psi0)
     err = float(np.linalg.norm(got - ref))
-    print(f"brick16 k={k} prec={prec} stages={nst} err={err:.3e}")
-    bound = 2e-5 * nst
+    bound = derived_bound(plan)
+    print(f"brick16 k={k} prec={prec} stages={len(plan.stages())} err={err:.3e} bound={bound:.3e}")
     assert err <= bound, (err, bound)
 
 
@@ -59,11 +72,11 @@ def test_random_circuits_gemm(sv, seed, prec):
     k = int(rng.integers(5, 8))
     circ = C.random_circuit(n, int(rng.integers(40, 200)), seed)
     psi0 = C.random_state(n, seed)
-    got, nst = _run(sv, circ, k, prec, psi0)
+    got, plan = _run(sv, circ, k, prec, psi0)
     ref = S.simulate(circ, None, psi0)
     err = float(np.linalg.norm(got - ref))
-    print(f"random n={n} k={k} prec={prec} stages={nst} err={err:.3e}")
-    bound = 2e-5 * nst
+    bound = derived_bound(plan)
+    print(f"random n={n} k={k} prec={prec} stages={len(plan.stages())} err={err:.3e} bound={bound:.3e}")
     assert err <= bound, (err, bound)
 
 
@@ -85,6 +98,78 @@ def test_gemm_errors(sv):
         sv.Plan(circ, 8, gemm=True)
 
 
+@pytest.fixture(scope="module")
+def brick26():
+    """The precision workload at 26 qubits: circuit, complex64-rounded input, and the
+    oracle's sampled amplitudes and <Z_q> (tests/golden/brick26_oracle.json, written by
+    make_brick26_oracle.py beside it, which calls the oracle only)."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "brick26_oracle.json")))
+    n = gold["n_qubits"]
+    circ = C.brickwork(n, gold["depth"], gold["circuit_seed"])
+    psi0 = C.random_state(n, gold["circuit_seed"]).astype(np.complex64)
+    return circ, psi0, gold
+
+
+def _z_expectations(sv, st, n):
+    out = []
+    for q in range(n):
+        s = ["I"] * n
+        s[q] = "Z"
+        out.append(st.expval(C.Observable(n, [(1.0, "".join(s))])))
+    return np.array(out)
+
+
+@pytest.fixture(scope="module")
+def brick26_c128(sv, brick26):
+    """The complex128 CUDA-core run of the 26-qubit workload, pinned to the oracle."""
+    import torch
+    circ, psi0, gold = brick26
+    n = circ.n_qubits
+    ref = sv.StateVector(n, sv.SV_C128)
+    ref.set_host(psi0.astype(np.complex128))
+    ref.run(sv.Plan(circ, 11))
+    got = ref.get_host()
+    idx = np.array(gold["indices"])
+    amp = np.array([complex(a, b) for a, b in gold["amplitudes"]])
+    # the complex128 bound 1e-12 on the whole vector bounds every amplitude
+    assert np.max(np.abs(got[idx] - amp)) <= 1e-12
+    assert np.max(np.abs(_z_expectations(sv, ref, n) - np.array(gold["z_expectations"]))) <= 2e-12
+    ref.close()
+    torch.cuda.empty_cache()
+    return got
+
+
+@pytest.mark.parametrize("k", [5, 6, 7])
+@pytest.mark.parametrize("prec", [1, 2])
+def test_brick26_vs_oracle(sv, brick26, brick26_c128, k, prec):
+    """The precision workload at 26 qubits: every fused stage's launch walks many tiles
+    per CTA (2^(26 - k_eff - 7) tiles on 152 CTAs), so the accumulator double buffer,
+    the tile walk and, at k = 7, the streamed-B ring run across tiles.  The whole vector
+    is compared with the complex128 run (pinned above to the oracle's samples), and the
+    oracle's sampled amplitudes and <Z_q> directly: each |psi_i - ref_i| and each
+    |<Z_q> - ref| / 2 is at most the vector error, so both are held to the bound."""
+    circ, psi0, gold = brick26
+    n = circ.n_qubits
+    plan = sv.Plan(circ, k, gemm=True)
+    st = sv.StateVector(n)
+    st.set_host(psi0)
+    st.run(plan, None, prec)
+    got = st.get_host().astype(np.complex128)
+    bound = derived_bound(plan)
+    err = float(np.linalg.norm(got - brick26_c128))
+    idx = np.array(gold["indices"])
+    amp = np.array([complex(a, b) for a, b in gold["amplitudes"]])
+    samp = float(np.max(np.abs(got[idx] - amp)))
+    zerr = float(np.max(np.abs(_z_expectations(sv, st, n) - np.array(gold["z_expectations"]))))
+    st.close()
+    print(f"brick26 k={k} prec={prec} stages={len(plan.stages())} err_vs_c128={err:.3e} "
+          f"max_sample_err={samp:.3e} max_Z_err={zerr:.3e} bound={bound:.3e} target=2e-5")
+    assert err <= bound, (err, bound)
+    assert samp <= bound and zerr <= 2 * bound
+
+
 @pytest.mark.parametrize("k", [5, 6, 7])
 @pytest.mark.parametrize("prec", [1, 2])
 def test_brick20_vs_complex128(sv, k, prec):
@@ -97,8 +182,8 @@ def test_brick20_vs_complex128(sv, k, prec):
     ref.set_host(psi0)
     ref.run(sv.Plan(circ, 11))
     r = ref.get_host()
-    got, nst = _run(sv, circ, k, prec, psi0.astype(np.complex64))
+    got, plan = _run(sv, circ, k, prec, psi0.astype(np.complex64))
     err = float(np.linalg.norm(got - r))
-    print(f"brick20 k={k} prec={prec} stages={nst} err={err:.3e}")
-    bound = 2e-5 * nst
+    bound = derived_bound(plan)
+    print(f"brick20 k={k} prec={prec} stages={len(plan.stages())} err={err:.3e} bound={bound:.3e}")
     assert err <= bound, (err, bound)
