@@ -236,6 +236,26 @@ sv_status sv_plan_centrality(const sv_plan* plan, uint32_t* reach, uint64_t* dis
 /* Free a plan. */
 sv_status sv_plan_destroy(sv_plan* plan);
 
+/* Generate and compile ahead of time the complex64 stage kernels of a plan (Sec. 4.3,
+ * "From Partitions to Code": each partition becomes one generated kernel with its
+ * tile geometry, register groups and gate sequence compiled in; here compiled at run
+ * time with NVRTC for sm_103a).  sv_run / sv_grad on complex64 states generate and
+ * compile the same kernels on first use; this call lets a caller pay that cost before
+ * a timed or latency-critical loop.  Kernels are cached for the life of the process
+ * by source text; their source depends on the partition's structure only (gate kinds
+ * and bit positions), not on angle values, so one compile serves every parameter
+ * value.  which: bit 0 = forward sweeps (sv_run), bit 1 = adjoint sweeps (sv_grad).
+ * params: host array of n_params angles (NULL if n_params == 0).  n_kernels
+ * (nullable): stage kernels of the plan (cache hits included).  Host only: needs no
+ * GPU.  Errors: SV_ERR_ARG, SV_ERR_UNSUPPORTED (tensor-core plan, unsupported
+ * parameter kind), SV_ERR_CUDA (the compiler failed; sv_last_error has its log). */
+sv_status sv_plan_compile(const sv_plan* plan, const double* params, uint32_t which, uint32_t* n_kernels);
+
+/* Counters of the run-time compiled stage kernels since the library was loaded: NVRTC
+ * compilations, cache hits, and the compile wall time in milliseconds (any pointer may
+ * be NULL).  Host only. */
+sv_status sv_jit_stats(uint64_t* compiles, uint64_t* cache_hits, double* compile_ms);
+
 /* ---------------------------------------------------------------------------
  * Execution
  * ------------------------------------------------------------------------- */

@@ -57,6 +57,15 @@ class Plan:
         N.check(N.lib.sv_plan_order(self.handle, order, fmap))
         return list(order), list(fmap)
 
+    def compile(self, params=None, forward=True, adjoint=False):
+        """Generate and compile the plan's complex64 stage kernels ahead of the first
+        run (sv_plan_compile); returns the number of stage kernels."""
+        p = None if params is None else np.ascontiguousarray(params, dtype=np.float64)
+        which = (1 if forward else 0) | (2 if adjoint else 0)
+        n = ctypes.c_uint32(0)
+        N.check(N.lib.sv_plan_compile(self.handle, N.as_double_ptr(p), which, ctypes.byref(n)))
+        return n.value
+
     def centrality(self):
         """(|RN|, dist, level) per gate."""
         G = len(self.circuit.gates)

@@ -56,11 +56,25 @@ def units():
     return out
 
 
+def _embed_prelude():
+    """jit_prelude.cuh as a C++ string constant: the run-time compiled stage kernels
+    include it from memory (NVRTC gets no include path)."""
+    src = open(os.path.join(CSRC, "jit_prelude.cuh")).read()
+    assert ")SVJIT\"" not in src
+    text = ("// generated by build.py from csrc/jit_prelude.cuh\n#pragma once\n"
+            "static const char kJitPrelude[] = R\"SVJIT(" + src + ")SVJIT\";\n")
+    out = os.path.join(BUILD, "jit_prelude_inc.h")
+    if not os.path.exists(out) or open(out).read() != text:
+        with open(out, "w") as f:
+            f.write(text)
+
+
 def build(verbose=False, force=False):
     cuda = _cuda_home()
     nvcc = os.path.join(cuda, "bin", "nvcc")
     os.makedirs(BUILD, exist_ok=True)
-    inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC]
+    _embed_prelude()
+    inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC, "-I", BUILD]
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(ROOT, "include", "sv.h"))
     newest_header = max(os.path.getmtime(h) for h in headers)
@@ -89,7 +103,7 @@ def build(verbose=False, force=False):
                 sys.stdout.write(o)
     if jobs or not os.path.exists(OUT):
         _run([nvcc, "-shared", "-o", OUT] + objs + ["-cudart", "shared",
-              "-L", os.path.join(cuda, "lib64"), "-Xlinker", "-rpath," + os.path.join(cuda, "lib64")])
+              "-L", os.path.join(cuda, "lib64"), "-lnvrtc", "-Xlinker", "-rpath," + os.path.join(cuda, "lib64")])
     return OUT
 
 

@@ -8,7 +8,12 @@
 #include <string>
 #include <vector>
 
+#include <memory>
+#include <mutex>
+#include <unordered_map>
+
 #include "gemm.h"
+#include "jit.h"
 #include "kernels.h"
 #include "planner.h"
 #include "internal.h"
@@ -703,6 +708,67 @@ static int env_int(const char* name, int dflt, int lo, int hi) {
 static int rmax_fwd(int eb) { return eb == 8 ? env_int("SVGB_RMAX_FWD", 4, 1, 5) : env_int("SVGB_RMAX_FWD", 4, 1, 4); }
 static int rmax_bwd(int eb) { return eb == 8 ? env_int("SVGB_RMAX_BWD", 4, 1, 4) : env_int("SVGB_RMAX_BWD", 3, 1, 3); }
 
+// ---------------- generated (run-time compiled) stage kernels ----------------
+// complex64 stage sweeps run as kernels generated per stage (jit.h); SVGB_JIT=0 selects
+// the generic interpreter kernel instead (both are GPU paths; there is no CPU path).
+static bool jit_enabled(sv_handle h) { return h->eb == 8 && env_int("SVGB_JIT", 1, 0, 1) == 1; }
+
+// Generated stages are memoised by the exact bytes of their lowered program section
+// (a pure function of those bytes), so repeated runs skip the generation; the memo is
+// dropped when it grows large (kernels themselves stay cached by source).
+static std::mutex g_jit_mu;
+static std::unordered_map<std::string, std::shared_ptr<svj::Built>> g_jit_memo;
+
+static sv_status jit_prepare(uint32_t n, const svh::Packed& pk, int nv,
+                             std::vector<std::shared_ptr<svj::Built>>* out) {
+    const uint8_t* blob = pk.blob.data();
+    const auto* groups = (const svk::Group*)(blob + pk.group_off);
+    const auto* ops = (const svk::DevOp<float>*)(blob + pk.op_off);
+    const auto* terms = (const svk::DevTerm<float>*)(blob + pk.term_off);
+    const auto* slots = (const svk::PhaseSlot<float>*)(blob + pk.slot_off);
+    out->clear();
+    std::vector<svj::Built*> fresh;
+    for (const svk::Stage& st : pk.stages) {
+        svj::StageView v{&st, groups + st.group_off, ops + st.op_off, terms, slots + st.phase_off, (int)n, nv};
+        std::string key;
+        key.append((const char*)&nv, sizeof(nv));
+        key.append((const char*)&n, sizeof(n));
+        key.append((const char*)&st, sizeof(st));
+        key.append((const char*)v.groups, st.n_groups * sizeof(svk::Group));
+        key.append((const char*)v.ops, st.n_ops * sizeof(svk::DevOp<float>));
+        key.append((const char*)v.slots, st.n_phase * sizeof(svk::PhaseSlot<float>));
+        for (uint32_t i = 0; i < st.n_ops; ++i)
+            if (v.ops[i].flags & svk::F_TERMS)
+                key.append((const char*)(terms + v.ops[i].term_off), v.ops[i].n_terms * sizeof(svk::DevTerm<float>));
+        for (uint32_t p = 0; p < st.n_phase; ++p)
+            key.append((const char*)(terms + v.slots[p].glob_off), v.slots[p].n_glob * sizeof(svk::DevTerm<float>));
+        std::shared_ptr<svj::Built> b;
+        {
+            std::lock_guard<std::mutex> lk(g_jit_mu);
+            auto it = g_jit_memo.find(key);
+            if (it != g_jit_memo.end()) b = it->second;
+        }
+        if (!b) {
+            b = std::make_shared<svj::Built>();
+            std::string err = svj::generate(v, b.get());
+            if (!err.empty()) return fail(SV_ERR_UNSUPPORTED, err);
+            if (b->smem > 227 * 1024) return fail(SV_ERR_UNSUPPORTED, "a generated stage needs more shared memory than a CTA has");
+            fresh.push_back(b.get());
+            std::lock_guard<std::mutex> lk(g_jit_mu);
+            if (g_jit_memo.size() > 4096) g_jit_memo.clear();
+            g_jit_memo[key] = b;
+        }
+        out->push_back(b);
+    }
+    if (!fresh.empty()) {
+        std::string err = svj::compile(fresh);
+        if (!err.empty()) return fail(SV_ERR_CUDA, "run-time compilation of a stage kernel failed: " + err);
+    }
+    for (auto& b : *out)
+        if (!b->kernel) return fail(SV_ERR_CUDA, "internal: stage kernel missing");
+    return SV_OK;
+}
+
 static sv_status run_forward(sv_handle h, const sv_plan* plan, const double* params, bool permute_back) {
     const svh::Plan& P = plan->plan;
     svh::Program prog;
@@ -710,12 +776,24 @@ static sv_status run_forward(sv_handle h, const sv_plan* plan, const double* par
     if (!err.empty()) return fail(SV_ERR_ARG, err);
     for (auto& st : prog.stages)
         if (((size_t)h->eb << st.T) > 227 * 1024) return fail(SV_ERR_UNSUPPORTED, "tile too wide for shared memory at this dtype (use L <= 13 for complex128)");
-    sv_status s = upload_program(h, prog, &h->fwd, false);
+    const bool jit = jit_enabled(h);
+    std::vector<std::shared_ptr<svj::Built>> built;
+    sv_status s = SV_OK;
+    if (jit) {
+        err = svh::pack(prog, (int)h->n, h->eb, &h->fwd.packed);
+        if (!err.empty()) return fail(SV_ERR_ARG, err);
+        s = jit_prepare(h->n, h->fwd.packed, 1, &built);
+    } else {
+        s = upload_program(h, prog, &h->fwd, false);
+    }
     if (s) return s;
     const auto& stages = h->fwd.packed.stages;
     for (size_t i = 0; i < stages.size(); ++i) {
         cudaEvent_t t0 = tick(h);
-        SV_CUDA(svk::launch_stage_fwd(h->eb, h->fwd.launch(i, h->psi, nullptr, nullptr), stages[i], h->stream));
+        if (jit)
+            SV_CUDA(svj::launch(*built[i], h->psi, nullptr, nullptr, h->stream, nullptr));
+        else
+            SV_CUDA(svk::launch_stage_fwd(h->eb, h->fwd.launch(i, h->psi, nullptr, nullptr), stages[i], h->stream));
         tock(h, t0, TK_STAGE);
         h->info.stage_sweeps += 1;
         h->info.kernel_launches += 1;
@@ -766,6 +844,34 @@ static sv_status run_gemm(sv_handle h, const sv_plan* plan, const double* params
     SV_CUDA(cudaMemcpyAsync(&st, h->status.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     SV_CUDA(cudaStreamSynchronize(h->stream));
     if (st) return fail(SV_ERR_TIMEOUT, "a tensor-core stage gave up waiting for its MMAs");
+    return SV_OK;
+}
+
+sv_status sv_plan_compile(const sv_plan* plan, const double* params, uint32_t which, uint32_t* n_kernels) {
+    if (!plan || which == 0 || which > 3) return fail(SV_ERR_ARG, "null plan or bad direction mask");
+    const svh::Plan& P = plan->plan;
+    if (P.n_params > 0 && !params) return fail(SV_ERR_ARG, "params is NULL");
+    if (P.gemm_k) return fail(SV_ERR_UNSUPPORTED, "tensor-core plans run the tcgen05 stage kernel, nothing to compile");
+    uint32_t count = 0;
+    for (int d = 0; d < 2; ++d) {
+        if (!((which >> d) & 1)) continue;
+        svh::Program prog;
+        std::string err = svh::lower(P, params, 8, d ? rmax_bwd(8) : rmax_fwd(8), d == 1, &prog);
+        if (!err.empty()) return fail(err.find("not supported") != std::string::npos ? SV_ERR_UNSUPPORTED : SV_ERR_ARG, err);
+        svh::Packed pk;
+        err = svh::pack(prog, P.n, 8, &pk);
+        if (!err.empty()) return fail(SV_ERR_ARG, err);
+        std::vector<std::shared_ptr<svj::Built>> built;
+        sv_status s = jit_prepare((uint32_t)P.n, pk, d + 1, &built);
+        if (s) return s;
+        count += (uint32_t)built.size();
+    }
+    if (n_kernels) *n_kernels = count;
+    return SV_OK;
+}
+
+sv_status sv_jit_stats(uint64_t* compiles, uint64_t* cache_hits, double* compile_ms) {
+    svj::stats(compiles, cache_hits, compile_ms);
     return SV_OK;
 }
 
@@ -867,7 +973,15 @@ sv_status sv_grad(sv_handle h, const sv_plan* plan, const double* params, const 
     if (s) return s;
     double E = 0.0;
     SV_CUDA(cudaMemcpyAsync(&E, h->red.p, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    s = upload_program(h, bprog, &h->bwd, true);
+    const bool jit = jit_enabled(h);
+    std::vector<std::shared_ptr<svj::Built>> built;
+    if (jit) {
+        err = svh::pack(bprog, (int)h->n, h->eb, &h->bwd.packed);
+        if (!err.empty()) return fail(SV_ERR_ARG, err);
+        s = jit_prepare(h->n, h->bwd.packed, 2, &built);
+    } else {
+        s = upload_program(h, bprog, &h->bwd, true);
+    }
     if (s) return s;
     const size_t nslots_total = bprog.slot_param.size();
     const auto& bst = h->bwd.packed.stages;
@@ -881,8 +995,11 @@ sv_status sv_grad(sv_handle h, const sv_plan* plan, const double* params, const 
         const uint64_t ntiles = 1ull << (h->n - st.T);
         cudaEvent_t t0 = tick(h);
         uint32_t grid = 0;
-        SV_CUDA(svk::launch_stage_bwd(h->eb, h->bwd.launch(i, h->psi, h->scratch.p, (double*)h->partial.p),
-                                      st, h->stream, &grid));
+        if (jit)
+            SV_CUDA(svj::launch(*built[i], h->psi, h->scratch.p, (double*)h->partial.p, h->stream, &grid));
+        else
+            SV_CUDA(svk::launch_stage_bwd(h->eb, h->bwd.launch(i, h->psi, h->scratch.p, (double*)h->partial.p),
+                                          st, h->stream, &grid));
         tock(h, t0, TK_BWD);
         h->info.backward_sweeps += 1;
         h->info.kernel_launches += 1;

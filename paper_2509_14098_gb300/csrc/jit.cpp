@@ -1,0 +1,689 @@
+// jit.cpp — generator, NVRTC compiler cache and launcher of the per-stage sweep
+// kernels (complex64).  See jit.h.
+//
+// A generated kernel is the stage sweep of Sec. 4.3 with one partition compiled in:
+// persistent CTAs walk the stage's tiles (2^T amplitudes whose local bits vary, the
+// lowest physical bits always among them, so every HBM access is a run of >= 128 B),
+// stage each tile into shared memory with 16-byte cp.async copies, run the register
+// groups (the partitioner re-run with the register budget: each thread holds 2^R
+// amplitudes in registers, applies the group's gates as straight-line code, and
+// exchanges through the swizzled shared-memory tile between groups), and write the
+// tile back in place.  The adjoint variant carries psi and lambda together and
+// accumulates Im <lambda|G|psi> per parametric rotation: a warp's sum over one tile in
+// FP32, added in FP64 to that warp's per-CTA slot sum across tiles.
+#include "jit.h"
+
+#include <nvrtc.h>
+
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+
+#include "jit_prelude_inc.h"   // kJitPrelude: jit_prelude.cuh as a string (generated by the build)
+
+namespace svj {
+
+struct Kernel {
+    std::vector<char> cubin;   // NVRTC output (sm_103a)
+    std::string err;
+    std::mutex mu;             // guards the lazy load below
+    cudaLibrary_t lib = nullptr;
+    cudaKernel_t fn = nullptr;
+    int per_sm_dev = -1;       // occupancy, cached for the device it was computed on
+    int dev = -1;
+    uint32_t smem_set = 0;
+};
+
+namespace {
+
+std::mutex g_mu;
+std::unordered_map<std::string, Kernel*> g_cache;   // source -> kernel (never freed: process lifetime)
+std::atomic<uint64_t> g_compiles{0}, g_hits{0};
+std::atomic<uint64_t> g_compile_us{0};
+
+std::string fmt(const char* f, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, f);
+    vsnprintf(buf, sizeof(buf), f, ap);
+    va_end(ap);
+    return buf;
+}
+
+uint64_t fnv1a(const std::string& s) {
+    uint64_t h = 1469598103934665603ull;
+    for (unsigned char c : s) {
+        h ^= c;
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+// ---------------------------------------------------------------------------
+// argument block: value arrays filled while generating, laid out after the pointers
+// ---------------------------------------------------------------------------
+struct ArgBuilder {
+    std::vector<uint64_t> q;   // 8-byte values (masks, physical bit values)
+    std::vector<uint32_t> u;   // 4-byte values (angles in turns, counts)
+    std::vector<float> f;      // FP32 constants (matrices, phase factors)
+    int Q(uint64_t v) { q.push_back(v); return (int)q.size() - 1; }
+    int U(uint32_t v) { u.push_back(v); return (int)u.size() - 1; }
+    int F(float v) { f.push_back(v); return (int)f.size() - 1; }
+};
+
+class Gen {
+  public:
+    Gen(const StageView& v, Built* out) : V(v), st(*v.st), B(out) {}
+    std::string run();
+
+  private:
+    const StageView& V;
+    const svk::Stage& st;
+    Built* B;
+    ArgBuilder A;
+    std::string s;            // kernel body
+    int T = 0, R = 0, TR = 0, NT = 0, NV = 1, NB = 1, NPH = 0, NSL = 0, NW = 1;
+    bool ttab = false;        // per-(slot, thread) thread-bit angle table in shared memory
+    std::vector<int> slot_thr;   // per phase slot: first u[] index of its J[i] (or -1)
+    int perm[32];             // logical register index -> variable holding it
+    std::string fixvar;       // name of the current group's fixed-index variable ("" = none)
+
+    void emit(const std::string& x) { s += x; }
+    std::string amp(int v, int k) const { return fmt("%c%d", v ? 'l' : 'p', perm[k]); }
+    std::string slot_angle(uint32_t slot);
+    std::string term_angle(const svk::DevOp<float>& o);
+    std::string phase_factor(const svk::DevOp<float>& o, int gi);
+    std::string fix_pred(uint64_t mask, bool all);
+    std::string op(const svk::DevOp<float>& o, int gi);
+    std::string dense(const svk::DevOp<float>& o, int gi);
+    std::string grad(const svk::DevOp<float>& o);
+};
+
+std::string Gen::slot_angle(uint32_t slot) {
+    std::string a = fmt("sang[%u]", slot);
+    if (slot_thr[slot] < 0) return a;
+    if (ttab) return a + fmt(" + tang[%u * %d + tid]", slot, NT);
+    std::string r = "(" + a;
+    for (int i = 0; i < TR; ++i) r += fmt(" + ((tid >> %d) & 1u ? S.u[%d] : 0u)", i, slot_thr[slot] + i);
+    return r + ")";
+}
+
+// sum of an op's terms (masks on the thread's fixed physical index) in turns
+std::string Gen::term_angle(const svk::DevOp<float>& o) {
+    std::string r = "0u";
+    for (uint32_t i = 0; i < o.n_terms; ++i) {
+        const svk::DevTerm<float>& t = V.terms[o.term_off + i];
+        const int ia = A.U(t.angle);
+        if (t.mask == 0) {
+            r += fmt(" + S.u[%d]", ia);
+        } else {
+            const int im = A.Q(t.mask);
+            r += fmt(" + ((%s & S.q[%d]) == S.q[%d] ? S.u[%d] : 0u)", fixvar.c_str(), im, im, ia);
+        }
+    }
+    return r;
+}
+
+// expression of an op's phase factor (float2)
+std::string Gen::phase_factor(const svk::DevOp<float>& o, int gi) {
+    (void)gi;
+    if (o.flags & svk::F_SLOT) return "svj_expi(" + slot_angle(o.slot) + ")";
+    if (o.flags & svk::F_TW) return "svj_expi(" + term_angle(o) + ")";
+    const int c = A.F(o.m[0]);
+    A.F(o.m[1]);
+    std::string w = fmt("make_float2(S.f[%d], S.f[%d])", c, c + 1);
+    if (o.flags & svk::F_TERMS) w = "svj_cmul(" + w + ", svj_expi(" + term_angle(o) + "))";
+    return w;
+}
+
+std::string Gen::fix_pred(uint64_t mask, bool all) {
+    const int im = A.Q(mask);
+    return all ? fmt("((%s & S.q[%d]) == S.q[%d])", fixvar.c_str(), im, im)
+               : fmt("((%s & S.q[%d]) != 0ull)", fixvar.c_str(), im);
+}
+
+std::string Gen::dense(const svk::DevOp<float>& o, int gi) {
+    const int j = o.j, bj = 1 << j, K = 1 << R;
+    std::string r = "{\n";
+    const bool pred = o.ctrl_fix != 0;
+    if (pred) r += "if " + fix_pred(o.ctrl_fix, true) + " {\n";
+    auto selected = [&](int k) { return !(k & bj) && ((uint32_t)k & o.ctrl_reg) == o.ctrl_reg; };
+    // phase on the target's |1> half first (the pending diagonal terms on the target)
+    if (o.flags & svk::F_PAIRS) {
+        // pair phases: the |1> amplitude of pair c (the other register bits) gets
+        // w0 * P[c], P[c] = exp(i * sum of the angles of the other bits set in c)
+        uint32_t ang[4] = {0, 0, 0, 0};
+        for (int i = 0; i < R - 1 && i < 3; ++i) std::memcpy(&ang[i], &o.m[1 + 2 * i], 4);
+        const bool tw = (o.flags & svk::F_TW) != 0;
+        if (tw) r += "const float2 w0 = " + phase_factor(o, gi) + ";\n";
+        for (int k = 0; k < K; ++k) {
+            if (!selected(k)) continue;
+            const int c = (k & (bj - 1)) | ((k >> (j + 1)) << j);
+            uint32_t t = 0;
+            for (int i = 0; i < R - 1; ++i)
+                if ((c >> i) & 1) t += ang[i];
+            if (t == 0 && !tw) continue;
+            std::string ph;
+            if (t == 0) {
+                ph = "w0";
+            } else {
+                const double rad = (double)t * (2.0 * M_PI / 4294967296.0);
+                const int fi = A.F((float)std::cos(rad));
+                A.F((float)std::sin(rad));
+                ph = fmt("make_float2(S.f[%d], S.f[%d])", fi, fi + 1);
+                if (tw) ph = "svj_cmul(w0, " + ph + ")";
+            }
+            for (int v = 0; v < NV; ++v) r += fmt("%s = svj_cmul(%s, %s);\n", amp(v, k | bj).c_str(), amp(v, k | bj).c_str(), ph.c_str());
+        }
+    } else if (o.flags & svk::F_TW) {
+        r += "const float2 w0 = " + phase_factor(o, gi) + ";\n";
+        for (int k = 0; k < K; ++k)
+            if (selected(k))
+                for (int v = 0; v < NV; ++v) r += fmt("%s = svj_cmul(%s, w0);\n", amp(v, k | bj).c_str(), amp(v, k | bj).c_str());
+    }
+    if (o.type == svk::OP_X) {
+        for (int k = 0; k < K; ++k) {
+            if (!selected(k)) continue;
+            if (pred) {
+                for (int v = 0; v < NV; ++v) r += fmt("svj_cswap(true, %s, %s);\n", amp(v, k).c_str(), amp(v, k | bj).c_str());
+            } else {
+                std::swap(perm[k], perm[k | bj]);   // a relabel of registers: no instruction
+            }
+        }
+    } else if (o.type == svk::OP_UR) {
+        const int m0 = A.F(o.m[0]), m2 = A.F(o.m[2]), m4 = A.F(o.m[4]), m6 = A.F(o.m[6]);
+        for (int k = 0; k < K; ++k)
+            if (selected(k))
+                for (int v = 0; v < NV; ++v)
+                    r += fmt("svj_ur(%s, %s, S.f[%d], S.f[%d], S.f[%d], S.f[%d]);\n", amp(v, k).c_str(),
+                             amp(v, k | bj).c_str(), m0, m2, m4, m6);
+    } else {   // OP_U
+        int m[8];
+        for (int i = 0; i < 8; ++i) m[i] = A.F(o.m[i]);
+        for (int k = 0; k < K; ++k)
+            if (selected(k))
+                for (int v = 0; v < NV; ++v)
+                    r += fmt("svj_u(%s, %s, S.f[%d], S.f[%d], S.f[%d], S.f[%d], S.f[%d], S.f[%d], S.f[%d], S.f[%d]);\n",
+                             amp(v, k).c_str(), amp(v, k | bj).c_str(), m[0], m[1], m[2], m[3], m[4], m[5], m[6], m[7]);
+    }
+    if (pred) r += "}\n";
+    return r + "}\n";
+}
+
+std::string Gen::grad(const svk::DevOp<float>& o) {
+    const int K = 1 << R;
+    std::string r = "{\nfloat acc = 0.f;\n";
+    if (o.type == svk::OP_GRAD_Z && o.u) {   // Z on a non-register bit: a sign per thread
+        for (int k = 0; k < K; ++k) r += fmt("acc += svj_imc(%s, %s);\n", amp(1, k).c_str(), amp(0, k).c_str());
+        r += "if " + fix_pred(o.ctrl_fix, false) + " acc = -acc;\n";
+    } else {
+        const int bj = 1 << o.j;
+        for (int k = 0; k < K; ++k) {
+            if (k & bj) continue;
+            const int k1 = k | bj;
+            if (o.type == svk::OP_GRAD_X)
+                r += fmt("acc += svj_imc(%s, %s) + svj_imc(%s, %s);\n", amp(1, k).c_str(), amp(0, k1).c_str(),
+                         amp(1, k1).c_str(), amp(0, k).c_str());
+            else if (o.type == svk::OP_GRAD_Y)   // Y|0> = i|1>, Y|1> = -i|0>
+                r += fmt("acc += svj_rec(%s, %s) - svj_rec(%s, %s);\n", amp(1, k1).c_str(), amp(0, k).c_str(),
+                         amp(1, k).c_str(), amp(0, k1).c_str());
+            else
+                r += fmt("acc += svj_imc(%s, %s) - svj_imc(%s, %s);\n", amp(1, k).c_str(), amp(0, k).c_str(),
+                         amp(1, k1).c_str(), amp(0, k1).c_str());
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1)
+        if (off < NT) r += fmt("acc += __shfl_xor_sync(%s, acc, %d);\n", NT >= 32 ? "0xffffffffu" : fmt("0x%xu", (1u << NT) - 1u).c_str(), off);
+    r += fmt("if ((tid & 31u) == 0u) gsm[%u * %d + (tid >> 5)] += (double)acc;\n}\n", o.slot, NW);
+    return r;
+}
+
+std::string Gen::op(const svk::DevOp<float>& o, int gi) {
+    const int K = 1 << R;
+    switch (o.type) {
+        case svk::OP_U: case svk::OP_UR: case svk::OP_X:
+            return dense(o, gi);
+        case svk::OP_PHASE0: case svk::OP_PHASE1: {
+            std::string r = "{\nconst float2 w = " + phase_factor(o, gi) + ";\n";
+            for (int k = 0; k < K; ++k)
+                if (o.type == svk::OP_PHASE0 || ((k >> o.j) & 1))
+                    for (int v = 0; v < NV; ++v) r += fmt("%s = svj_cmul(%s, w);\n", amp(v, k).c_str(), amp(v, k).c_str());
+            return r + "}\n";
+        }
+        case svk::OP_PHASE2: {
+            const int c = A.F(o.m[0]);
+            A.F(o.m[1]);
+            std::string r = fmt("{\nconst float2 w = make_float2(S.f[%d], S.f[%d]);\n", c, c + 1);
+            for (int k = 0; k < K; ++k)
+                if (((k >> o.j) & 1) && ((k >> o.u) & 1))
+                    for (int v = 0; v < NV; ++v) r += fmt("%s = svj_cmul(%s, w);\n", amp(v, k).c_str(), amp(v, k).c_str());
+            return r + "}\n";
+        }
+        case svk::OP_GRAD_X: case svk::OP_GRAD_Y: case svk::OP_GRAD_Z:
+            if (NV != 2) return "#error gradient op in a forward program\n";
+            return grad(o);
+        default:
+            return "#error unknown op\n";
+    }
+}
+
+std::string Gen::run() {
+    T = (int)st.T;
+    R = (int)st.R;
+    TR = T - R;
+    NT = 1 << TR;
+    NV = V.nv;
+    NW = (NT + 31) / 32;
+    NPH = (int)st.n_phase;
+    NSL = NV == 2 ? (int)st.n_slots : 0;
+    const int n = V.n, NG = n - T;
+    if (R < 1 || R > 5 || TR < 0 || TR > 9 || T > svk::kMaxT) return "jit: unsupported tile shape";
+    if (st.tile_pos[0] != 0) return "jit: the tile must hold physical bit 0";
+    for (uint32_t i = 0; i < st.n_ops; ++i)
+        if (V.ops[i].flags & svk::F_BIND) return "jit: bound (device-formed) ops are not generated";
+    const size_t tile_b = (size_t)8 << T;
+    // double-buffer the tiles when that still leaves the target residency
+    // resident threads per SM the register budget is sized for (64 registers per thread
+    // forward, 128 adjoint); SVGB_JIT_THR / SVGB_JIT_THR_BWD override for tuning
+    int thr_per_sm = NV == 2 ? 512 : 1024;
+    if (const char* e = getenv(NV == 2 ? "SVGB_JIT_THR_BWD" : "SVGB_JIT_THR"))
+        thr_per_sm = std::max(64, std::min(2048, atoi(e)));
+    const int ctas = std::max(1, thr_per_sm / std::max(NT, 32));
+    NB = (NG > 0 && (size_t)ctas * 2 * NV * tile_b <= 200 * 1024) ? 2 : 1;
+    if (const char* e = getenv("SVGB_JIT_NB")) NB = std::max(1, std::min(2, atoi(e)));
+    if (NG == 0) NB = 1;
+    ttab = (size_t)NPH * NT * 4 <= 16 * 1024;
+
+    // ---- argument block layout: v0, v1, partial, pad | q[] | u[] | f[] ----
+    // q: global bit values (NG), tile bit values (T), then op masks
+    for (int i = 0; i < NG; ++i) A.Q(1ull << st.glob_pos[i]);
+    for (int b = 0; b < T; ++b) A.Q(1ull << st.tile_pos[b]);
+    const int QG = 0, QT = NG;
+    // phase slots: per slot [cangle, n_glob, first term] in u[], global-term masks in
+    // q[] and their angles in u[]; thread-bit coefficients J[i] in u[]
+    slot_thr.assign(NPH, -1);
+    int slot_u = (int)A.u.size();
+    for (int p = 0; p < NPH; ++p) {
+        A.U(0);
+        A.U(0);
+        A.U(0);
+    }
+    for (int p = 0; p < NPH; ++p) {
+        const svk::PhaseSlot<float>& ps = V.slots[p];
+        A.u[slot_u + 3 * p] = ps.cangle;
+        A.u[slot_u + 3 * p + 1] = ps.n_glob;
+        A.u[slot_u + 3 * p + 2] = (uint32_t)A.q.size();   // first mask (angles follow in u at the same rank)
+        for (uint32_t i = 0; i < ps.n_glob; ++i) A.Q(V.terms[ps.glob_off + i].mask);
+    }
+    int slot_ang_u = (int)A.u.size();   // angles of the global terms, in mask order from slot_q0
+    const int slot_q0 = QT + T;
+    for (int p = 0; p < NPH; ++p) {
+        const svk::PhaseSlot<float>& ps = V.slots[p];
+        for (uint32_t i = 0; i < ps.n_glob; ++i) A.U(V.terms[ps.glob_off + i].angle);
+    }
+    for (int p = 0; p < NPH; ++p)
+        if (V.slots[p].has_thr) {
+            slot_thr[p] = (int)A.u.size();
+            for (int i = 0; i < TR; ++i) A.U(V.slots[p].J[i]);
+        }
+
+    // ---- per-CTA setup ----
+    std::string pre;
+    pre += fmt("const u32 tid = threadIdx.x;\n");
+    pre += fmt("const u64 ntiles = 1ull << %d;\n", NG);
+    pre += "u64 t = blockIdx.x;\nif (t >= ntiles) return;\n";
+    pre += "u64 base = 0, pstep = 0, gmask = 0;\n";
+    if (NG > 0)
+        pre += fmt("#pragma unroll 1\nfor (int i = 0; i < %d; ++i) {\nconst u64 b = a.q[%d + i];\ngmask |= b;\n"
+                   "if ((t >> i) & 1ull) base |= b;\nif (((u64)gridDim.x >> i) & 1ull) pstep |= b;\n}\n", NG, QG);
+    // this thread's 16-byte chunks: chunk c = tid + i * NT holds tile elements 2c, 2c + 1;
+    // tile bit 1 + b <- tid bit b, tile bit 1 + TR + b <- i bit b
+    pre += "u64 ptid = 0;\nu32 stid = 0;\n";
+    for (int b = 0; b < TR; ++b)
+        pre += fmt("if ((tid >> %d) & 1u) { ptid |= a.q[%d]; stid ^= %uu; }\n", b, QT + 1 + b, svk::swizzle8(1u << (1 + b)));
+    const int NCH = 1 << (R - 1);
+    std::vector<uint32_t> chs(NCH);
+    std::vector<std::string> chp(NCH);
+    for (int i = 0; i < NCH; ++i) {
+        uint32_t sw = 0;
+        std::string pe = "0ull";
+        for (int b = 0; (1 << b) < NCH; ++b)
+            if ((i >> b) & 1) {
+                sw ^= svk::swizzle8(1u << (1 + TR + b));
+                pe += fmt(" | S.q[%d]", QT + 1 + TR + b);
+            }
+        chs[i] = sw;
+        chp[i] = pe;
+    }
+    // register groups: per group the thread's swizzled offset and (if used) its physical part
+    const int ng = (int)st.n_groups;
+    std::vector<bool> needfix(ng, false);
+    for (int g = 0; g < ng; ++g) {
+        const svk::Group& G = V.groups[g];
+        for (uint32_t oi = 0; oi < G.n_ops; ++oi) {
+            const svk::DevOp<float>& o = V.ops[G.op_off + oi];
+            if (o.ctrl_fix || ((o.flags & svk::F_TERMS) && o.n_terms)) needfix[g] = true;
+        }
+    }
+    // Each group's thread offsets (the swizzled shared-memory offset of the thread's
+    // amplitudes, and the physical value of its thread bits where ops test it) would
+    // stay live in registers for the whole kernel; they go to a per-CTA table in shared
+    // memory instead, or, for stages with very many groups, are recomputed per tile.
+    int nfix = 0;
+    for (int g = 0; g < ng; ++g) nfix += needfix[g] ? 1 : 0;
+    const bool gtab = (size_t)NT * (4 * (size_t)ng + 8 * (size_t)nfix) <= 24 * 1024;
+    std::vector<int> fixrow(ng, -1);
+    {
+        int r = 0;
+        for (int g = 0; g < ng; ++g)
+            if (needfix[g]) fixrow[g] = r++;
+    }
+    auto so_expr = [&](int g) {
+        const svk::Group& G = V.groups[g];
+        std::string e = "(0u";
+        for (int i = 0; i < TR; ++i) e += fmt(" ^ ((tid >> %d) & 1u ? %uu : 0u)", i, svk::swizzle8(1u << G.thr_pos[i]));
+        return e + ")";
+    };
+    auto pf_expr = [&](int g, const char* src) {
+        const svk::Group& G = V.groups[g];
+        std::string e = "(0ull";
+        for (int i = 0; i < TR; ++i) e += fmt(" | ((tid >> %d) & 1u ? %s.q[%d] : 0ull)", i, src, QT + G.thr_pos[i]);
+        return e + ")";
+    };
+    // shared memory: tiles | sang[NPH] | tang[NPH][NT] | gsm[NSL][NW]
+    size_t o = (size_t)NV * NB * tile_b;
+    const size_t o_sang = o;
+    o = (o + 4 * (size_t)NPH + 15) & ~(size_t)15;
+    const size_t o_tang = o;
+    if (ttab) o = (o + 4 * (size_t)NPH * NT + 15) & ~(size_t)15;
+    const size_t o_gpf = o;   // u64 [nfix][NT]
+    if (gtab) o += 8 * (size_t)nfix * NT;
+    const size_t o_gso = o;   // u32 [ng][NT]
+    if (gtab) o = (o + 4 * (size_t)ng * NT + 15) & ~(size_t)15;
+    const size_t o_gsm = o;
+    o += 8 * (size_t)NSL * NW;
+    o = (o + 15) & ~(size_t)15;
+    const size_t o_args = o;   // the argument block's shared-memory copy (size known at the end)
+    pre += fmt("float2* const tl = reinterpret_cast<float2*>(smem);\n");
+    pre += fmt("u32* const sang = reinterpret_cast<u32*>(smem + %zu);\n", o_sang);
+    pre += fmt("u32* const tang = reinterpret_cast<u32*>(smem + %zu);\n", o_tang);
+    pre += fmt("double* const gsm = reinterpret_cast<double*>(smem + %zu);\n", o_gsm);
+    // per-op constants are read from a shared-memory copy of the arguments: read from
+    // the parameter bank they would be hoisted out of the tile loop into registers
+    pre += fmt("{\nconst uint4* src = reinterpret_cast<const uint4*>(&a);\nuint4* dst = reinterpret_cast<uint4*>(smem + %zu);\n"
+               "for (u32 i = tid; i < (u32)(sizeof(Args) / 16); i += %du) dst[i] = src[i];\n}\n", o_args, NT);
+    pre += fmt("const Args& S = *reinterpret_cast<const Args*>(smem + %zu);\n", o_args);
+    if (gtab) {
+        pre += fmt("u64* const gpf = reinterpret_cast<u64*>(smem + %zu);\n", o_gpf);
+        pre += fmt("u32* const gso = reinterpret_cast<u32*>(smem + %zu);\n", o_gso);
+        for (int g = 0; g < ng; ++g) {
+            pre += fmt("gso[%d * %d + tid] = %s;\n", g, NT, so_expr(g).c_str());
+            if (needfix[g]) pre += fmt("gpf[%d * %d + tid] = %s;\n", fixrow[g], NT, pf_expr(g, "a").c_str());
+        }
+    }
+    pre += "__syncthreads();\n";
+    if (ttab)
+        for (int p = 0; p < NPH; ++p)
+            if (slot_thr[p] >= 0) {
+                pre += fmt("{ u32 x = 0;\n");
+                for (int i = 0; i < TR; ++i) pre += fmt("if ((tid >> %d) & 1u) x += a.u[%d];\n", i, slot_thr[p] + i);
+                pre += fmt("tang[%d * %d + tid] = x; }\n", p, NT);
+            }
+    if (NSL) pre += fmt("for (u32 i = tid; i < %du; i += %du) gsm[i] = 0.0;\n", NSL * NW, NT);
+
+    // tile load / store
+    auto load = [&](const char* buf, const char* bexpr) {
+        std::string r;
+        for (int i = 0; i < NCH; ++i)
+            for (int v = 0; v < NV; ++v)
+                r += fmt("svj_cp_async16(tl + ((%d * %d + (%s)) << %d) + (stid ^ %uu), a.v%d + (%s | ptid | %s));\n", v,
+                         NB, buf, T, chs[i], v, bexpr, chp[i].c_str());
+        return r + "svj_cp_commit();\n";
+    };
+    std::string body;
+    body += load("0", "base");
+    body += "#pragma unroll 1\nfor (u32 it = 0; t < ntiles; t += gridDim.x, ++it) {\n";
+    body += "const u64 bn = ((base | ~gmask) + pstep) & gmask;\n";
+    if (NB == 2) {
+        body += "const u32 cb = it & 1u;\n";
+        body += "if (t + gridDim.x < ntiles) {\n" + load("cb ^ 1u", "bn") + "svj_cp_wait1();\n} else {\nsvj_cp_wait0();\n}\n";
+    } else {
+        body += "const u32 cb = 0u;\n";
+        body += "if (it > 0) {\n" + load("0", "base") + "}\nsvj_cp_wait0();\n";
+    }
+    if (NPH) {   // per-tile slot angles: the constant plus the global-bit terms set in this tile
+        body += fmt("#pragma unroll 1\nfor (u32 p = tid; p < %du; p += %du) {\nu32 x = S.u[%d + 3 * p];\nconst u32 ng = S.u[%d + 3 * p + 1], q0 = S.u[%d + 3 * p + 2];\n",
+                    NPH, NT, slot_u, slot_u, slot_u);
+        body += fmt("#pragma unroll 1\nfor (u32 i = 0; i < ng; ++i)\nif (base & S.q[q0 + i]) x += S.u[%d + (q0 - %d) + i];\nsang[p] = x;\n}\n",
+                    slot_ang_u, slot_q0);
+    }
+    body += "__syncthreads();\n";
+    for (int v = 0; v < NV; ++v) body += fmt("float2* const T%d = tl + ((%d * %d + cb) << %d);\n", v, v, NB, T);
+    for (int g = 0; g < ng; ++g) {
+        const svk::Group& G = V.groups[g];
+        const int K = 1 << R;
+        for (int k = 0; k < K; ++k) perm[k] = k;
+        std::vector<uint32_t> sr(K);
+        for (int k = 0; k < K; ++k) {
+            uint32_t x = 0;
+            for (int j = 0; j < R; ++j)
+                if ((k >> j) & 1) x ^= svk::swizzle8(1u << G.reg_pos[j]);
+            sr[k] = x;
+        }
+        const bool pairs = G.reg_pos[0] == 0;
+        body += fmt("{ // group %d\n", g);
+        if (gtab) body += fmt("const u32 so%d = gso[%d * %d + tid];\n", g, g, NT);
+        else body += fmt("const u32 so%d = %s;\n", g, so_expr(g).c_str());
+        fixvar = "";
+        if (needfix[g]) {
+            if (gtab) body += fmt("const u64 fix = base ^ gpf[%d * %d + tid];\n", fixrow[g], NT);
+            else body += fmt("const u64 fix = base ^ %s;\n", pf_expr(g, "S").c_str());
+            fixvar = "fix";
+        }
+        for (int v = 0; v < NV; ++v) {
+            for (int k = 0; k < K; ++k) body += fmt("float2 %c%d;\n", v ? 'l' : 'p', k);
+            if (pairs) {
+                for (int k = 0; k < K; k += 2)
+                    body += fmt("{ const float4 q = *reinterpret_cast<const float4*>(T%d + (so%d ^ %uu)); %c%d = make_float2(q.x, q.y); %c%d = make_float2(q.z, q.w); }\n",
+                                v, g, sr[k], v ? 'l' : 'p', k, v ? 'l' : 'p', k + 1);
+            } else {
+                for (int k = 0; k < K; ++k) body += fmt("%c%d = T%d[so%d ^ %uu];\n", v ? 'l' : 'p', k, v, g, sr[k]);
+            }
+        }
+        for (uint32_t oi = 0; oi < G.n_ops; ++oi) body += op(V.ops[G.op_off + oi], g);
+        for (int v = 0; v < NV; ++v) {
+            if (pairs) {
+                for (int k = 0; k < K; k += 2)
+                    body += fmt("*reinterpret_cast<float4*>(T%d + (so%d ^ %uu)) = make_float4(%s.x, %s.y, %s.x, %s.y);\n", v, g,
+                                sr[k], amp(v, k).c_str(), amp(v, k).c_str(), amp(v, k + 1).c_str(), amp(v, k + 1).c_str());
+            } else {
+                for (int k = 0; k < K; ++k) body += fmt("T%d[so%d ^ %uu] = %s;\n", v, g, sr[k], amp(v, k).c_str());
+            }
+        }
+        body += "}\n__syncthreads();\n";
+    }
+    // write the tile back in place
+    for (int i = 0; i < NCH; ++i)
+        for (int v = 0; v < NV; ++v)
+            body += fmt("*reinterpret_cast<float4*>(a.v%d + (base | ptid | %s)) = *reinterpret_cast<const float4*>(T%d + (stid ^ %uu));\n",
+                        v, chp[i].c_str(), v, chs[i]);
+    body += "base = bn;\n__syncthreads();\n}\n";
+    if (NSL)
+        body += fmt("for (u32 sl = tid; sl < %du; sl += %du) {\ndouble x = 0.0;\nfor (int w = 0; w < %d; ++w) x += gsm[sl * %d + w];\n"
+                    "a.partial[(u64)blockIdx.x * %d + sl] = x;\n}\n", NSL, NT, NW, NW, NSL);
+
+    // ---- assemble ----
+    const int nq = std::max<int>(1, (int)A.q.size()), nu = std::max<int>(1, (int)A.u.size()),
+              nf = std::max<int>(1, (int)A.f.size());
+    const int minb = std::max(1, std::min(32, thr_per_sm / NT));
+    std::string head;
+    head += "#include \"jit_prelude.cuh\"\n";
+    head += fmt("struct alignas(16) Args {\nfloat2* v0;\nfloat2* v1;\ndouble* partial;\nu64 pad;\nu64 q[%d];\nu32 u[%d];\nfloat f[%d];\n};\n",
+                nq, nu, nf);
+    std::string src = head + "extern \"C\" __global__ void __launch_bounds__(" + std::to_string(NT) + ", " +
+                      std::to_string(minb) + ") KNAME(const __grid_constant__ Args a) {\n"
+                      "extern __shared__ __attribute__((aligned(16))) unsigned char smem[];\n" + pre + body + "}\n";
+    const std::string name = fmt("svj_stage_%016llx", (unsigned long long)fnv1a(src));
+    size_t pos;
+    while ((pos = src.find("KNAME")) != std::string::npos) src.replace(pos, 5, name);
+    B->src = src;
+    B->name = name;
+    B->nthr = (uint32_t)NT;
+    B->n_slots = (uint32_t)NSL;
+    B->ntiles = 1ull << NG;
+    // argument bytes, matching the struct: 32 B of pointers/pad, q, u, f, padded to 16
+    size_t bytes = 32 + 8 * (size_t)nq + 4 * (size_t)nu;
+    bytes = (bytes + 3) & ~(size_t)3;
+    const size_t off_f = bytes;
+    bytes += 4 * (size_t)nf;
+    bytes = (bytes + 15) & ~(size_t)15;
+    if (bytes > 32000) return "jit: stage constants exceed the kernel argument space";
+    B->smem = (uint32_t)(o_args + bytes);
+    B->args.assign(bytes, 0);
+    std::memcpy(B->args.data() + 32, A.q.data(), 8 * A.q.size());
+    std::memcpy(B->args.data() + 32 + 8 * nq, A.u.data(), 4 * A.u.size());
+    std::memcpy(B->args.data() + off_f, A.f.data(), 4 * A.f.size());
+    return "";
+}
+
+}  // namespace
+
+std::string generate(const StageView& v, Built* out) {
+    Gen g(v, out);
+    return g.run();
+}
+
+static std::string nvrtc_compile(const std::string& src, const std::string& name, std::vector<char>* cubin) {
+    if (const char* dir = getenv("SVGB_JIT_DUMP")) {   // keep the generated source (profiling, reading)
+        if (FILE* f = fopen((std::string(dir) + "/" + name + ".cu").c_str(), "w")) {
+            fwrite(src.data(), 1, src.size(), f);
+            fclose(f);
+        }
+    }
+    nvrtcProgram prog;
+    const char* hdrs[1] = {kJitPrelude};
+    const char* hnames[1] = {"jit_prelude.cuh"};
+    if (nvrtcCreateProgram(&prog, src.c_str(), (name + ".cu").c_str(), 1, hdrs, hnames) != NVRTC_SUCCESS)
+        return "nvrtcCreateProgram failed";
+    const char* opts[] = {"-arch=sm_103a", "-std=c++17", "-default-device", "-lineinfo"};
+    nvrtcResult r = nvrtcCompileProgram(prog, 4, opts);
+    std::string err;
+    if (r != NVRTC_SUCCESS) {
+        size_t n = 0;
+        nvrtcGetProgramLogSize(prog, &n);
+        std::string log(n, '\0');
+        nvrtcGetProgramLog(prog, &log[0]);
+        err = std::string("NVRTC: ") + nvrtcGetErrorString(r) + "\n" + log.substr(0, 4000);
+    } else {
+        size_t n = 0;
+        nvrtcGetCUBINSize(prog, &n);
+        cubin->resize(n);
+        nvrtcGetCUBIN(prog, cubin->data());
+    }
+    nvrtcDestroyProgram(&prog);
+    return err;
+}
+
+std::string compile(std::vector<Built*>& kernels) {
+    std::vector<std::pair<Built*, Kernel*>> todo;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        std::unordered_map<std::string, Kernel*> fresh;
+        for (Built* b : kernels) {
+            auto it = g_cache.find(b->src);
+            if (it != g_cache.end()) {
+                b->kernel = it->second;
+                g_hits++;
+                continue;
+            }
+            auto jt = fresh.find(b->src);
+            if (jt != fresh.end()) {
+                b->kernel = jt->second;
+                continue;
+            }
+            Kernel* k = new Kernel();
+            fresh[b->src] = k;
+            b->kernel = k;
+            todo.push_back({b, k});
+        }
+    }
+    if (!todo.empty()) {
+        const auto t0 = std::chrono::steady_clock::now();
+        std::vector<std::vector<char>> bins(todo.size());
+        std::vector<std::string> errs(todo.size());
+        std::atomic<size_t> next{0};
+        const unsigned nth = std::max(1u, std::min<unsigned>((unsigned)todo.size(), std::thread::hardware_concurrency()));
+        std::vector<std::thread> pool;
+        for (unsigned w = 0; w < nth; ++w)
+            pool.emplace_back([&]() {
+                for (size_t i; (i = next++) < todo.size();)
+                    errs[i] = nvrtc_compile(todo[i].first->src, todo[i].first->name, &bins[i]);
+            });
+        for (auto& th : pool) th.join();
+        std::string first_err;
+        for (size_t i = 0; i < todo.size(); ++i) {
+            Kernel* k = todo[i].second;
+            k->cubin.swap(bins[i]);
+            k->err = errs[i];
+            if (!errs[i].empty() && first_err.empty()) first_err = errs[i];
+        }
+        g_compiles += todo.size();
+        g_compile_us += (uint64_t)std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t0).count();
+        std::lock_guard<std::mutex> lk(g_mu);
+        for (auto& p : todo) g_cache[p.first->src] = p.second;
+        if (!first_err.empty()) return first_err;
+    }
+    for (Built* b : kernels)
+        if (!b->kernel->err.empty()) return b->kernel->err;
+    return "";
+}
+
+cudaError_t launch(const Built& b, void* v0, void* v1, double* partial, cudaStream_t s, uint32_t* grid_out) {
+    Kernel* k = b.kernel;
+    if (!k || !k->err.empty() || k->cubin.empty()) return cudaErrorInvalidDeviceFunction;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(k->mu);
+    if (!k->fn) {   // context-independent load: the library is usable on every device
+        e = cudaLibraryLoadData(&k->lib, k->cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+        if (e != cudaSuccess) return e;
+        e = cudaLibraryGetKernel(&k->fn, k->lib, b.name.c_str());
+        if (e != cudaSuccess) return e;
+    }
+    if (k->dev != dev || k->smem_set < b.smem) {
+        e = cudaFuncSetAttribute((const void*)k->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b.smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k->fn, (int)b.nthr, b.smem);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        k->per_sm_dev = per_sm;
+        k->dev = dev;
+        k->smem_set = b.smem;
+    }
+    int nsm = 0;
+    e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t grid = std::min<uint64_t>(b.ntiles, (uint64_t)k->per_sm_dev * (uint64_t)nsm);
+    if (grid_out) *grid_out = (uint32_t)grid;
+    std::vector<uint8_t> args = b.args;
+    std::memcpy(args.data() + 0, &v0, 8);
+    std::memcpy(args.data() + 8, &v1, 8);
+    std::memcpy(args.data() + 16, &partial, 8);
+    void* params[1] = {args.data()};
+    return cudaLaunchKernel((const void*)k->fn, dim3((unsigned)grid), dim3(b.nthr), params, b.smem, s);
+}
+
+void stats(uint64_t* compiles, uint64_t* hits, double* compile_ms) {
+    if (compiles) *compiles = g_compiles.load();
+    if (hits) *hits = g_hits.load();
+    if (compile_ms) *compile_ms = g_compile_us.load() / 1000.0;
+}
+
+}  // namespace svj

@@ -1,0 +1,61 @@
+// jit.h — per-stage specialised sweep kernels, generated and compiled at run time.
+//
+// The paper turns each partition into generated code (Sec. 4.3, "From Partitions to
+// Code"); here each stage of a lowered complex64 program becomes one CUDA kernel whose
+// tile geometry, register groups and op sequence are compiled in, so the op dispatch,
+// descriptor loads and runtime bit loops of the generic interpreter disappear.  The
+// kernel source depends only on the stage's structure (bit positions inside the tile,
+// op kinds and register bits); every numeric value (gate matrices, phase angles,
+// physical bit positions, control masks) travels in the launch's argument block, so
+// a kernel is reused across parameter values and across stages of the same shape.
+//
+// Kernels are compiled with NVRTC for sm_103a and cached per process by source text.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "program.h"
+
+namespace svj {
+
+// One stage of a packed complex64 program (host copies of its blob sections).
+struct StageView {
+    const svk::Stage* st;
+    const svk::Group* groups;            // this stage's groups
+    const svk::DevOp<float>* ops;        // this stage's ops (group op_off is relative)
+    const svk::DevTerm<float>* terms;    // the program's whole term array
+    const svk::PhaseSlot<float>* slots;  // this stage's phase slots
+    int n;                               // state width
+    int nv;                              // 1: forward (psi); 2: adjoint (psi and lambda)
+};
+
+struct Kernel;
+
+// A generated stage: kernel source (structure only) and its argument block (values).
+struct Built {
+    std::string src;
+    std::string name;
+    std::vector<uint8_t> args;   // pointers at offsets 0 (v0), 8 (v1), 16 (partial) patched at launch
+    uint32_t nthr = 0, smem = 0, n_slots = 0;
+    uint64_t ntiles = 0;
+    Kernel* kernel = nullptr;    // set by compile()
+};
+
+// Generate the kernel of one stage.  Returns "" or an error (an op the generator does
+// not handle: the caller then reports it; there is no fallback path).
+std::string generate(const StageView& v, Built* out);
+
+// Compile every kernel not yet in the cache (in parallel host threads).
+std::string compile(std::vector<Built*>& kernels);
+
+// Launch a built stage: persistent grid of min(tiles, CTAs per SM x SMs) CTAs.
+// grid_out: CTAs launched (rows of gradient partials for the adjoint).
+cudaError_t launch(const Built& b, void* v0, void* v1, double* partial, cudaStream_t s, uint32_t* grid_out);
+
+// NVRTC compiles and cache hits since load (diagnostics).
+void stats(uint64_t* compiles, uint64_t* hits, double* compile_ms);
+
+}  // namespace svj
