@@ -449,6 +449,28 @@ def gemm_oracle26(args):
             "c128_max_err_vs_oracle_samples": c128_sample_err, "runs": rows}
 
 
+def partition_section(widths=(30, 34, 37), L=11, reps=3):
+    """Host partitioner (C++, exact closeness, Sec. 4.1-4.2) on the paper's benchmark
+    families at its 30-37 qubit widths: best-of-reps wall time per circuit, with
+    gate and stage counts.  The paper's own figures (Python + NetworkX) are context."""
+    import circuits as C
+    import paper_2509_14098_gb300 as sv
+    rows = []
+    for name in sorted(C.FAMILIES):
+        for n in widths:
+            c = C.FAMILIES[name](n)
+            best = float("inf")
+            for _ in range(reps):
+                t0 = time.perf_counter()
+                plan = sv.Plan(c, L)
+                best = min(best, time.perf_counter() - t0)
+            rows.append({"family": name, "n_qubits": n, "gates": len(c.gates), "stages": len(plan.stages()),
+                         "partition_ms": best * 1e3})
+    return {"L": L, "n_fixed": 4, "runs": rows,
+            "paper_context": "Sec. 5.2: under 1 s for most circuits, about 4-5 s for qnn and vqc "
+                             "(Python + NetworkX, 30-37 qubits, three-level hierarchy; other hardware)"}
+
+
 def aux_section(n, reps=3):
     """Permutation sweep (bit reversal of n qubits: out-of-place, then copied back) and the
     FP64 reductions (norm; TFIM expectation by Pauli sweeps) on a 2^n complex64 state:
@@ -666,6 +688,7 @@ def main_ours(args):
         extras["tensor_core_stages"] = gemm_section(args)
         torch.cuda.empty_cache()
         extras["permutation_and_reductions"] = aux_section(n)
+        extras["partitioner"] = partition_section()
     cpu = None
     if rank == 0 and world == 1 and not args.no_extras:
         cpu = run_cpu_sample(args.sample_seconds)

@@ -194,6 +194,146 @@ def batch_spec(count: int, seed: int, n_lo: int = 10, n_hi: int = 20, layers: in
 
 
 # ----------------------------------------------------------------------------
+# The paper's other benchmark families (Sec. 5.1: AE, DJ, GHZ, Ising, QFT, QPE,
+# SU2, VQC), as seeded generators written from each algorithm's definition.  They
+# stand in for the MQTBench / QASMBench circuit files, which are not available.
+# ----------------------------------------------------------------------------
+
+def _iqft_on(qubits: Sequence[int]) -> List[Gate]:
+    """Inverse QFT (with the final swaps) on the listed qubits, qubits[0] the least
+    significant."""
+    m = len(qubits)
+    return [Gate(g.kind, tuple(qubits[q] for q in g.qubits), g.param, g.angles) for g in inverse(qft(m)).gates]
+
+
+def qpe(n: int, seed: int = 0, exact: bool = False) -> Circuit:
+    """Phase estimation of P(2 pi phi) on qubit n-1 (prepared in |1>) with n-1
+    counting qubits 0..n-2: H on the counting register, CP(2 pi phi 2^k) from counting
+    qubit k, then the inverse QFT on the counting register.  phi is drawn from
+    default_rng(seed) (exact=True: a multiple of 2^-(n-1), which the circuit resolves
+    to a basis state)."""
+    m = n - 1
+    rng = np.random.default_rng(seed)
+    phi = int(rng.integers(1 << m)) / (1 << m) if exact else float(rng.uniform(0.0, 1.0))
+    gates = [Gate("X", (n - 1,))] + [Gate("H", (q,)) for q in range(m)]
+    for k in range(m):
+        gates.append(Gate("CP", (k, n - 1), -1, (2.0 * math.pi * phi * (1 << k) % (2.0 * math.pi),)))
+    gates += _iqft_on(list(range(m)))
+    c = Circuit(n, gates, 0, f"qpe{n}")
+    c.phase = phi
+    return c
+
+
+def dj(n: int, seed: int = 0) -> Circuit:
+    """Deutsch-Jozsa with a balanced oracle on n-1 input qubits and ancilla n-1:
+    X(anc); H on all; oracle f(x) = x.b xor parity of the X-mask (X on the masked
+    inputs, CX from every input to the ancilla, X again); H on the inputs."""
+    m = n - 1
+    rng = np.random.default_rng(seed)
+    xmask = rng.integers(0, 2, size=m)
+    gates = [Gate("X", (m,))] + [Gate("H", (q,)) for q in range(n)]
+    gates += [Gate("X", (q,)) for q in range(m) if xmask[q]]
+    gates += [Gate("CX", (q, m)) for q in range(m)]
+    gates += [Gate("X", (q,)) for q in range(m) if xmask[q]]
+    gates += [Gate("H", (q,)) for q in range(m)]
+    return Circuit(n, gates, 0, f"dj{n}")
+
+
+def su2(n: int, reps: int = 3) -> Circuit:
+    """EfficientSU2-style ansatz: per repetition RY and RZ on every qubit and a linear
+    CX chain, then a final RY / RZ layer.  Parameters: layer-major, RY before RZ."""
+    gates: List[Gate] = []
+    slot = 0
+    for r in range(reps + 1):
+        for kind in ("RY", "RZ"):
+            for q in range(n):
+                gates.append(Gate(kind, (q,), slot))
+                slot += 1
+        if r < reps:
+            gates += [Gate("CX", (q, q + 1)) for q in range(n - 1)]
+    return Circuit(n, gates, slot, f"su2_{n}x{reps}")
+
+
+def ising(n: int, steps: int = 4, J: float = 1.0, h: float = 0.7, dt: float = 0.1) -> Circuit:
+    """First-order Trotter steps of the transverse-field Ising chain: per step
+    exp(-i J dt Z_q Z_{q+1}) as CX(q, q+1) RZ(2 J dt)(q+1) CX(q, q+1) on every bond,
+    then RX(2 h dt) on every qubit."""
+    gates: List[Gate] = []
+    for _ in range(steps):
+        for q in range(n - 1):
+            gates += [Gate("CX", (q, q + 1)), Gate("RZ", (q + 1,), -1, (2 * J * dt,)), Gate("CX", (q, q + 1))]
+        gates += [Gate("RX", (q,), -1, (2 * h * dt,)) for q in range(n)]
+    return Circuit(n, gates, 0, f"ising{n}x{steps}")
+
+
+def vqc(n: int, reps: int = 2, seed: int = 0) -> Circuit:
+    """Variational classifier: a second-order Pauli-Z feature map of seeded data x
+    (H, P(2 x_q), and per neighbour pair CX . P(2 (pi - x_q)(pi - x_{q+1})) . CX),
+    then a real-amplitudes ansatz (RY layers and CX chains, parameters layer-major)."""
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(0.0, 2.0 * math.pi, size=n)
+    gates = [Gate("H", (q,)) for q in range(n)]
+    gates += [Gate("P", (q,), -1, (2.0 * float(x[q]),)) for q in range(n)]
+    for q in range(n - 1):
+        a = 2.0 * (math.pi - float(x[q])) * (math.pi - float(x[q + 1]))
+        gates += [Gate("CX", (q, q + 1)), Gate("P", (q + 1,), -1, (a,)), Gate("CX", (q, q + 1))]
+    slot = 0
+    for r in range(reps + 1):
+        for q in range(n):
+            gates.append(Gate("RY", (q,), slot))
+            slot += 1
+        if r < reps:
+            gates += [Gate("CX", (q, q + 1)) for q in range(n - 1)]
+    return Circuit(n, gates, slot, f"vqc{n}x{reps}")
+
+
+def ae(n: int, p: float = 0.2) -> Circuit:
+    """Amplitude estimation of a = p for A = RY(theta_p) on objective qubit n-1
+    (sin^2(theta_p / 2) = p), with n-1 counting qubits: A, H on the counting register,
+    controlled powers Q^(2^k) of the Grover operator (for one objective qubit, Q is
+    RY(2 theta_p); controlled RY(t) is emitted as RY(t/2) CX RY(-t/2) CX on the
+    target), then the inverse QFT on the counting register."""
+    m = n - 1
+    tgt = n - 1
+    theta = 2.0 * math.asin(math.sqrt(p))
+    gates = [Gate("RY", (tgt,), -1, (theta,))] + [Gate("H", (q,)) for q in range(m)]
+    for k in range(m):
+        t = (2.0 * theta * (1 << k)) % (4.0 * math.pi)
+        gates += [Gate("RY", (tgt,), -1, (t / 2,)), Gate("CX", (k, tgt)),
+                  Gate("RY", (tgt,), -1, (-t / 2,)), Gate("CX", (k, tgt))]
+    gates += _iqft_on(list(range(m)))
+    return Circuit(n, gates, 0, f"ae{n}")
+
+
+# name -> (generator of width n, number of parameters or 0)
+FAMILIES = {
+    "ae": lambda n: ae(n),
+    "dj": lambda n: dj(n, 1),
+    "ghz": lambda n: ghz(n),
+    "ising": lambda n: ising(n, 4),
+    "qft": lambda n: qft(n),
+    "qpe": lambda n: qpe(n, 1),
+    "su2": lambda n: su2(n, 3),
+    "vqc": lambda n: vqc(n, 2, 1),
+}
+
+
+def to_qasm(c: Circuit, params: Optional[Sequence[float]] = None) -> str:
+    """OpenQASM 2.0 text of a circuit (parameters substituted; angles in full
+    precision)."""
+    names = {"H": "h", "X": "x", "Y": "y", "Z": "z", "S": "s", "SDG": "sdg", "T": "t", "TDG": "tdg",
+             "RX": "rx", "RY": "ry", "RZ": "rz", "P": "p", "U3": "u3", "CX": "cx", "CY": "cy", "CZ": "cz",
+             "CP": "cp", "SWAP": "swap"}
+    out = ["OPENQASM 2.0;", 'include "qelib1.inc";', f"qreg q[{c.n_qubits}];", f"creg c[{c.n_qubits}];"]
+    for g in c.gates:
+        ang = c.angles_of(g, params)
+        a = "(" + ",".join(repr(float(x)) for x in ang) + ")" if ang else ""
+        out.append(f"{names[g.kind]}{a} " + ",".join(f"q[{q}]" for q in g.qubits) + ";")
+    out.append("measure q -> c;")
+    return "\n".join(out) + "\n"
+
+
+# ----------------------------------------------------------------------------
 # States and observables (data)
 # ----------------------------------------------------------------------------
 

@@ -236,6 +236,23 @@ sv_status sv_plan_centrality(const sv_plan* plan, uint32_t* reach, uint64_t* dis
 /* Free a plan. */
 sv_status sv_plan_destroy(sv_plan* plan);
 
+/* Read an OpenQASM 2.0 program into a flat gate list (Sec. 4.1: the circuit enters
+ * as a QASM file; Step A then builds the dependency graph from the gate list).
+ * Accepted: the OPENQASM header, include lines, qreg / creg declarations (several
+ * quantum registers are numbered one after another), gate calls on single qubits or
+ * element-wise on whole registers, parameter expressions (numbers, pi, + - * / ^,
+ * unary minus, parentheses, sin cos tan exp ln sqrt), and the gates id u u1 u2 u3 U p
+ * x y z h s sdg t tdg rx ry rz cx CX cy cz cp cu1 swap rzz (rzz(t) a,b becomes
+ * CX(a,b) RZ(t)(b) CX(a,b), the same unitary); measure and barrier emit nothing.
+ * Gate definitions, opaque gates, reset and conditionals are rejected.
+ * text: NUL-terminated.  gates: caller-owned array of capacity entries, or NULL to
+ * only count.  On success *n_qubits and *n_gates hold the circuit's sizes (also when
+ * gates is NULL).  Errors: SV_ERR_ARG with the line and reason in sv_last_error
+ * (syntax, unknown register or gate, index out of range, capacity too small, more
+ * than 255 qubits).  Host only. */
+sv_status sv_qasm_parse(const char* text, sv_gate* gates, uint32_t capacity, uint32_t* n_qubits,
+                        uint32_t* n_gates);
+
 /* Generate and compile ahead of time the complex64 stage kernels of a plan (Sec. 4.3,
  * "From Partitions to Code": each partition becomes one generated kernel with its
  * tile geometry, register groups and gate sequence compiled in; here compiled at run

@@ -12,8 +12,44 @@ import numpy as np
 from . import _native as N
 from ._native import SvError, SV_C64, SV_C128, SV_PREC_CUDACORE, SV_PREC_TF32X3, SV_PREC_BF16X3
 
-__all__ = ["Plan", "StateVector", "Batch", "SvError", "partition", "SV_C64", "SV_C128",
+__all__ = ["Plan", "StateVector", "Batch", "SvError", "partition", "parse_qasm", "SV_C64", "SV_C128",
            "SV_PREC_CUDACORE", "SV_PREC_TF32X3", "SV_PREC_BF16X3"]
+
+_KIND_NAMES = {v: k for k, v in N.GATE_CODES.items()}
+_N_ANGLES = {"RX": 1, "RY": 1, "RZ": 1, "P": 1, "CP": 1, "U3": 3}
+
+
+class QasmGate:
+    """One gate of a parsed circuit: kind name, qubits (control first), fixed angles."""
+    __slots__ = ("kind", "qubits", "param", "angles")
+
+    def __init__(self, kind, qubits, angles):
+        self.kind, self.qubits, self.param, self.angles = kind, tuple(qubits), -1, tuple(angles)
+
+    def __repr__(self):
+        return f"QasmGate({self.kind}, {self.qubits}, {self.angles})"
+
+
+class QasmCircuit:
+    """A flat gate list read from OpenQASM 2.0 text (sv_qasm_parse); Plan accepts it."""
+
+    def __init__(self, n_qubits, gates):
+        self.n_qubits, self.gates, self.n_params, self.name = n_qubits, gates, 0, "qasm"
+
+
+def parse_qasm(text):
+    """Parse OpenQASM 2.0 text (the subset sv_qasm_parse documents) into a QasmCircuit."""
+    src = text.encode() if isinstance(text, str) else bytes(text)
+    nq, ng = ctypes.c_uint32(), ctypes.c_uint32()
+    N.check(N.lib.sv_qasm_parse(src, None, 0, ctypes.byref(nq), ctypes.byref(ng)))
+    arr = (N.sv_gate * max(1, ng.value))()
+    N.check(N.lib.sv_qasm_parse(src, arr, ng.value, ctypes.byref(nq), ctypes.byref(ng)))
+    gates = []
+    for i in range(ng.value):
+        g = arr[i]
+        kind = _KIND_NAMES[g.kind]
+        gates.append(QasmGate(kind, [g.q[k] for k in range(g.nq)], [g.angle[k] for k in range(_N_ANGLES.get(kind, 0))]))
+    return QasmCircuit(nq.value, gates)
 
 
 class Plan:

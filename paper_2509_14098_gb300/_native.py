@@ -100,6 +100,8 @@ _SIGS = {
     "sv_plan_destroy": ([_vp], ctypes.c_int),
     "sv_plan_compile": ([_vp, _dp, _u32, ctypes.POINTER(_u32)], ctypes.c_int),
     "sv_jit_stats": ([ctypes.POINTER(_u64), ctypes.POINTER(_u64), _dp], ctypes.c_int),
+    "sv_qasm_parse": ([ctypes.c_char_p, ctypes.POINTER(sv_gate), _u32, ctypes.POINTER(_u32), ctypes.POINTER(_u32)],
+                      ctypes.c_int),
     "sv_run": ([_vp, _vp, _dp, ctypes.c_int], ctypes.c_int),
     "sv_permute": ([_vp, ctypes.POINTER(_u32)], ctypes.c_int),
     "sv_expval": ([_vp, ctypes.POINTER(sv_observable), _dp], ctypes.c_int),
