@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--grad-n", type=int, default=28)
     ap.add_argument("--grad-L", type=int, default=12)
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, grad ratio, batch and CPU baseline")
-    ap.add_argument("--part", default="all", choices=["all", "batch", "gemm", "aux"],
+    ap.add_argument("--part", default="all", choices=["all", "batch", "gemm", "aux", "grad"],
                     help="batch / gemm / aux: only that section (for profiling)")
     ap.add_argument("--aux-n", type=int, default=N_QUBITS, help="state width of the aux section")
     ap.add_argument("--gemm-n", type=int, default=32)
@@ -187,7 +187,7 @@ def peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("stage_impl.cuh", "stage_layout.cuh", "kdev.cuh", "program.h", "lower.cpp"):
+    for f in ("jit.cpp", "jit_prelude.cuh", "program.h", "lower.cpp"):
         h.update(open(os.path.join(ROOT, "paper_2509_14098_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -264,6 +264,47 @@ def main_reference(args):
                      f"({cb['measured_s']:.1f} s of measured CPU time in all); see cpu_baseline"),
         "cpu_baseline": cb, "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
+
+
+def grad_ratio(args, gn):
+    """Adjoint gradient against the forward pass on the hardware-efficient ansatz
+    (10 layers, TFIM): wall time of sv_grad and sv_run (3 each after a warm-up that
+    also compiles the stage kernels) and the per-kernel-class device times."""
+    import torch
+
+    import circuits as C
+    import paper_2509_14098_gb300 as sv
+    hc = C.hea(gn, 10)
+    hp = C.hea_params(hc.n_params, 4)
+    hplan = sv.Plan(hc, args.grad_L)
+    g = sv.StateVector(gn)
+    obs = C.tfim(gn)
+
+    def grad():
+        g.reset()
+        return g.grad(hplan, hp, obs)
+
+    g.reset(); g.run(hplan, hp); g.expval(obs); grad()
+    torch.cuda.synchronize()
+    g.timing(True); g.timing(reset=True)
+    t0 = time.perf_counter(); [g.run(hplan, hp) for _ in range(3)]; torch.cuda.synchronize()
+    t_fwd = (time.perf_counter() - t0) / 3
+    tf = g.timing(reset=True)
+    t0 = time.perf_counter(); [grad() for _ in range(3)]; torch.cuda.synchronize()
+    t_grad = (time.perf_counter() - t0) / 3
+    tg = g.timing(reset=True)
+    g.timing(False)
+    g.close()
+    torch.cuda.empty_cache()
+    return {
+        "workload": f"hea{gn}x10 ({hc.n_params} params), TFIM open chain, L={args.grad_L}",
+        "ratio": (t_grad - t_fwd) / t_fwd, "grad_over_forward": t_grad / t_fwd,
+        "forward_ms": t_fwd * 1e3, "grad_ms": t_grad * 1e3,
+        "kernel_ms": {"forward_stages": tf["stage_ms"] / 3, "grad_forward_stages": tg["stage_ms"] / 3,
+                      "backward_stages": tg["backward_ms"] / 3, "lambda_and_expval": tg["observable_ms"] / 3},
+        "definition": "(time(sv_grad) - time(sv_run)) / time(sv_run): lambda formation + backward over forward",
+    }
+
 
 
 def batch_section(args, steps):
@@ -540,6 +581,11 @@ def main_ours(args):
         if rank == 0:
             print(json.dumps({"part": "gemm", "gemm": r}))
         return
+    if args.part == "grad":
+        r = {"grad_forward_ratio": grad_ratio(args, args.grad_n)}
+        if rank == 0:
+            print(json.dumps({"part": "grad", "grad": r}))
+        return
     if args.part == "aux":
         r = aux_section(args.aux_n)
         if rank == 0:
@@ -604,7 +650,7 @@ def main_ours(args):
     achieved = bytes_per_launch / (avg_stage_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": traffic_per_launch(),
-                "kernel": "k_stage_fwd (one partition sweep, complex64)",
+                "kernel": "svj_fwd_* (generated sweep of one partition, complex64)",
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback",
                 "avg_launch_ms": avg_stage_ms, "launches": tm["stage_launches"]}
     whole_gbs = passes * bytes_per_launch / (ms_step * 1e-3) / 1e9
@@ -648,41 +694,9 @@ def main_ours(args):
         del st, psi
         torch.cuda.empty_cache()
 
-        def grad_ratio(gn):
-            hc = C.hea(gn, 10)
-            hp = C.hea_params(hc.n_params, 4)
-            hplan = sv.Plan(hc, args.grad_L)
-            g = sv.StateVector(gn)
-            obs = C.tfim(gn)
-
-            def grad():
-                g.reset()
-                return g.grad(hplan, hp, obs)
-
-            g.reset(); g.run(hplan, hp); g.expval(obs); grad()
-            torch.cuda.synchronize()
-            g.timing(True); g.timing(reset=True)
-            t0 = time.perf_counter(); [g.run(hplan, hp) for _ in range(3)]; torch.cuda.synchronize()
-            t_fwd = (time.perf_counter() - t0) / 3
-            tf = g.timing(reset=True)
-            t0 = time.perf_counter(); [grad() for _ in range(3)]; torch.cuda.synchronize()
-            t_grad = (time.perf_counter() - t0) / 3
-            tg = g.timing(reset=True)
-            g.timing(False)
-            g.close()
-            torch.cuda.empty_cache()
-            return {
-                "workload": f"hea{gn}x10 ({hc.n_params} params), TFIM open chain, L={args.grad_L}",
-                "ratio": (t_grad - t_fwd) / t_fwd, "grad_over_forward": t_grad / t_fwd,
-                "forward_ms": t_fwd * 1e3, "grad_ms": t_grad * 1e3,
-                "kernel_ms": {"forward_stages": tf["stage_ms"] / 3, "grad_forward_stages": tg["stage_ms"] / 3,
-                              "backward_stages": tg["backward_ms"] / 3, "lambda_and_expval": tg["observable_ms"] / 3},
-                "definition": "(time(sv_grad) - time(sv_run)) / time(sv_run): lambda formation + backward over forward",
-            }
-
-        extras["grad_forward_ratio"] = grad_ratio(args.grad_n)
+        extras["grad_forward_ratio"] = grad_ratio(args, args.grad_n)
         if args.grad_n != N_QUBITS:
-            extras["grad_forward_ratio_30q"] = grad_ratio(N_QUBITS)
+            extras["grad_forward_ratio_30q"] = grad_ratio(args, N_QUBITS)
         extras["batch"] = batch_section(args, 3)
         torch.cuda.empty_cache()
         extras["tensor_core_stages"] = gemm_section(args)

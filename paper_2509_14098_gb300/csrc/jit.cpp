@@ -20,6 +20,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -46,7 +47,12 @@ std::unordered_map<std::string, Kernel*> g_cache;   // source -> kernel (never f
 std::atomic<uint64_t> g_compiles{0}, g_hits{0};
 std::atomic<uint64_t> g_compile_us{0};
 
+// Set while a stage of an already-generated structure is re-walked to fill only its
+// argument block: the source text is not needed then, so formatting is skipped.
+thread_local bool g_quiet = false;
+
 std::string fmt(const char* f, ...) {
+    if (g_quiet) return std::string();
     char buf[1024];
     va_list ap;
     va_start(ap, f);
@@ -89,6 +95,7 @@ class Gen {
     std::string s;            // kernel body
     int T = 0, R = 0, TR = 0, NT = 0, NV = 1, NB = 1, NPH = 0, NSL = 0, NW = 1;
     bool ttab = false;        // per-(slot, thread) thread-bit angle table in shared memory
+    bool cbank = false;       // per-op constants read from the parameter bank (else shared memory)
     std::vector<int> slot_thr;   // per phase slot: first u[] index of its J[i] (or -1)
     int perm[32];             // logical register index -> variable holding it
     std::string fixvar;       // name of the current group's fixed-index variable ("" = none)
@@ -167,9 +174,9 @@ std::string Gen::dense(const svk::DevOp<float>& o, int gi) {
             uint32_t t = 0;
             for (int i = 0; i < R - 1; ++i)
                 if ((c >> i) & 1) t += ang[i];
-            if (t == 0 && !tw) continue;
+            if (c == 0 && !tw) continue;   // (no other register bit set: no pair phase)
             std::string ph;
-            if (t == 0) {
+            if (c == 0) {
                 ph = "w0";
             } else {
                 const double rad = (double)t * (2.0 * M_PI / 4294967296.0);
@@ -298,6 +305,11 @@ std::string Gen::run() {
     if (const char* e = getenv("SVGB_JIT_NB")) NB = std::max(1, std::min(2, atoi(e)));
     if (NG == 0) NB = 1;
     ttab = (size_t)NPH * NT * 4 <= 16 * 1024;
+    // Where per-op constants live: read from the parameter bank they are free operands
+    // of the FP32 instructions, but in long stages the compiler hoists them out of the
+    // tile loop into registers and spills; those stages read a shared-memory copy.
+    cbank = NV == 1 && st.n_ops <= 24;
+    if (const char* e = getenv("SVGB_JIT_CBANK")) cbank = atoi(e) != 0;
 
     // ---- argument block layout: v0, v1, partial, pad | q[] | u[] | f[] ----
     // q: global bit values (NG), tile bit values (T), then op masks
@@ -376,7 +388,8 @@ std::string Gen::run() {
     // memory instead, or, for stages with very many groups, are recomputed per tile.
     int nfix = 0;
     for (int g = 0; g < ng; ++g) nfix += needfix[g] ? 1 : 0;
-    const bool gtab = (size_t)NT * (4 * (size_t)ng + 8 * (size_t)nfix) <= 24 * 1024;
+    bool gtab = ng > 4 && (size_t)NT * (4 * (size_t)ng + 8 * (size_t)nfix) <= 24 * 1024;
+    if (const char* e = getenv("SVGB_JIT_GTAB")) gtab = atoi(e) != 0 && (size_t)NT * (4 * (size_t)ng + 8 * (size_t)nfix) <= 24 * 1024;
     std::vector<int> fixrow(ng, -1);
     {
         int r = 0;
@@ -415,15 +428,24 @@ std::string Gen::run() {
     pre += fmt("double* const gsm = reinterpret_cast<double*>(smem + %zu);\n", o_gsm);
     // per-op constants are read from a shared-memory copy of the arguments: read from
     // the parameter bank they would be hoisted out of the tile loop into registers
-    pre += fmt("{\nconst uint4* src = reinterpret_cast<const uint4*>(&a);\nuint4* dst = reinterpret_cast<uint4*>(smem + %zu);\n"
-               "for (u32 i = tid; i < (u32)(sizeof(Args) / 16); i += %du) dst[i] = src[i];\n}\n", o_args, NT);
-    pre += fmt("const Args& S = *reinterpret_cast<const Args*>(smem + %zu);\n", o_args);
+    if (cbank) {
+        pre += "const Args& S = a;\n";
+    } else {
+        pre += fmt("{\nconst uint4* src = reinterpret_cast<const uint4*>(&a);\nuint4* dst = reinterpret_cast<uint4*>(smem + %zu);\n"
+                   "for (u32 i = tid; i < (u32)(sizeof(Args) / 16); i += %du) dst[i] = src[i];\n}\n", o_args, NT);
+        pre += fmt("const Args& S = *reinterpret_cast<const Args*>(smem + %zu);\n", o_args);
+    }
     if (gtab) {
         pre += fmt("u64* const gpf = reinterpret_cast<u64*>(smem + %zu);\n", o_gpf);
         pre += fmt("u32* const gso = reinterpret_cast<u32*>(smem + %zu);\n", o_gso);
         for (int g = 0; g < ng; ++g) {
             pre += fmt("gso[%d * %d + tid] = %s;\n", g, NT, so_expr(g).c_str());
             if (needfix[g]) pre += fmt("gpf[%d * %d + tid] = %s;\n", fixrow[g], NT, pf_expr(g, "a").c_str());
+        }
+    } else {   // few groups: the offsets stay in registers
+        for (int g = 0; g < ng; ++g) {
+            pre += fmt("const u32 so%d = %s;\n", g, so_expr(g).c_str());
+            if (needfix[g]) pre += fmt("const u64 pf%d = %s;\n", g, pf_expr(g, "a").c_str());
         }
     }
     pre += "__syncthreads();\n";
@@ -478,11 +500,10 @@ std::string Gen::run() {
         const bool pairs = G.reg_pos[0] == 0;
         body += fmt("{ // group %d\n", g);
         if (gtab) body += fmt("const u32 so%d = gso[%d * %d + tid];\n", g, g, NT);
-        else body += fmt("const u32 so%d = %s;\n", g, so_expr(g).c_str());
         fixvar = "";
         if (needfix[g]) {
             if (gtab) body += fmt("const u64 fix = base ^ gpf[%d * %d + tid];\n", fixrow[g], NT);
-            else body += fmt("const u64 fix = base ^ %s;\n", pf_expr(g, "S").c_str());
+            else body += fmt("const u64 fix = base ^ pf%d;\n", g);
             fixvar = "fix";
         }
         for (int v = 0; v < NV; ++v) {
@@ -528,7 +549,7 @@ std::string Gen::run() {
     std::string src = head + "extern \"C\" __global__ void __launch_bounds__(" + std::to_string(NT) + ", " +
                       std::to_string(minb) + ") KNAME(const __grid_constant__ Args a) {\n"
                       "extern __shared__ __attribute__((aligned(16))) unsigned char smem[];\n" + pre + body + "}\n";
-    const std::string name = fmt("svj_stage_%016llx", (unsigned long long)fnv1a(src));
+    const std::string name = fmt("svj_%s_%016llx", NV == 2 ? "adj" : "fwd", (unsigned long long)fnv1a(src));
     size_t pos;
     while ((pos = src.find("KNAME")) != std::string::npos) src.replace(pos, 5, name);
     B->src = src;
@@ -543,7 +564,7 @@ std::string Gen::run() {
     bytes += 4 * (size_t)nf;
     bytes = (bytes + 15) & ~(size_t)15;
     if (bytes > 32000) return "jit: stage constants exceed the kernel argument space";
-    B->smem = (uint32_t)(o_args + bytes);
+    B->smem = (uint32_t)(cbank ? o_args : o_args + bytes);
     B->args.assign(bytes, 0);
     std::memcpy(B->args.data() + 32, A.q.data(), 8 * A.q.size());
     std::memcpy(B->args.data() + 32 + 8 * nq, A.u.data(), 4 * A.u.size());
@@ -551,11 +572,90 @@ std::string Gen::run() {
     return "";
 }
 
+// The generated source depends on a stage's structure only: tile and register-group
+// shapes (tile-bit indices), op kinds, register bits, flags and counts, and which
+// masks are empty.  The key below holds exactly those fields (plus the tuning
+// variables the generator reads), so stages that differ in values only — angles,
+// matrices, physical bit positions, control masks — share one source, and a new
+// stage of a known structure needs only its argument block (a quiet re-walk).
+std::string structure_key(const StageView& v) {
+    std::string k;
+    auto put = [&](uint64_t x) { k.append((const char*)&x, sizeof(x)); };
+    const svk::Stage& st = *v.st;
+    put((uint64_t)v.nv);
+    put((uint64_t)v.n);
+    put(st.T);
+    put(st.R);
+    put(st.n_groups);
+    put(v.nv == 2 ? st.n_slots : 0);
+    put(st.n_phase);
+    put(st.n_ops);
+    put(st.tile_pos[0]);
+    for (const char* e : {"SVGB_JIT_NB", "SVGB_JIT_THR", "SVGB_JIT_THR_BWD", "SVGB_JIT_CBANK", "SVGB_JIT_GTAB"}) {
+        const char* x = getenv(e);
+        k += x ? x : "-";
+        k += '|';
+    }
+    const int TR = (int)st.T - (int)st.R;
+    for (uint32_t g = 0; g < st.n_groups; ++g) {
+        const svk::Group& G = v.groups[g];
+        put(G.op_off);
+        put(G.n_ops);
+        for (uint32_t j = 0; j < st.R; ++j) put(G.reg_pos[j]);
+        for (int i = 0; i < TR; ++i) put(G.thr_pos[i]);
+    }
+    for (uint32_t i = 0; i < st.n_ops; ++i) {
+        const svk::DevOp<float>& o = v.ops[i];
+        put(o.type | (uint64_t)o.j << 8 | (uint64_t)o.u << 16 | (uint64_t)o.flags << 24 | (uint64_t)(o.ctrl_fix != 0) << 32);
+        put(o.ctrl_reg);
+        put(o.slot);
+        put(o.n_terms);
+        if (o.flags & (svk::F_TERMS | svk::F_TW))
+            for (uint32_t t = 0; t < o.n_terms; ++t) put(v.terms[o.term_off + t].mask == 0);
+    }
+    for (uint32_t p = 0; p < st.n_phase; ++p) {
+        put(v.slots[p].n_glob);
+        put(v.slots[p].has_thr);
+    }
+    return k;
+}
+
+struct Shape {
+    std::string src, name;
+};
+std::mutex g_shape_mu;
+std::unordered_map<std::string, std::shared_ptr<Shape>> g_shapes;   // structure key -> source
+
 }  // namespace
 
 std::string generate(const StageView& v, Built* out) {
+    const std::string key = structure_key(v);
+    std::shared_ptr<Shape> sh;
+    {
+        std::lock_guard<std::mutex> lk(g_shape_mu);
+        auto it = g_shapes.find(key);
+        if (it != g_shapes.end()) sh = it->second;
+    }
+    if (sh) {   // known structure: fill the argument block only
+        g_quiet = true;
+        Gen g(v, out);
+        std::string err = g.run();
+        g_quiet = false;
+        if (!err.empty()) return err;
+        out->src = sh->src;
+        out->name = sh->name;
+        return "";
+    }
     Gen g(v, out);
-    return g.run();
+    std::string err = g.run();
+    if (!err.empty()) return err;
+    auto ns = std::make_shared<Shape>();
+    ns->src = out->src;
+    ns->name = out->name;
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    if (g_shapes.size() > 8192) g_shapes.clear();
+    g_shapes[key] = ns;
+    return "";
 }
 
 static std::string nvrtc_compile(const std::string& src, const std::string& name, std::vector<char>* cubin) {
