@@ -99,6 +99,12 @@ class Gen {
     std::vector<int> slot_thr;   // per phase slot: first u[] index of its J[i] (or -1)
     int perm[32];             // logical register index -> variable holding it
     std::string fixvar;       // name of the current group's fixed-index variable ("" = none)
+    std::vector<std::pair<std::string, uint32_t>> pend;   // deferred gradient partials: variable, slot
+    int ngvar = 0;            // deferred partials named so far (unique names)
+    int zgen = -1;            // Im(conj(lambda_r) psi_r) per register r is held in zi<zgen>_<r> (-1: none valid)
+    int nzgen = 0;
+    int nred = 0;             // reductions emitted so far (unique names)
+    std::string reduce_pending();
 
     void emit(const std::string& x) { s += x; }
     std::string amp(int v, int k) const { return fmt("%c%d", v ? 'l' : 'p', perm[k]); }
@@ -156,6 +162,7 @@ std::string Gen::fix_pred(uint64_t mask, bool all) {
 
 std::string Gen::dense(const svk::DevOp<float>& o, int gi) {
     const int j = o.j, bj = 1 << j, K = 1 << R;
+    zgen = -1;   // psi and lambda change: the shared Z-gradient products are stale
     std::string r = "{\n";
     const bool pred = o.ctrl_fix != 0;
     if (pred) r += "if " + fix_pred(o.ctrl_fix, true) + " {\n";
@@ -224,29 +231,102 @@ std::string Gen::dense(const svk::DevOp<float>& o, int gi) {
 
 std::string Gen::grad(const svk::DevOp<float>& o) {
     const int K = 1 << R;
-    std::string r = "{\nfloat acc = 0.f;\n";
-    if (o.type == svk::OP_GRAD_Z && o.u) {   // Z on a non-register bit: a sign per thread
-        for (int k = 0; k < K; ++k) r += fmt("acc += svj_imc(%s, %s);\n", amp(1, k).c_str(), amp(0, k).c_str());
-        r += "if " + fix_pred(o.ctrl_fix, false) + " acc = -acc;\n";
+    // full warps: the partial stays in a register until the group's end, where all of
+    // the group's gradient partials are reduced across the warp together
+    const bool defer = NT >= 32;
+    std::string r;
+    if (defer && pend.size() == 32) r += reduce_pending();   // at most 32 values per reduction
+    const std::string acc = defer ? fmt("ga%d", ngvar++) : std::string("acc");
+    r += defer ? "float " + acc + " = 0.f;\n{\n" : "{\nfloat acc = 0.f;\n";
+    const char* A_ = acc.c_str();
+    if (o.type == svk::OP_GRAD_Z) {
+        // Im(conj(lambda_k) psi_k) per amplitude; diagonal ops multiply psi_k and lambda_k by
+        // the same phase, which cancels here, so the products stay valid until a dense op
+        // and consecutive Z gradients share them (register r's product in zi<g>_<r>)
+        if (zgen < 0) {
+            zgen = nzgen++;
+            std::string d = "";
+            for (int k = 0; k < K; ++k)
+                d += fmt("const float zi%d_%d = svj_imc(%s, %s);\n", zgen, perm[k], amp(1, k).c_str(), amp(0, k).c_str());
+            r = d + r;
+        }
+        std::string sum;
+        for (int k = 0; k < K; ++k) {
+            const bool neg = !o.u && ((k >> o.j) & 1);
+            sum += fmt("%c zi%d_%d", k == 0 ? (neg ? '-' : ' ') : (neg ? '-' : '+'), zgen, perm[k]);
+        }
+        r += fmt("%s = %s;\n", A_, sum.c_str());
+        if (o.u) r += "if " + fix_pred(o.ctrl_fix, false) + fmt(" %s = -%s;\n", A_, A_);   // Z on a non-register bit
+    } else if (o.type == svk::OP_GRAD_Y) {   // Y|0> = i|1>, Y|1> = -i|0>: Re(conj(l1) p0) - Re(conj(l0) p1), packed
+        const int bj = 1 << o.j;
+        r += "float2 yp = make_float2(0.f, 0.f), ym = make_float2(0.f, 0.f);\n";
+        for (int k = 0; k < K; ++k) {
+            if (k & bj) continue;
+            const int k1 = k | bj;
+            r += fmt("yp = svj_rec2(yp, %s, %s);\nym = svj_rec2(ym, %s, %s);\n", amp(1, k1).c_str(), amp(0, k).c_str(),
+                     amp(1, k).c_str(), amp(0, k1).c_str());
+        }
+        r += fmt("%s = (yp.x + yp.y) - (ym.x + ym.y);\n", A_);
     } else {
         const int bj = 1 << o.j;
         for (int k = 0; k < K; ++k) {
             if (k & bj) continue;
             const int k1 = k | bj;
-            if (o.type == svk::OP_GRAD_X)
-                r += fmt("acc += svj_imc(%s, %s) + svj_imc(%s, %s);\n", amp(1, k).c_str(), amp(0, k1).c_str(),
-                         amp(1, k1).c_str(), amp(0, k).c_str());
-            else if (o.type == svk::OP_GRAD_Y)   // Y|0> = i|1>, Y|1> = -i|0>
-                r += fmt("acc += svj_rec(%s, %s) - svj_rec(%s, %s);\n", amp(1, k1).c_str(), amp(0, k).c_str(),
-                         amp(1, k).c_str(), amp(0, k1).c_str());
-            else
-                r += fmt("acc += svj_imc(%s, %s) - svj_imc(%s, %s);\n", amp(1, k).c_str(), amp(0, k).c_str(),
-                         amp(1, k1).c_str(), amp(0, k1).c_str());
+            r += fmt("%s += svj_imc(%s, %s) + svj_imc(%s, %s);\n", A_, amp(1, k).c_str(), amp(0, k1).c_str(),
+                     amp(1, k1).c_str(), amp(0, k).c_str());   // X
         }
+    }
+    if (defer) {
+        pend.push_back({acc, o.slot});
+        return r + "}\n";
     }
     for (int off = 16; off > 0; off >>= 1)
         if (off < NT) r += fmt("acc += __shfl_xor_sync(%s, acc, %d);\n", NT >= 32 ? "0xffffffffu" : fmt("0x%xu", (1u << NT) - 1u).c_str(), off);
     r += fmt("if ((tid & 31u) == 0u) gsm[%u * %d + (tid >> 5)] += (double)acc;\n}\n", o.slot, NW);
+    return r;
+}
+
+// The group's m gradient partials (one per lane and op) summed over the warp together:
+// a butterfly reduce-scatter halves the set at each of the first log2(m) exchange
+// steps (a lane keeps the half its lane bit selects and adds its partner's copy), the
+// remaining steps finish the sum; value i then sits in the lanes whose upper bits
+// spell i, and one of them adds it in FP64 to the warp's slot sum.
+std::string Gen::reduce_pending() {
+    const int m = (int)pend.size();
+    if (m == 0) return "";
+    int P2 = 1;
+    while (P2 < m) P2 <<= 1;
+    const int id = nred++;
+    std::string r = "{\n";
+    std::vector<std::string> v(P2);
+    for (int i = 0; i < P2; ++i) v[i] = i < m ? pend[i].first : std::string("0.f");
+    r += "const u32 lane = tid & 31u;\n";
+    int cnt = P2, step = 0;
+    for (int off = 16; off > 0; off >>= 1) {
+        if (cnt > 1) {
+            const int h = cnt / 2;
+            for (int i = 0; i < h; ++i) {
+                const std::string nv = fmt("gr%d_%d_%d", id, step, i);
+                r += fmt("const float %s = ((lane & %du) ? %s : %s) + __shfl_xor_sync(0xffffffffu, (lane & %du) ? %s : %s, %d);\n",
+                         nv.c_str(), off, v[i + h].c_str(), v[i].c_str(), off, v[i].c_str(), v[i + h].c_str(), off);
+                v[i] = nv;
+            }
+            cnt = h;
+        } else {
+            const std::string nv = fmt("gr%d_%d_0", id, step);
+            r += fmt("const float %s = %s + __shfl_xor_sync(0xffffffffu, %s, %d);\n", nv.c_str(), v[0].c_str(), v[0].c_str(), off);
+            v[0] = nv;
+        }
+        ++step;
+    }
+    // value index of this lane: the lane bits of the halving steps, highest first
+    int lg = 0;
+    while ((1 << lg) < P2) ++lg;
+    r += fmt("const u32 gi = lane >> %d;\n", 5 - lg);
+    r += fmt("if ((lane & %uu) == 0u && gi < %du) {\nu32 sl = 0u;\n", (1u << (5 - lg)) - 1u, m);
+    for (int i = 0; i < m; ++i) r += fmt("sl = gi == %du ? %uu : sl;\n", i, pend[i].second);
+    r += fmt("gsm[sl * %d + (tid >> 5)] += (double)%s;\n}\n}\n", NW, v[0].c_str());
+    pend.clear();
     return r;
 }
 
@@ -308,7 +388,9 @@ std::string Gen::run() {
     // Where per-op constants live: read from the parameter bank they are free operands
     // of the FP32 instructions, but in long stages the compiler hoists them out of the
     // tile loop into registers and spills; those stages read a shared-memory copy.
-    cbank = NV == 1 && st.n_ops <= 24;
+    int cbank_ops = 160;
+    if (const char* e = getenv("SVGB_JIT_CBANK_OPS")) cbank_ops = atoi(e);
+    cbank = NV == 1 && (int)st.n_ops <= cbank_ops;
     if (const char* e = getenv("SVGB_JIT_CBANK")) cbank = atoi(e) != 0;
 
     // ---- argument block layout: v0, v1, partial, pad | q[] | u[] | f[] ----
@@ -516,7 +598,10 @@ std::string Gen::run() {
                 for (int k = 0; k < K; ++k) body += fmt("%c%d = T%d[so%d ^ %uu];\n", v ? 'l' : 'p', k, v, g, sr[k]);
             }
         }
+        pend.clear();
+        zgen = -1;
         for (uint32_t oi = 0; oi < G.n_ops; ++oi) body += op(V.ops[G.op_off + oi], g);
+        body += reduce_pending();
         for (int v = 0; v < NV; ++v) {
             if (pairs) {
                 for (int k = 0; k < K; k += 2)
@@ -591,7 +676,7 @@ std::string structure_key(const StageView& v) {
     put(st.n_phase);
     put(st.n_ops);
     put(st.tile_pos[0]);
-    for (const char* e : {"SVGB_JIT_NB", "SVGB_JIT_THR", "SVGB_JIT_THR_BWD", "SVGB_JIT_CBANK", "SVGB_JIT_GTAB"}) {
+    for (const char* e : {"SVGB_JIT_NB", "SVGB_JIT_THR", "SVGB_JIT_THR_BWD", "SVGB_JIT_CBANK", "SVGB_JIT_CBANK_OPS", "SVGB_JIT_GTAB"}) {
         const char* x = getenv(e);
         k += x ? x : "-";
         k += '|';

@@ -51,6 +51,9 @@ SVJ_DI void svj_cswap(bool p, float2& a, float2& b) {
     b = p ? t : b;
 }
 
+// acc + (l.x p.x, l.y p.y): Re(conj(l) p) summed in packed FP32x2 halves
+SVJ_DI float2 svj_rec2(float2 acc, float2 l, float2 p) { return __ffma2_rn(l, p, acc); }
+
 // Im(conj(l) p), Re(conj(l) p)
 SVJ_DI float svj_imc(float2 l, float2 p) { return fmaf(l.x, p.y, -l.y * p.x); }
 SVJ_DI float svj_rec(float2 l, float2 p) { return fmaf(l.x, p.x, l.y * p.y); }
@@ -62,3 +65,55 @@ SVJ_DI void svj_cp_async16(void* smem, const void* gmem) {
 SVJ_DI void svj_cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 SVJ_DI void svj_cp_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 SVJ_DI void svj_cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
+// Tensor-memory-access (TMA) tile staging.  A stage's tile is one 5-D box of the state
+// viewed as a tensor whose dimensions are the runs of consecutive local / global
+// physical bits (local runs are box extents, global runs have box extent 1); the
+// innermost dimension is physical bits 0..3 (128 bytes), loaded with the 128-byte
+// swizzle, so tile element e sits at e ^ (((e >> 4) & 7) << 1).
+// ---------------------------------------------------------------------------
+struct alignas(64) SvjTmap { u64 w[16]; };   // CUtensorMap, filled by the host
+
+SVJ_DI u32 svj_saddr(const void* p) { return (u32)__cvta_generic_to_shared(p); }
+SVJ_DI void svj_mbar_init(u64* bar, u32 count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(svj_saddr(bar)), "r"(count) : "memory");
+}
+// make the initialised barriers visible to the asynchronous (TMA) proxy
+SVJ_DI void svj_fence_barrier_init() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+SVJ_DI void svj_mbar_expect_tx(u64* bar, u32 bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(svj_saddr(bar)), "r"(bytes) : "memory");
+}
+SVJ_DI bool svj_mbar_try_wait(u64* bar, u32 parity) {
+    u32 ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+                 : "=r"(ok)
+                 : "r"(svj_saddr(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+// bounded wait on a barrier phase: false (and *flag set) if it did not complete in
+// about a second; the caller skips its work and the host reports SV_ERR_TIMEOUT
+SVJ_DI bool svj_mbar_wait(u64* bar, u32 parity, int* flag) {
+    for (u32 i = 0; i < (1u << 26); ++i)
+        if (svj_mbar_try_wait(bar, parity)) return true;
+    if (flag) atomicExch(flag, 1);
+    return false;
+}
+SVJ_DI void svj_tma_load(void* dst, const SvjTmap* map, int c0, int c1, int c2, int c3, int c4, u64* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], [%7];\n" ::"r"(
+            svj_saddr(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(svj_saddr(bar))
+        : "memory");
+}
+SVJ_DI void svj_tma_store(const SvjTmap* map, int c0, int c1, int c2, int c3, int c4, const void* src) {
+    asm volatile("cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4, %5}], [%6];\n" ::"l"(map),
+                 "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(svj_saddr(src))
+                 : "memory");
+}
+SVJ_DI void svj_bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+SVJ_DI void svj_bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+SVJ_DI void svj_bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+// generic-proxy shared-memory writes become visible to a following TMA store
+SVJ_DI void svj_fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
