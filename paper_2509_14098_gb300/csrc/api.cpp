@@ -131,6 +131,8 @@ struct sv_handle_s {
     DevBuf aux;          // Pauli sweeps / permutation descriptors
     DevBuf gemm;         // tensor-core stage descriptors + operand chunks
     DevBuf status;       // device-side error flag (bounded waits)
+    DevBuf jflag;        // generated stage kernels' bounded-wait flag (sticky until reported)
+    bool jflag_pending = false;   // a generated kernel ran since the flag was last read
     std::vector<uint8_t> gemm_host;
     std::vector<uint8_t> aux_host;
     sv_run_info info{};
@@ -187,6 +189,31 @@ static sv_status check_handle(sv_handle h) {
 }
 
 static size_t state_bytes(sv_handle h) { return ((size_t)1 << h->n) * (size_t)h->eb; }
+
+// The generated stage kernels bound their waits for tile copies; a kernel that gave
+// up sets the handle's flag.  sv_run stays asynchronous, so the flag is read at the
+// next call that synchronises the stream (and then cleared).
+static sv_status jflag_device(sv_handle h, int** out) {
+    if (!h->jflag.p) {
+        SV_CUDA(h->jflag.ensure(sizeof(int)));
+        SV_CUDA(cudaMemsetAsync(h->jflag.p, 0, sizeof(int), h->stream));
+    }
+    *out = (int*)h->jflag.p;
+    h->jflag_pending = true;
+    return SV_OK;
+}
+static sv_status jflag_check(sv_handle h) {
+    if (!h->jflag_pending) return SV_OK;
+    h->jflag_pending = false;
+    int v = 0;
+    SV_CUDA(cudaMemcpyAsync(&v, h->jflag.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    SV_CUDA(cudaStreamSynchronize(h->stream));
+    if (v) {
+        SV_CUDA(cudaMemsetAsync(h->jflag.p, 0, sizeof(int), h->stream));
+        return fail(SV_ERR_TIMEOUT, "a stage kernel gave up waiting for its tile copies (bounded wait); the state is invalid");
+    }
+    return SV_OK;
+}
 
 // ---------------------------------------------------------------------------
 // permutation sweep: new[y] = old[x], bit phys_of_qubit[q] of x = bit q of y
@@ -529,6 +556,7 @@ sv_status sv_destroy(sv_handle h) {
     h->aux.release();
     h->gemm.release();
     h->status.release();
+    h->jflag.release();
     delete h;
     return SV_OK;
 }
@@ -566,13 +594,13 @@ sv_status sv_get_state_host(sv_handle h, void* host_dst) {
     if (check_handle(h) || !host_dst) return fail(SV_ERR_ARG, "null argument");
     SV_CUDA(cudaMemcpyAsync(host_dst, h->psi, state_bytes(h), cudaMemcpyDeviceToHost, h->stream));
     SV_CUDA(cudaStreamSynchronize(h->stream));
-    return SV_OK;
+    return jflag_check(h);
 }
 
 sv_status sv_synchronize(sv_handle h) {
     if (check_handle(h)) return SV_ERR_ARG;
     SV_CUDA(cudaStreamSynchronize(h->stream));
-    return SV_OK;
+    return jflag_check(h);
 }
 
 sv_status sv_last_run_info(sv_handle h, sv_run_info* out) {
@@ -712,6 +740,9 @@ static int rmax_bwd(int eb) { return eb == 8 ? env_int("SVGB_RMAX_BWD", 4, 1, 4)
 // complex64 stage sweeps run as kernels generated per stage (jit.h); SVGB_JIT=0 selects
 // the generic interpreter kernel instead (both are GPU paths; there is no CPU path).
 static bool jit_enabled(sv_handle h) { return h->eb == 8 && env_int("SVGB_JIT", 1, 0, 1) == 1; }
+// generated forward sweeps: stages needing 4+ register groups at R = 4 may use R = 5
+// (SVGB_RWIDE_FWD=5; off by default: measured slower on QFT30, 26.8 -> 28.9 ms)
+static int rwide_fwd() { return env_int("SVGB_RWIDE_FWD", 0, 0, 5); }
 
 // Generated stages are memoised by the exact bytes of their lowered program section
 // (a pure function of those bytes), so repeated runs skip the generation; the memo is
@@ -772,17 +803,19 @@ static sv_status jit_prepare(uint32_t n, const svh::Packed& pk, int nv,
 static sv_status run_forward(sv_handle h, const sv_plan* plan, const double* params, bool permute_back) {
     const svh::Plan& P = plan->plan;
     svh::Program prog;
-    std::string err = svh::lower(P, params, h->eb, rmax_fwd(h->eb), false, &prog);
+    const bool jit = jit_enabled(h);
+    std::string err = svh::lower(P, params, h->eb, rmax_fwd(h->eb), false, &prog, false, jit ? rwide_fwd() : 0);
     if (!err.empty()) return fail(SV_ERR_ARG, err);
     for (auto& st : prog.stages)
         if (((size_t)h->eb << st.T) > 227 * 1024) return fail(SV_ERR_UNSUPPORTED, "tile too wide for shared memory at this dtype (use L <= 13 for complex128)");
-    const bool jit = jit_enabled(h);
     std::vector<std::shared_ptr<svj::Built>> built;
     sv_status s = SV_OK;
+    int* flag = nullptr;
     if (jit) {
         err = svh::pack(prog, (int)h->n, h->eb, &h->fwd.packed);
         if (!err.empty()) return fail(SV_ERR_ARG, err);
         s = jit_prepare(h->n, h->fwd.packed, 1, &built);
+        if (!s) s = jflag_device(h, &flag);
     } else {
         s = upload_program(h, prog, &h->fwd, false);
     }
@@ -791,7 +824,7 @@ static sv_status run_forward(sv_handle h, const sv_plan* plan, const double* par
     for (size_t i = 0; i < stages.size(); ++i) {
         cudaEvent_t t0 = tick(h);
         if (jit)
-            SV_CUDA(svj::launch(*built[i], h->psi, nullptr, nullptr, h->stream, nullptr));
+            SV_CUDA(svj::launch(*built[i], h->psi, nullptr, nullptr, flag, h->stream, nullptr));
         else
             SV_CUDA(svk::launch_stage_fwd(h->eb, h->fwd.launch(i, h->psi, nullptr, nullptr), stages[i], h->stream));
         tock(h, t0, TK_STAGE);
@@ -856,7 +889,7 @@ sv_status sv_plan_compile(const sv_plan* plan, const double* params, uint32_t wh
     for (int d = 0; d < 2; ++d) {
         if (!((which >> d) & 1)) continue;
         svh::Program prog;
-        std::string err = svh::lower(P, params, 8, d ? rmax_bwd(8) : rmax_fwd(8), d == 1, &prog);
+        std::string err = svh::lower(P, params, 8, d ? rmax_bwd(8) : rmax_fwd(8), d == 1, &prog, false, d ? 0 : rwide_fwd());
         if (!err.empty()) return fail(err.find("not supported") != std::string::npos ? SV_ERR_UNSUPPORTED : SV_ERR_ARG, err);
         svh::Packed pk;
         err = svh::pack(prog, P.n, 8, &pk);
@@ -906,7 +939,7 @@ sv_status sv_norm(sv_handle h, double* out) {
     SV_CUDA(svk::launch_reduce_rows(part, nb, 1, (double*)h->red.p, h->stream));
     SV_CUDA(cudaMemcpyAsync(out, h->red.p, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     SV_CUDA(cudaStreamSynchronize(h->stream));
-    return SV_OK;
+    return jflag_check(h);
 }
 
 sv_status sv_expval(sv_handle h, const sv_observable* obs, double* out) {
@@ -920,7 +953,7 @@ sv_status sv_expval(sv_handle h, const sv_observable* obs, double* out) {
     if (s) return s;
     SV_CUDA(cudaMemcpyAsync(out, h->red.p, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     SV_CUDA(cudaStreamSynchronize(h->stream));
-    return SV_OK;
+    return jflag_check(h);
 }
 
 sv_status sv_pauli_plan_info(uint32_t n_qubits, sv_dtype dtype, const sv_observable* obs, uint32_t* n_sweeps,
@@ -975,10 +1008,12 @@ sv_status sv_grad(sv_handle h, const sv_plan* plan, const double* params, const 
     SV_CUDA(cudaMemcpyAsync(&E, h->red.p, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     const bool jit = jit_enabled(h);
     std::vector<std::shared_ptr<svj::Built>> built;
+    int* flag = nullptr;
     if (jit) {
         err = svh::pack(bprog, (int)h->n, h->eb, &h->bwd.packed);
         if (!err.empty()) return fail(SV_ERR_ARG, err);
         s = jit_prepare(h->n, h->bwd.packed, 2, &built);
+        if (!s) s = jflag_device(h, &flag);
     } else {
         s = upload_program(h, bprog, &h->bwd, true);
     }
@@ -996,7 +1031,7 @@ sv_status sv_grad(sv_handle h, const sv_plan* plan, const double* params, const 
         cudaEvent_t t0 = tick(h);
         uint32_t grid = 0;
         if (jit)
-            SV_CUDA(svj::launch(*built[i], h->psi, h->scratch.p, (double*)h->partial.p, h->stream, &grid));
+            SV_CUDA(svj::launch(*built[i], h->psi, h->scratch.p, (double*)h->partial.p, flag, h->stream, &grid));
         else
             SV_CUDA(svk::launch_stage_bwd(h->eb, h->bwd.launch(i, h->psi, h->scratch.p, (double*)h->partial.p),
                                           st, h->stream, &grid));
@@ -1016,6 +1051,8 @@ sv_status sv_grad(sv_handle h, const sv_plan* plan, const double* params, const 
         SV_CUDA(cudaMemcpyAsync(slots.data(), h->slot_sum.p, nslots_total * sizeof(double),
                                 cudaMemcpyDeviceToHost, h->stream));
     SV_CUDA(cudaStreamSynchronize(h->stream));
+    s = jflag_check(h);
+    if (s) return s;
     if (expval_out) *expval_out = E;
     if (grad_out) {
         for (int k = 0; k < P.n_params; ++k) grad_out[k] = 0.0;

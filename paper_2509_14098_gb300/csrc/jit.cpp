@@ -13,8 +13,10 @@
 // FP32, added in FP64 to that warp's per-CTA slot sum across tiles.
 #include "jit.h"
 
+#include <cuda.h>   // tensor-map types (the encoder is looked up at run time)
 #include <nvrtc.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -41,6 +43,10 @@ struct Kernel {
 };
 
 namespace {
+
+// argument block layout (generated struct Args): m0 @0, m1 @128 (CUtensorMap, 64-byte
+// aligned), v0 @256, v1 @264, partial @272, flag @280, q[] @288
+constexpr size_t kArgV0 = 256, kArgV1 = 264, kArgPartial = 272, kArgFlag = 280, kArgQ = 288;
 
 std::mutex g_mu;
 std::unordered_map<std::string, Kernel*> g_cache;   // source -> kernel (never freed: process lifetime)
@@ -82,6 +88,42 @@ struct ArgBuilder {
     int F(float v) { f.push_back(v); return (int)f.size() - 1; }
 };
 
+struct Run { int start, len; bool local; };
+
+// TMA eligibility of a stage: the tile holds physical bits 0..3 and is at least 1 KiB
+// (the 128-byte swizzle repeats every 1 KiB), and the runs of local / global physical bits
+// (local runs cut into pieces of at most 8 bits, the first piece exactly bits 0..3, global
+// runs of at most 32 bits) form at most 5 dimensions.  SVGB_JIT_TMA=0 disables it.
+bool tma_runs(const svk::Stage& st, int n, int nv, std::vector<Run>* dims) {
+    dims->clear();
+    const int T = (int)st.T;
+    uint64_t tmask = 0;
+    for (int b = 0; b < T; ++b) tmask |= 1ull << st.tile_pos[b];
+    bool ok = n > T && T >= 7 && (tmask & 15ull) == 15ull;
+    for (int b = 0; ok && b < n;) {
+        const bool loc = (tmask >> b) & 1;
+        int e = b;
+        while (e < n && (((tmask >> e) & 1) != 0) == loc) ++e;
+        if (loc) {
+            for (int x = b; x < e;) {
+                const int len = (x == 0) ? 4 : std::min(8, e - x);
+                dims->push_back({x, len, true});
+                x += len;
+            }
+        } else {
+            if (e - b > 32) ok = false;
+            dims->push_back({b, e - b, false});
+        }
+        b = e;
+    }
+    if ((int)dims->size() > 5) ok = false;
+    // measured: the second ring slot costs the forward sweep more resident CTAs than the
+    // overlap gains (QFT30 26.5 -> 27.7 ms), while the adjoint gains about 4 %
+    bool want = nv == 2;
+    if (const char* e = getenv("SVGB_JIT_TMA")) want = atoi(e) != 0;
+    return ok && want;
+}
+
 class Gen {
   public:
     Gen(const StageView& v, Built* out) : V(v), st(*v.st), B(out) {}
@@ -96,6 +138,10 @@ class Gen {
     int T = 0, R = 0, TR = 0, NT = 0, NV = 1, NB = 1, NPH = 0, NSL = 0, NW = 1;
     bool ttab = false;        // per-(slot, thread) thread-bit angle table in shared memory
     bool cbank = false;       // per-op constants read from the parameter bank (else shared memory)
+    bool tma = false;         // tiles staged by TMA (128-byte swizzle) instead of cp.async (software swizzle)
+    int NS = 2;               // TMA ring slots
+    uint32_t swz(uint32_t e) const { return tma ? (e ^ (((e >> 4) & 7u) << 1)) : svk::swizzle8(e); }
+    std::vector<std::vector<int>> tbo;   // per group: tile bit of each thread bit
     std::vector<int> slot_thr;   // per phase slot: first u[] index of its J[i] (or -1)
     int perm[32];             // logical register index -> variable holding it
     std::string fixvar;       // name of the current group's fixed-index variable ("" = none)
@@ -377,7 +423,7 @@ std::string Gen::run() {
     // double-buffer the tiles when that still leaves the target residency
     // resident threads per SM the register budget is sized for (64 registers per thread
     // forward, 128 adjoint); SVGB_JIT_THR / SVGB_JIT_THR_BWD override for tuning
-    int thr_per_sm = NV == 2 ? 512 : 1024;
+    int thr_per_sm = (NV == 2 || R >= 5) ? 512 : 1024;
     if (const char* e = getenv(NV == 2 ? "SVGB_JIT_THR_BWD" : "SVGB_JIT_THR"))
         thr_per_sm = std::max(64, std::min(2048, atoi(e)));
     const int ctas = std::max(1, thr_per_sm / std::max(NT, 32));
@@ -393,7 +439,68 @@ std::string Gen::run() {
     cbank = NV == 1 && (int)st.n_ops <= cbank_ops;
     if (const char* e = getenv("SVGB_JIT_CBANK")) cbank = atoi(e) != 0;
 
-    // ---- argument block layout: v0, v1, partial, pad | q[] | u[] | f[] ----
+    // ---- TMA eligibility: the tile holds physical bits 0..3, the tile is at least 1 KiB
+    // (the 128-byte swizzle repeats every 1 KiB), and the runs of local / global physical
+    // bits (local runs cut into pieces of at most 8 bits, the first piece exactly bits 0..3)
+    // form at most 5 dimensions ----
+    std::vector<Run> dims;
+    tma = tma_runs(st, n, NV, &dims);
+    if (const char* e = getenv("SVGB_JIT_NS")) NS = std::max(2, std::min(4, atoi(e)));
+    if (tma) {   // coordinates of a tile along each dimension: (tile index >> shift) & mask
+        B->tma = true;
+        int gbits = 0;
+        uint32_t sh[5] = {0, 0, 0, 0, 0}, mk[5] = {0, 0, 0, 0, 0};
+        for (size_t d = 0; d < dims.size(); ++d) {
+            B->gdim[d] = 1ull << dims[d].len;
+            if (d > 0) B->gstride[d - 1] = 8ull << dims[d].start;
+            B->box[d] = dims[d].local ? (1u << dims[d].len) : 1u;
+            if (!dims[d].local) {
+                sh[d] = (uint32_t)gbits;
+                mk[d] = (uint32_t)((1ull << dims[d].len) - 1);
+                gbits += dims[d].len;
+            }
+        }
+        for (size_t d = dims.size(); d < 5; ++d) {   // unused dimensions of extent 1
+            if (d > 0) B->gstride[d - 1] = 8ull << n;
+        }
+        for (int d = 0; d < 5; ++d) A.U(sh[d]);
+        for (int d = 0; d < 5; ++d) A.U(mk[d]);
+    }
+    // thread-bit order of each register group: the tile's non-register bits, the first
+    // lanes on bits whose shared-memory bank images are independent (TMA layout)
+    tbo.assign(st.n_groups, std::vector<int>());
+    for (uint32_t g = 0; g < st.n_groups; ++g) {
+        const svk::Group& G = V.groups[g];
+        std::vector<int> rest(G.thr_pos, G.thr_pos + TR);
+        if (tma) {
+            const bool pr = G.reg_pos[0] == 0;
+            const uint32_t bmask = pr ? 0xEu : 0xFu;   // bank-select bits of a 16-byte / 8-byte access
+            const int want = pr ? 3 : 4;
+            std::vector<int> first;
+            std::vector<uint32_t> basis;
+            for (int round = 0; round < want; ++round) {
+                int pick = -1;
+                for (size_t i = 0; i < rest.size() && pick < 0; ++i) {
+                    uint32_t img = swz(1u << rest[i]) & bmask;
+                    for (uint32_t bv : basis)   // reduce against the chosen images
+                        if ((img ^ bv) < img) img ^= bv;
+                    if (img) {
+                        pick = (int)i;
+                        basis.push_back(img);
+                        std::sort(basis.rbegin(), basis.rend());
+                    }
+                }
+                if (pick < 0) break;
+                first.push_back(rest[pick]);
+                rest.erase(rest.begin() + pick);
+            }
+            first.insert(first.end(), rest.begin(), rest.end());
+            rest = first;
+        }
+        tbo[g] = rest;
+    }
+
+    // ---- argument block layout: m0, m1 (tensor maps), v0, v1, partial, flag | q[] | u[] | f[] ----
     // q: global bit values (NG), tile bit values (T), then op masks
     for (int i = 0; i < NG; ++i) A.Q(1ull << st.glob_pos[i]);
     for (int b = 0; b < T; ++b) A.Q(1ull << st.tile_pos[b]);
@@ -420,10 +527,26 @@ std::string Gen::run() {
         const svk::PhaseSlot<float>& ps = V.slots[p];
         for (uint32_t i = 0; i < ps.n_glob; ++i) A.U(V.terms[ps.glob_off + i].angle);
     }
+    // J[i] is the slot's angle per thread bit i in the lowering's order of its group's
+    // thread bits; the generated kernel may order them differently (tbo), so map them
+    std::vector<int> slot_group(NPH, -1);
+    for (uint32_t g = 0; g < st.n_groups; ++g)
+        for (uint32_t oi = 0; oi < V.groups[g].n_ops; ++oi) {
+            const svk::DevOp<float>& o = V.ops[V.groups[g].op_off + oi];
+            if ((o.flags & svk::F_SLOT) && (int)o.slot < NPH) slot_group[o.slot] = (int)g;
+        }
     for (int p = 0; p < NPH; ++p)
         if (V.slots[p].has_thr) {
+            if (slot_group[p] < 0) return "jit: a phase slot without an op";
+            const svk::Group& G = V.groups[slot_group[p]];
             slot_thr[p] = (int)A.u.size();
-            for (int i = 0; i < TR; ++i) A.U(V.slots[p].J[i]);
+            for (int i = 0; i < TR; ++i) {
+                int src = -1;
+                for (int k = 0; k < TR; ++k)
+                    if (G.thr_pos[k] == tbo[slot_group[p]][i]) src = k;
+                if (src < 0) return "internal: thread-bit order";
+                A.U(V.slots[p].J[src]);
+            }
         }
 
     // ---- per-CTA setup ----
@@ -437,9 +560,11 @@ std::string Gen::run() {
                    "if ((t >> i) & 1ull) base |= b;\nif (((u64)gridDim.x >> i) & 1ull) pstep |= b;\n}\n", NG, QG);
     // this thread's 16-byte chunks: chunk c = tid + i * NT holds tile elements 2c, 2c + 1;
     // tile bit 1 + b <- tid bit b, tile bit 1 + TR + b <- i bit b
-    pre += "u64 ptid = 0;\nu32 stid = 0;\n";
-    for (int b = 0; b < TR; ++b)
-        pre += fmt("if ((tid >> %d) & 1u) { ptid |= a.q[%d]; stid ^= %uu; }\n", b, QT + 1 + b, svk::swizzle8(1u << (1 + b)));
+    if (!tma) {
+        pre += "u64 ptid = 0;\nu32 stid = 0;\n";
+        for (int b = 0; b < TR; ++b)
+            pre += fmt("if ((tid >> %d) & 1u) { ptid |= a.q[%d]; stid ^= %uu; }\n", b, QT + 1 + b, svk::swizzle8(1u << (1 + b)));
+    }
     const int NCH = 1 << (R - 1);
     std::vector<uint32_t> chs(NCH);
     std::vector<std::string> chp(NCH);
@@ -479,19 +604,20 @@ std::string Gen::run() {
             if (needfix[g]) fixrow[g] = r++;
     }
     auto so_expr = [&](int g) {
-        const svk::Group& G = V.groups[g];
         std::string e = "(0u";
-        for (int i = 0; i < TR; ++i) e += fmt(" ^ ((tid >> %d) & 1u ? %uu : 0u)", i, svk::swizzle8(1u << G.thr_pos[i]));
+        for (int i = 0; i < TR; ++i) e += fmt(" ^ ((tid >> %d) & 1u ? %uu : 0u)", i, swz(1u << tbo[g][i]));
         return e + ")";
     };
     auto pf_expr = [&](int g, const char* src) {
-        const svk::Group& G = V.groups[g];
         std::string e = "(0ull";
-        for (int i = 0; i < TR; ++i) e += fmt(" | ((tid >> %d) & 1u ? %s.q[%d] : 0ull)", i, src, QT + G.thr_pos[i]);
+        for (int i = 0; i < TR; ++i) e += fmt(" | ((tid >> %d) & 1u ? %s.q[%d] : 0ull)", i, src, QT + tbo[g][i]);
         return e + ")";
     };
-    // shared memory: tiles | sang[NPH] | tang[NPH][NT] | gsm[NSL][NW]
-    size_t o = (size_t)NV * NB * tile_b;
+    // shared memory: tiles | mbarriers (TMA) | sang[NPH] | tang[NPH][NT] | gsm[NSL][NW]
+    size_t o = (size_t)NV * (tma ? NS : NB) * tile_b;
+    const size_t o_bar = o;
+    if (tma) o += 8 * (size_t)NS;
+    o = (o + 15) & ~(size_t)15;
     const size_t o_sang = o;
     o = (o + 4 * (size_t)NPH + 15) & ~(size_t)15;
     const size_t o_tang = o;
@@ -530,6 +656,10 @@ std::string Gen::run() {
             if (needfix[g]) pre += fmt("const u64 pf%d = %s;\n", g, pf_expr(g, "a").c_str());
         }
     }
+    if (tma) {
+        pre += fmt("u64* const bars = reinterpret_cast<u64*>(smem + %zu);\n", o_bar);
+        pre += fmt("if (tid == 0) {\nfor (int s = 0; s < %d; ++s) svj_mbar_init(&bars[s], 1u);\nsvj_fence_barrier_init();\n}\n", NS);
+    }
     pre += "__syncthreads();\n";
     if (ttab)
         for (int p = 0; p < NPH; ++p)
@@ -550,10 +680,34 @@ std::string Gen::run() {
         return r + "svj_cp_commit();\n";
     };
     std::string body;
-    body += load("0", "base");
+    // TMA: a tile is one box of the 5-D view; its coordinates come from the tile index
+    auto crd = [&](const char* tt) {
+        std::string r;
+        for (int d = 0; d < 5; ++d) r += fmt("%s(int)(((%s) >> S.u[%d]) & (u64)S.u[%d])", d ? ", " : "", tt, d, 5 + d);
+        return r;
+    };
+    auto tma_load = [&](const char* slot, const char* tt) {
+        std::string r = fmt("svj_mbar_expect_tx(&bars[%s], %zuu);\n", slot, (size_t)NV * tile_b);
+        for (int v = 0; v < NV; ++v)
+            r += fmt("svj_tma_load(tl + ((%s * %d + %d) << %d), &a.m%d, %s, &bars[%s]);\n", slot, NV, v, T, v, crd(tt).c_str(), slot);
+        return r;
+    };
+    if (tma) {
+        body += "if (tid == 0) {\n";
+        for (int sl = 0; sl < NS; ++sl)
+            body += fmt("if (t + %du * (u64)gridDim.x < ntiles) {\nconst u64 tt = t + %du * (u64)gridDim.x;\n", sl, sl) +
+                    tma_load(std::to_string(sl).c_str(), "tt") + "}\n";
+        body += "}\n";
+    } else {
+        body += load("0", "base");
+    }
+    if (tma) body += "u32 brk = 0xffffffffu;   // iteration whose tile wait gave up\n";
     body += "#pragma unroll 1\nfor (u32 it = 0; t < ntiles; t += gridDim.x, ++it) {\n";
     body += "const u64 bn = ((base | ~gmask) + pstep) & gmask;\n";
-    if (NB == 2) {
+    if (tma) {
+        body += fmt("const u32 cb = it %% %du;\n", NS);
+        body += fmt("if (!__syncthreads_and(svj_mbar_wait(&bars[cb], (it / %du) & 1u, a.flag))) {\nbrk = it;\nbreak;\n}\n", NS);
+    } else if (NB == 2) {
         body += "const u32 cb = it & 1u;\n";
         body += "if (t + gridDim.x < ntiles) {\n" + load("cb ^ 1u", "bn") + "svj_cp_wait1();\n} else {\nsvj_cp_wait0();\n}\n";
     } else {
@@ -567,7 +721,10 @@ std::string Gen::run() {
                     slot_ang_u, slot_q0);
     }
     body += "__syncthreads();\n";
-    for (int v = 0; v < NV; ++v) body += fmt("float2* const T%d = tl + ((%d * %d + cb) << %d);\n", v, v, NB, T);
+    for (int v = 0; v < NV; ++v) {
+        if (tma) body += fmt("float2* const T%d = tl + ((cb * %d + %d) << %d);\n", v, NV, v, T);
+        else body += fmt("float2* const T%d = tl + ((%d * %d + cb) << %d);\n", v, v, NB, T);
+    }
     for (int g = 0; g < ng; ++g) {
         const svk::Group& G = V.groups[g];
         const int K = 1 << R;
@@ -576,7 +733,7 @@ std::string Gen::run() {
         for (int k = 0; k < K; ++k) {
             uint32_t x = 0;
             for (int j = 0; j < R; ++j)
-                if ((k >> j) & 1) x ^= svk::swizzle8(1u << G.reg_pos[j]);
+                if ((k >> j) & 1) x ^= swz(1u << G.reg_pos[j]);
             sr[k] = x;
         }
         const bool pairs = G.reg_pos[0] == 0;
@@ -611,14 +768,31 @@ std::string Gen::run() {
                 for (int k = 0; k < K; ++k) body += fmt("T%d[so%d ^ %uu] = %s;\n", v, g, sr[k], amp(v, k).c_str());
             }
         }
-        body += "}\n__syncthreads();\n";
+        // the last group's writes become visible to the tile's TMA store
+        body += (tma && g == ng - 1) ? "}\nsvj_fence_async_smem();\n__syncthreads();\n" : "}\n__syncthreads();\n";
     }
-    // write the tile back in place
-    for (int i = 0; i < NCH; ++i)
-        for (int v = 0; v < NV; ++v)
-            body += fmt("*reinterpret_cast<float4*>(a.v%d + (base | ptid | %s)) = *reinterpret_cast<const float4*>(T%d + (stid ^ %uu));\n",
-                        v, chp[i].c_str(), v, chs[i]);
-    body += "base = bn;\n__syncthreads();\n}\n";
+    if (tma) {
+        // one thread stores the tile (bulk tensor copy) and refills the slot with the tile
+        // NS steps ahead once the store has read it
+        body += "if (tid == 0) {\n";
+        for (int v = 0; v < NV; ++v) body += fmt("svj_tma_store(&a.m%d, %s, T%d);\n", v, crd("t").c_str(), v);
+        body += "svj_bulk_commit();\n";
+        body += fmt("const u64 tn = t + %du * (u64)gridDim.x;\nif (tn < ntiles) {\nsvj_bulk_wait_read0();\n", NS) +
+                tma_load("cb", "tn") + "}\n}\n";
+        body += "base = bn;\n}\n";
+        // a wait that gave up leaves loads in flight: wait for them (bounded) before the
+        // CTA's shared memory goes away; then for the tile stores
+        body += fmt("if (tid == 0) {\nif (brk != 0xffffffffu)\nfor (u32 k = 0; k < %du; ++k) {\nconst u32 i2 = brk + k;\n"
+                    "if ((u64)blockIdx.x + (u64)i2 * gridDim.x < ntiles) svj_mbar_wait(&bars[i2 %% %du], (i2 / %du) & 1u, nullptr);\n}\n"
+                    "svj_bulk_wait0();\n}\n", NS, NS, NS);
+    } else {
+        // write the tile back in place
+        for (int i = 0; i < NCH; ++i)
+            for (int v = 0; v < NV; ++v)
+                body += fmt("*reinterpret_cast<float4*>(a.v%d + (base | ptid | %s)) = *reinterpret_cast<const float4*>(T%d + (stid ^ %uu));\n",
+                            v, chp[i].c_str(), v, chs[i]);
+        body += "base = bn;\n__syncthreads();\n}\n";
+    }
     if (NSL)
         body += fmt("for (u32 sl = tid; sl < %du; sl += %du) {\ndouble x = 0.0;\nfor (int w = 0; w < %d; ++w) x += gsm[sl * %d + w];\n"
                     "a.partial[(u64)blockIdx.x * %d + sl] = x;\n}\n", NSL, NT, NW, NW, NSL);
@@ -629,11 +803,11 @@ std::string Gen::run() {
     const int minb = std::max(1, std::min(32, thr_per_sm / NT));
     std::string head;
     head += "#include \"jit_prelude.cuh\"\n";
-    head += fmt("struct alignas(16) Args {\nfloat2* v0;\nfloat2* v1;\ndouble* partial;\nu64 pad;\nu64 q[%d];\nu32 u[%d];\nfloat f[%d];\n};\n",
-                nq, nu, nf);
+    head += fmt("struct alignas(64) Args {\nSvjTmap m0;\nSvjTmap m1;\nfloat2* v0;\nfloat2* v1;\ndouble* partial;\nint* flag;\n"
+                "u64 q[%d];\nu32 u[%d];\nfloat f[%d];\n};\n", nq, nu, nf);
     std::string src = head + "extern \"C\" __global__ void __launch_bounds__(" + std::to_string(NT) + ", " +
                       std::to_string(minb) + ") KNAME(const __grid_constant__ Args a) {\n"
-                      "extern __shared__ __attribute__((aligned(16))) unsigned char smem[];\n" + pre + body + "}\n";
+                      "extern __shared__ __attribute__((aligned(1024))) unsigned char smem[];\n" + pre + body + "}\n";
     const std::string name = fmt("svj_%s_%016llx", NV == 2 ? "adj" : "fwd", (unsigned long long)fnv1a(src));
     size_t pos;
     while ((pos = src.find("KNAME")) != std::string::npos) src.replace(pos, 5, name);
@@ -642,17 +816,19 @@ std::string Gen::run() {
     B->nthr = (uint32_t)NT;
     B->n_slots = (uint32_t)NSL;
     B->ntiles = 1ull << NG;
-    // argument bytes, matching the struct: 32 B of pointers/pad, q, u, f, padded to 16
-    size_t bytes = 32 + 8 * (size_t)nq + 4 * (size_t)nu;
+    // argument bytes, matching the struct: two 128-byte tensor maps, four pointers, q, u,
+    // f, padded to the struct's 64-byte alignment
+    const size_t off_q = kArgQ;
+    size_t bytes = off_q + 8 * (size_t)nq + 4 * (size_t)nu;
     bytes = (bytes + 3) & ~(size_t)3;
     const size_t off_f = bytes;
     bytes += 4 * (size_t)nf;
-    bytes = (bytes + 15) & ~(size_t)15;
+    bytes = (bytes + 63) & ~(size_t)63;
     if (bytes > 32000) return "jit: stage constants exceed the kernel argument space";
     B->smem = (uint32_t)(cbank ? o_args : o_args + bytes);
     B->args.assign(bytes, 0);
-    std::memcpy(B->args.data() + 32, A.q.data(), 8 * A.q.size());
-    std::memcpy(B->args.data() + 32 + 8 * nq, A.u.data(), 4 * A.u.size());
+    std::memcpy(B->args.data() + off_q, A.q.data(), 8 * A.q.size());
+    std::memcpy(B->args.data() + off_q + 8 * nq, A.u.data(), 4 * A.u.size());
     std::memcpy(B->args.data() + off_f, A.f.data(), 4 * A.f.size());
     return "";
 }
@@ -676,7 +852,12 @@ std::string structure_key(const StageView& v) {
     put(st.n_phase);
     put(st.n_ops);
     put(st.tile_pos[0]);
-    for (const char* e : {"SVGB_JIT_NB", "SVGB_JIT_THR", "SVGB_JIT_THR_BWD", "SVGB_JIT_CBANK", "SVGB_JIT_CBANK_OPS", "SVGB_JIT_GTAB"}) {
+    put(st.R);
+    {
+        std::vector<Run> dims;
+        put(tma_runs(st, v.n, v.nv, &dims) ? 1 : 0);
+    }
+    for (const char* e : {"SVGB_JIT_TMA", "SVGB_JIT_NS", "SVGB_JIT_NB", "SVGB_JIT_THR", "SVGB_JIT_THR_BWD", "SVGB_JIT_CBANK", "SVGB_JIT_CBANK_OPS", "SVGB_JIT_GTAB"}) {
         const char* x = getenv(e);
         k += x ? x : "-";
         k += '|';
@@ -828,7 +1009,44 @@ std::string compile(std::vector<Built*>& kernels) {
     return "";
 }
 
-cudaError_t launch(const Built& b, void* v0, void* v1, double* partial, cudaStream_t s, uint32_t* grid_out) {
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime (the
+// library links the runtime only)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, []() {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    });
+    return fn;
+}
+
+// the stage's 5-D view of a state vector at ptr (8-byte elements, 128-byte swizzle)
+static cudaError_t encode_map(const Built& b, void* ptr, void* out) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    const cuuint32_t estride[5] = {1, 1, 1, 1, 1};
+    cuuint64_t gdim[5], gstr[4];
+    cuuint32_t box[5];
+    for (int d = 0; d < 5; ++d) {
+        gdim[d] = b.gdim[d];
+        box[d] = b.box[d];
+    }
+    for (int d = 0; d < 4; ++d) gstr[d] = b.gstride[d];
+    const CUresult r = fn((CUtensorMap*)out, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 5, ptr, gdim, gstr, box, estride,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch(const Built& b, void* v0, void* v1, double* partial, int* flag, cudaStream_t s,
+                   uint32_t* grid_out) {
     Kernel* k = b.kernel;
     if (!k || !k->err.empty() || k->cubin.empty()) return cudaErrorInvalidDeviceFunction;
     int dev = 0;
@@ -857,11 +1075,24 @@ cudaError_t launch(const Built& b, void* v0, void* v1, double* partial, cudaStre
     if (e != cudaSuccess) return e;
     const uint64_t grid = std::min<uint64_t>(b.ntiles, (uint64_t)k->per_sm_dev * (uint64_t)nsm);
     if (grid_out) *grid_out = (uint32_t)grid;
-    std::vector<uint8_t> args = b.args;
-    std::memcpy(args.data() + 0, &v0, 8);
-    std::memcpy(args.data() + 8, &v1, 8);
-    std::memcpy(args.data() + 16, &partial, 8);
-    void* params[1] = {args.data()};
+    // the argument block, 64-byte aligned (the tensor maps inside must be)
+    alignas(64) static thread_local uint8_t argbuf[32768];
+    if (b.args.size() > sizeof(argbuf)) return cudaErrorInvalidValue;
+    uint8_t* args = argbuf;
+    std::memcpy(args, b.args.data(), b.args.size());
+    std::memcpy(args + kArgV0, &v0, 8);
+    std::memcpy(args + kArgV1, &v1, 8);
+    std::memcpy(args + kArgPartial, &partial, 8);
+    std::memcpy(args + kArgFlag, &flag, 8);
+    if (b.tma) {
+        e = encode_map(b, v0, args + 0);
+        if (e != cudaSuccess) return e;
+        if (v1) {
+            e = encode_map(b, v1, args + 128);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    void* params[1] = {args};
     return cudaLaunchKernel((const void*)k->fn, dim3((unsigned)grid), dim3(b.nthr), params, b.smem, s);
 }
 

@@ -41,6 +41,12 @@ struct Built {
     std::vector<uint8_t> args;   // pointers at offsets 0 (v0), 8 (v1), 16 (partial) patched at launch
     uint32_t nthr = 0, smem = 0, n_slots = 0;
     uint64_t ntiles = 0;
+    // TMA tile staging (tma): the state seen as a 5-D tensor of 8-byte elements whose
+    // dimensions are runs of consecutive physical bits; the tile is one box
+    bool tma = false;
+    uint64_t gdim[5] = {1, 1, 1, 1, 1};
+    uint64_t gstride[4] = {0, 0, 0, 0};   // bytes, dimensions 1..4
+    uint32_t box[5] = {1, 1, 1, 1, 1};
     Kernel* kernel = nullptr;    // set by compile()
 };
 
@@ -52,8 +58,10 @@ std::string generate(const StageView& v, Built* out);
 std::string compile(std::vector<Built*>& kernels);
 
 // Launch a built stage: persistent grid of min(tiles, CTAs per SM x SMs) CTAs.
-// grid_out: CTAs launched (rows of gradient partials for the adjoint).
-cudaError_t launch(const Built& b, void* v0, void* v1, double* partial, cudaStream_t s, uint32_t* grid_out);
+// grid_out: CTAs launched (rows of gradient partials for the adjoint).  flag: device
+// int set to 1 if a bounded wait of the kernel gave up (the caller reports it).
+cudaError_t launch(const Built& b, void* v0, void* v1, double* partial, int* flag, cudaStream_t s,
+                   uint32_t* grid_out);
 
 // NVRTC compiles and cache hits since load (diagnostics).
 void stats(uint64_t* compiles, uint64_t* hits, double* compile_ms);

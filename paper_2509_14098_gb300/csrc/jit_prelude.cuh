@@ -92,10 +92,10 @@ SVJ_DI bool svj_mbar_try_wait(u64* bar, u32 parity) {
                  : "memory");
     return ok != 0;
 }
-// bounded wait on a barrier phase: false (and *flag set) if it did not complete in
-// about a second; the caller skips its work and the host reports SV_ERR_TIMEOUT
+// bounded wait on a barrier phase: false (and *flag set) if it did not complete within
+// 2^22 polls (a few seconds at most); the caller stops and the host reports SV_ERR_TIMEOUT
 SVJ_DI bool svj_mbar_wait(u64* bar, u32 parity, int* flag) {
-    for (u32 i = 0; i < (1u << 26); ++i)
+    for (u32 i = 0; i < (1u << 22); ++i)
         if (svj_mbar_try_wait(bar, parity)) return true;
     if (flag) atomicExch(flag, 1);
     return false;

@@ -36,15 +36,15 @@ struct Pend {
 
 class Lowerer {
   public:
-    Lowerer(const Plan& p, const double* params, int eb, int rmax, bool bwd, bool bind, Program* out)
-        : P_(p), params_(params), eb_(eb), rmax_(rmax), bwd_(bwd), bind_(bind), out_(out) {}
+    Lowerer(const Plan& p, const double* params, int eb, int rmax, bool bwd, bool bind, Program* out, int rwide)
+        : P_(p), params_(params), eb_(eb), rmax_(rmax), rwide_(rwide), bwd_(bwd), bind_(bind), out_(out) {}
 
     std::string run();
 
   private:
     const Plan& P_;
     const double* params_;
-    int eb_, rmax_;
+    int eb_, rmax_, rwide_;
     bool bwd_, bind_;
     Program* out_;
     std::map<uint64_t, Pend> pending_;
@@ -361,9 +361,8 @@ std::string Lowerer::stage(int s) {
     int ng = 0;
     for (int b = 0; b < n; ++b)
         if (!((tile >> b) & 1)) st.glob_pos[ng++] = (uint8_t)b;
-    const int R = std::min(rmax_, T);
+    int R = std::min(rmax_, T);
     st.T = (uint32_t)T;
-    st.R = (uint32_t)R;
     st.n_glob = (uint32_t)ng;
     for (int b = 0; b < T; ++b) {
         st.ptile[b] = 1ull << st.tile_pos[b];
@@ -382,6 +381,17 @@ std::string Lowerer::stage(int s) {
     Partition groups;
     std::string err = partition_core(n, sub, R, 0, tile, &groups, nullptr);
     if (!err.empty()) return "register partition: " + err;
+    // deep stages: a wider register level (more amplitudes per thread) when it needs
+    // fewer register groups, i.e. fewer shared-memory exchanges per tile
+    if (rwide_ > R && groups.local.size() >= 4 && std::min(rwide_, T) > R) {
+        Partition wide;
+        const int R2 = std::min(rwide_, T);
+        if (partition_core(n, sub, R2, 0, tile, &wide, nullptr).empty() && wide.local.size() < groups.local.size()) {
+            groups = wide;
+            R = R2;
+        }
+    }
+    st.R = (uint32_t)R;
 
     st.group_off = (uint32_t)out_->groups.size();
     st.n_groups = (uint32_t)groups.local.size();
@@ -615,9 +625,9 @@ std::string pack(const Program& p, int n, int elem_bytes, Packed* out) {
 }
 
 std::string lower(const Plan& plan, const double* params, int elem_bytes, int rmax, bool backward,
-                  Program* out, bool bind) {
+                  Program* out, bool bind, int rwide) {
     if (plan.n_params > 0 && params == nullptr && !bind) return "circuit has parameters but params is NULL";
-    Lowerer L(plan, params, elem_bytes, rmax, backward, bind, out);
+    Lowerer L(plan, params, elem_bytes, rmax, backward, bind, out, rwide);
     return L.run();
 }
 

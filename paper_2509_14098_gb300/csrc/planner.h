@@ -102,7 +102,9 @@ std::string pack(const Program& p, int n, int elem_bytes, Packed* out);
 // PGate::bound), so the program's structure does not depend on the parameters;
 // params may then be NULL (the kernel forms those matrices).  Parametric P / CP are
 // rejected in this mode.
+// rwide > rmax: a stage that needs 4 or more register groups at rmax is lowered with
+// rwide register bits instead when that needs fewer groups (0: never).
 std::string lower(const Plan& plan, const double* params, int elem_bytes, int rmax, bool backward,
-                  Program* out, bool bind = false);
+                  Program* out, bool bind = false, int rwide = 0);
 
 }  // namespace svh
