@@ -343,13 +343,21 @@ def batch_section(args, steps):
            "tune": {str(k): list(v) for k, v in sorted(table.items())},
            "programs": info["n_programs"], "resident_circuits": info["n_resident"],
            "workspace_gb": info["workspace_bytes"] / 1e9, "smem_bytes": info["smem_bytes"], "grid": info["grid"],
-           "graph": bool(info["graph"]), "launches_per_batch": 1}
+           "graph": bool(info["graph"]), "graph_launches_per_batch": 1,
+           "wide_threshold": int(os.environ.get("SVGB_BATCH_WIDE", "14")),
+           "fusion_width_k": "register-group width (amplitudes per thread 2^k) of the persistent kernel; "
+                             "circuits at or above wide_threshold qubits run as wide groups (one generated "
+                             "kernel per stage over all circuits of a structure, L = 12, k = 4)"}
     b.close()
     if args.part == "all":
         plans = [sv.Plan(c, min(12, c.n_qubits)) for c in circs]
         offs = np.concatenate([[0], np.cumsum([c.n_params for c in circs])])
         sts = {}
-        for i in range(min(16, len(circs))):   # warm-up: one handle per width
+        seen = set()
+        for i in range(len(circs)):   # warm-up: one handle and one run (kernel compile) per width
+            if circs[i].n_qubits in seen:
+                continue
+            seen.add(circs[i].n_qubits)
             st = sts.setdefault(circs[i].n_qubits, sv.StateVector(circs[i].n_qubits))
             st.reset()
             st.grad(plans[i], params[offs[i]:offs[i + 1]], obs[i])

@@ -5,13 +5,16 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <string>
 #include <vector>
 
 #include "batch.h"
 #include "internal.h"
+#include "jit.h"
 #include "kernels.h"
 #include "planner.h"
 #include "sv.h"
@@ -86,7 +89,7 @@ void append_section(std::vector<T>* dst, const svh::Packed& p, size_t off, size_
 }
 
 // Build the programs, queue and shared-memory layout for the circuits `ids` under
-// tuning table `tune`.  Expectation values go to position j of ids (out = j).
+// tuning table `tune`.  Circuit ids[j]'s expectation value goes to index ids[j].
 sv_status build(const std::vector<CircIn>& in, const std::vector<uint32_t>& ids, const sv_tune& tune, Built* B) {
     *B = Built();
     std::vector<svk::BatchProg> progs;
@@ -195,7 +198,7 @@ sv_status build(const std::vector<CircIn>& in, const std::vector<uint32_t>& ids,
         std::memset(&bc, 0, sizeof(bc));
         bc.prog = prog_of[j];
         bc.param_off = c.param_off;
-        bc.out = j;
+        bc.out = ids[j];
         bc.obs_off = (uint32_t)obs.size();
         bc.n_obs = (uint32_t)c.obs.size();
         const std::vector<int>& fm = final_maps[prog_of[j]];
@@ -260,6 +263,25 @@ sv_status build(const std::vector<CircIn>& in, const std::vector<uint32_t>& ids,
     return SV_OK;
 }
 
+// Circuits of at least this many qubits run as wide groups: all circuits of one
+// structure sweep each stage together in one generated kernel (jit.h, batched mode),
+// instead of one CTA per circuit in the persistent kernel (SVGB_BATCH_WIDE; 0 = never).
+uint32_t wide_threshold() {
+    const char* e = getenv("SVGB_BATCH_WIDE");
+    return e ? (uint32_t)std::max(0, atoi(e)) : 14u;
+}
+constexpr uint32_t kWideL = 12;   // tile width of the wide groups' stages
+
+struct WideGroup {
+    uint32_t n = 0, ncirc = 0, np = 0, nst = 0, nblk = 0;
+    std::vector<uint32_t> circ;                         // indices into the batch's circuits
+    std::vector<std::shared_ptr<svj::Built>> fwd, bwd;  // generated batched stage kernels
+    std::vector<svk::Stage> bst;                        // adjoint stages (T, slots)
+    DevMem ws, tab, partial, slotsum, epart;
+    size_t o_pofs = 0, o_out = 0, o_obsoff = 0, o_obs = 0, o_pidx = 0, o_plist = 0;
+    size_t partial_bytes = 0;
+};
+
 }  // namespace
 
 struct sv_batch_s {
@@ -279,6 +301,7 @@ struct sv_batch_s {
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     double last_ms = 0.0;
+    std::vector<std::unique_ptr<WideGroup>> wide;
 
     void drop_graph() {
         if (exec) cudaGraphExecDestroy(exec);
@@ -293,6 +316,13 @@ struct sv_batch_s {
         params.release();
         out.release();
         queue.release();
+        for (auto& g : wide) {
+            g->ws.release();
+            g->tab.release();
+            g->partial.release();
+            g->slotsum.release();
+            g->epart.release();
+        }
         if (h_params) cudaFreeHost(h_params);
         if (h_out) cudaFreeHost(h_out);
         if (ev0) cudaEventDestroy(ev0);
@@ -335,6 +365,166 @@ sv_status upload(sv_batch* b, const Built& B) {
     return SV_OK;
 }
 
+// Build the wide groups: per structure, the partition (tile width kWideL), the bind-mode
+// programs, their generated batched kernels (compiled and loaded here, before any
+// capture), the per-circuit tables and the workspaces.
+sv_status build_wide(sv_batch* b) {
+    b->wide.clear();
+    const uint32_t W = wide_threshold();
+    if (W == 0) return SV_OK;
+    std::map<std::string, size_t> by_key;
+    for (uint32_t i = 0; i < b->in.size(); ++i) {
+        const CircIn& c = b->in[i];
+        if (c.n < W || c.n <= kWideL) continue;
+        auto it = by_key.find(c.key);
+        if (it == by_key.end()) {
+            by_key[c.key] = b->wide.size();
+            b->wide.emplace_back(new WideGroup());
+            b->wide.back()->n = c.n;
+            b->wide.back()->np = c.n_params;
+            it = by_key.find(c.key);
+        }
+        b->wide[it->second]->circ.push_back(i);
+    }
+    std::vector<svj::Built*> to_compile;
+    std::vector<std::vector<std::pair<uint64_t, double>>> gobs;
+    for (auto& gp : b->wide) {
+        WideGroup& G = *gp;
+        const CircIn& c0 = b->in[G.circ[0]];
+        G.ncirc = (uint32_t)G.circ.size();
+        svh::Plan P;
+        P.n = (int)c0.n;
+        P.n_params = (int)c0.n_params;
+        P.L = (int)kWideL;
+        P.gates = c0.gates;
+        svh::relabel(P.n, P.gates, &P.phys, &P.final_map);
+        for (size_t g = 0; g < P.gates.size(); ++g)
+            if (P.gates[g].kind == svh::K_RZ && P.gates[g].param >= 0) P.phys[g].bound = true;
+        std::string err = svh::partition_core(P.n, P.phys, (int)kWideL, 15ull, (1ull << c0.n) - 1, &P.top, nullptr);
+        if (!err.empty()) return set_error(SV_ERR_PARTITION, err.c_str());
+        svh::Program fp, bp;
+        err = svh::lower(P, nullptr, 8, 4, false, &fp, true);
+        if (err.empty()) err = svh::lower(P, nullptr, 8, 4, true, &bp, true);
+        if (!err.empty()) return set_error(SV_ERR_UNSUPPORTED, err.c_str());
+        svh::Packed pf, pb;
+        svh::pack(fp, P.n, 8, &pf);
+        svh::pack(bp, P.n, 8, &pb);
+        for (int d = 0; d < 2; ++d) {
+            const svh::Packed& pk = d ? pb : pf;
+            const uint8_t* blob = pk.blob.data();
+            const auto* groups = (const svk::Group*)(blob + pk.group_off);
+            const auto* ops = (const svk::DevOp<float>*)(blob + pk.op_off);
+            const auto* terms = (const svk::DevTerm<float>*)(blob + pk.term_off);
+            const auto* slots = (const svk::PhaseSlot<float>*)(blob + pk.slot_off);
+            for (size_t si = 0; si < pk.stages.size(); ++si) {
+                const svk::Stage& st = pk.stages[si];
+                svj::StageView v{&st, groups + st.group_off, ops + st.op_off, terms, slots + st.phase_off, (int)c0.n, d + 1};
+                v.batched = 1;
+                v.zero_init = (d == 0 && si == 0) ? 1 : 0;
+                auto bt = std::make_shared<svj::Built>();
+                err = svj::generate(v, bt.get());
+                if (!err.empty()) return set_error(SV_ERR_UNSUPPORTED, err.c_str());
+                if (bt->smem > 227 * 1024) return set_error(SV_ERR_UNSUPPORTED, "wide batch stage exceeds shared memory");
+                (d ? G.bwd : G.fwd).push_back(bt);
+                to_compile.push_back(bt.get());
+            }
+        }
+        G.bst = pb.stages;
+        G.nst = (uint32_t)bp.slot_param.size();
+        // parameter -> slots (CSR)
+        std::vector<uint32_t> pidx(G.np + 1, 0), plist;
+        for (int sp : bp.slot_param)
+            if (sp >= 0 && (uint32_t)sp < G.np) pidx[sp + 1]++;
+        for (uint32_t p = 0; p < G.np; ++p) pidx[p + 1] += pidx[p];
+        plist.assign(pidx[G.np], 0);
+        std::vector<uint32_t> fill(pidx.begin(), pidx.end() - 1);
+        for (size_t sl = 0; sl < bp.slot_param.size(); ++sl) {
+            const int sp = bp.slot_param[sl];
+            if (sp >= 0 && (uint32_t)sp < G.np) plist[fill[sp]++] = (uint32_t)sl;
+        }
+        // per-circuit tables: parameter offsets, output index, observable terms (physical)
+        std::vector<uint32_t> pofs, outidx, obs_off(1, 0);
+        std::vector<svk::ObsTerm> obs;
+        for (uint32_t ci : G.circ) {
+            const CircIn& c = b->in[ci];
+            pofs.push_back(c.param_off);
+            outidx.push_back(ci);
+            for (auto& t : c.obs) {
+                uint64_t m = 0;
+                for (uint32_t q = 0; q < c.n; ++q)
+                    if ((t.first >> q) & 1) m |= 1ull << P.final_map[q];
+                obs.push_back(svk::ObsTerm{m, t.second});
+            }
+            obs_off.push_back((uint32_t)obs.size());
+        }
+        std::vector<uint8_t> tab;
+        auto place = [&](const void* src, size_t bytes) {
+            size_t off = align_to(tab.size(), 16);
+            tab.resize(off + bytes + 16, 0);
+            if (bytes) std::memcpy(tab.data() + off, src, bytes);
+            return off;
+        };
+        G.o_pofs = place(pofs.data(), pofs.size() * 4);
+        G.o_out = place(outidx.data(), outidx.size() * 4);
+        G.o_obsoff = place(obs_off.data(), obs_off.size() * 4);
+        G.o_obs = place(obs.data(), obs.size() * sizeof(svk::ObsTerm));
+        G.o_pidx = place(pidx.data(), pidx.size() * 4);
+        G.o_plist = place(plist.data(), std::max<size_t>(1, plist.size()) * 4);
+        BT_CUDA(G.tab.ensure(tab.size()));
+        BT_CUDA(cudaMemcpy(G.tab.p, tab.data(), tab.size(), cudaMemcpyHostToDevice));
+        BT_CUDA(G.ws.ensure((size_t)G.ncirc * 2 * 8 << c0.n));
+        size_t pmax = 8;
+        for (const svk::Stage& st : G.bst)
+            pmax = std::max<size_t>(pmax, (size_t)G.ncirc * ((size_t)st.n_slots << (c0.n - st.T)) * 8);
+        G.partial_bytes = pmax;
+        BT_CUDA(G.partial.ensure(pmax));
+        BT_CUDA(G.slotsum.ensure(std::max<size_t>(8, (size_t)G.ncirc * G.nst * 8)));
+        G.nblk = (uint32_t)std::max<uint64_t>(1, (1ull << c0.n) / 4096);
+        BT_CUDA(G.epart.ensure((size_t)G.ncirc * G.nblk * 8));
+    }
+    if (!to_compile.empty()) {
+        std::string err = svj::compile(to_compile);
+        if (!err.empty()) return set_error(SV_ERR_CUDA, ("compiling the wide batch kernels: " + err).c_str());
+        for (svj::Built* bt : to_compile) BT_CUDA(svj::preload(*bt));
+    }
+    return SV_OK;
+}
+
+// the wide groups' part of one evaluation (stream-ordered after the persistent launch)
+cudaError_t launch_wide(sv_batch* b) {
+    for (auto& gp : b->wide) {
+        WideGroup& G = *gp;
+        const uint8_t* tab = (const uint8_t*)G.tab.p;
+        float2* psi = (float2*)G.ws.p;
+        float2* lam = psi + ((size_t)G.ncirc << G.n);
+        const uint32_t* pofs = (const uint32_t*)(tab + G.o_pofs);
+        const double* prm = (const double*)b->params.p;
+        cudaError_t e = cudaSuccess;
+        for (auto& k : G.fwd)
+            if ((e = svj::launch_batched(*k, psi, nullptr, nullptr, nullptr, prm, pofs, G.ncirc, b->stream)) != cudaSuccess)
+                return e;
+        e = svk::launch_bgs_obs(psi, lam, (int)G.n, G.ncirc, (const svk::ObsTerm*)(tab + G.o_obs),
+                                (const uint32_t*)(tab + G.o_obsoff), (double*)G.epart.p, G.nblk, b->stream);
+        if (e != cudaSuccess) return e;
+        for (size_t i = 0; i < G.bwd.size(); ++i) {
+            const svk::Stage& st = G.bst[i];
+            if (st.n_slots && (e = cudaMemsetAsync(G.partial.p, 0, G.partial_bytes, b->stream)) != cudaSuccess) return e;
+            if ((e = svj::launch_batched(*G.bwd[i], psi, lam, (double*)G.partial.p, nullptr, prm, pofs, G.ncirc,
+                                         b->stream)) != cudaSuccess)
+                return e;
+            if (st.n_slots &&
+                (e = svk::launch_bgs_slotsum((const double*)G.partial.p, G.ncirc, 1u << (G.n - st.T), st.n_slots,
+                                             st.slot_off, G.nst, (double*)G.slotsum.p, b->stream)) != cudaSuccess)
+                return e;
+        }
+        e = svk::launch_bgs_finish((const double*)G.epart.p, G.nblk, (const double*)G.slotsum.p, G.nst,
+                                   (const uint32_t*)(tab + G.o_pidx), (const uint32_t*)(tab + G.o_plist), G.np, pofs,
+                                   (const uint32_t*)(tab + G.o_out), G.ncirc, b->args.expval, b->args.grad, b->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 // one evaluation without the graph (queue and gradient reset, launch)
 sv_status launch_direct(sv_batch* b) {
     BT_CUDA(cudaMemsetAsync(b->queue.p, 0, 4, b->stream));
@@ -351,7 +541,8 @@ sv_status capture(sv_batch* b) {
                                     cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->queue.p, 0, 4, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->args.grad, 0, std::max<size_t>(8, b->total_params * 8), b->stream);
-    if (e == cudaSuccess) e = svk::launch_batch(b->args, b->grid, b->stream);
+    if (e == cudaSuccess && b->built.n_circ) e = svk::launch_batch(b->args, b->grid, b->stream);
+    if (e == cudaSuccess) e = launch_wide(b);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_out, b->out.p, n_out * 8, cudaMemcpyDeviceToHost, b->stream);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
@@ -364,14 +555,24 @@ sv_status capture(sv_batch* b) {
     return SV_OK;
 }
 
+bool is_wide(const CircIn& c) {
+    const uint32_t W = wide_threshold();
+    return W && c.n >= W && c.n > kWideL;
+}
+
 sv_status rebuild(sv_batch* b) {
-    std::vector<uint32_t> all(b->in.size());
-    for (size_t i = 0; i < all.size(); ++i) all[i] = (uint32_t)i;
-    sv_status s = build(b->in, all, b->tune, &b->built);
+    std::vector<uint32_t> small;
+    for (uint32_t i = 0; i < b->in.size(); ++i)
+        if (!is_wide(b->in[i])) small.push_back(i);
+    sv_status s = build(b->in, small, b->tune, &b->built);
     if (s != SV_OK) return s;
     b->drop_graph();
     s = upload(b, b->built);
     if (s != SV_OK) return s;
+    if (b->wide.empty()) {
+        s = build_wide(b);
+        if (s != SV_OK) return s;
+    }
     return capture(b);
 }
 
@@ -484,7 +685,7 @@ sv_status sv_autotune(sv_batch* b, const double* params, sv_tune* table_out) {
     BT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->dev));
     std::map<uint32_t, std::vector<uint32_t>> by_n;
     for (uint32_t i = 0; i < b->in.size(); ++i)
-        if (by_n[b->in[i].n].size() < (size_t)nsm) by_n[b->in[i].n].push_back(i);
+        if (!is_wide(b->in[i]) && by_n[b->in[i].n].size() < (size_t)nsm) by_n[b->in[i].n].push_back(i);
     sv_tune best_table = b->tune;
     for (auto& kv : by_n) {
         const uint32_t n = kv.first;
@@ -535,10 +736,11 @@ sv_status sv_batch_info_get(const sv_batch* b, sv_batch_info* out) {
     if (!b || !out) return set_error(SV_ERR_ARG, "null argument");
     std::memset(out, 0, sizeof(*out));
     out->n_circuits = (uint32_t)b->in.size();
-    out->n_programs = b->built.n_prog;
+    out->n_programs = b->built.n_prog + (uint32_t)b->wide.size();
     out->n_resident = b->built.n_resident;
     out->total_params = b->total_params;
     out->workspace_bytes = b->built.ws_amps * 8;
+    for (const auto& g : b->wide) out->workspace_bytes += (uint64_t)g->ncirc * 2 * 8 << g->n;
     out->smem_bytes = b->built.sm.total;
     out->grid = (uint32_t)b->grid;
     out->graph = b->exec ? 1u : 0u;

@@ -418,4 +418,97 @@ cudaError_t batch_occupancy(size_t smem, int* per_sm) {
 
 int batch_threads() { return kNT; }
 
+// ---------------------------------------------------------------------------
+// Wide circuits of a batch run as generated stage kernels over all circuits of one
+// structure at once (jit.h, batched mode); these three kernels do the rest of one
+// evaluation for such a group of ncirc circuits of n qubits (states of circuit c at
+// psi + c 2^n, lambda at lam + c 2^n).
+// ---------------------------------------------------------------------------
+
+// lambda_x = h(x) psi_x and the partial sums of E = sum_x h(x) |psi_x|^2, with
+// h(x) = sum_t coeff_t (-1)^{|x & zmask_t|} (circuit c's terms obs[obs_off[c] ..
+// obs_off[c + 1])); block (b, c) covers amplitudes [b chunk, (b + 1) chunk) and writes
+// epart[c * gridDim.x + b] (FP32 per thread over its amplitudes, FP64 above).
+__global__ void __launch_bounds__(256) k_bgs_obs(const float2* __restrict__ psi, float2* __restrict__ lam, int n,
+                                                 const ObsTerm* __restrict__ obs, const uint32_t* __restrict__ obs_off,
+                                                 double* __restrict__ epart) {
+    __shared__ double red[8];
+    const uint32_t c = blockIdx.y, tid = threadIdx.x;
+    const uint64_t amps = 1ull << n;
+    const uint64_t chunk = amps / gridDim.x;
+    const uint64_t x0 = (uint64_t)blockIdx.x * chunk;
+    const float2* ps = psi + ((uint64_t)c << n);
+    float2* ls = lam + ((uint64_t)c << n);
+    const uint32_t t0 = obs_off[c], t1 = obs_off[c + 1];
+    float e = 0.f;
+    for (uint64_t x = x0 + tid; x < x0 + chunk; x += blockDim.x) {
+        float h = 0.f;
+        for (uint32_t t = t0; t < t1; ++t) {
+            const float cf = (float)obs[t].coeff;
+            h += (__popcll(x & obs[t].zmask) & 1) ? -cf : cf;
+        }
+        const float2 v = ps[x];
+        ls[x] = make_float2(h * v.x, h * v.y);
+        e = fmaf(h, fmaf(v.x, v.x, v.y * v.y), e);
+    }
+    double d = (double)e;
+    for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
+    if ((tid & 31) == 0) red[tid >> 5] = d;
+    __syncthreads();
+    if (tid == 0) {
+        double sum = 0.0;
+        for (uint32_t w = 0; w < (blockDim.x + 31) / 32; ++w) sum += red[w];
+        epart[(uint64_t)c * gridDim.x + blockIdx.x] = sum;
+    }
+}
+
+// slotsum[c * nst + slot_off + s] = sum over tiles t of partial[(c * ntiles + t) * nsl + s]
+// (one block per circuit, one thread per slot, tiles in order)
+__global__ void k_bgs_slotsum(const double* __restrict__ partial, uint32_t ntiles, uint32_t nsl, uint32_t slot_off,
+                              uint32_t nst, double* __restrict__ slotsum) {
+    const uint32_t c = blockIdx.x;
+    for (uint32_t sl = threadIdx.x; sl < nsl; sl += blockDim.x) {
+        double x = 0.0;
+        for (uint32_t t = 0; t < ntiles; ++t) x += partial[((uint64_t)c * ntiles + t) * nsl + sl];
+        slotsum[(uint64_t)c * nst + slot_off + sl] = x;
+    }
+}
+
+// E and the gradient of circuit c: expval[outidx[c]] = sum of its nblk E partials;
+// grad[pofs[c] + p] = sum of its slot sums over the slots of parameter p
+// (slots plist[pidx[p] .. pidx[p + 1]))
+__global__ void k_bgs_finish(const double* __restrict__ epart, uint32_t nblk, const double* __restrict__ slotsum,
+                             uint32_t nst, const uint32_t* __restrict__ pidx, const uint32_t* __restrict__ plist,
+                             uint32_t np, const uint32_t* __restrict__ pofs, const uint32_t* __restrict__ outidx,
+                             double* __restrict__ expval, double* __restrict__ grad) {
+    const uint32_t c = blockIdx.x;
+    if (threadIdx.x == 0) {
+        double e = 0.0;
+        for (uint32_t b = 0; b < nblk; ++b) e += epart[(uint64_t)c * nblk + b];
+        expval[outidx[c]] = e;
+    }
+    for (uint32_t p = threadIdx.x; p < np; p += blockDim.x) {
+        double g = 0.0;
+        for (uint32_t k = pidx[p]; k < pidx[p + 1]; ++k) g += slotsum[(uint64_t)c * nst + plist[k]];
+        grad[pofs[c] + p] = g;
+    }
+}
+
+cudaError_t launch_bgs_obs(const void* psi, void* lam, int n, uint32_t ncirc, const ObsTerm* obs,
+                           const uint32_t* obs_off, double* epart, uint32_t nblk, cudaStream_t s) {
+    k_bgs_obs<<<dim3(nblk, ncirc), 256, 0, s>>>((const float2*)psi, (float2*)lam, n, obs, obs_off, epart);
+    return cudaGetLastError();
+}
+cudaError_t launch_bgs_slotsum(const double* partial, uint32_t ncirc, uint32_t ntiles, uint32_t nsl, uint32_t slot_off,
+                               uint32_t nst, double* slotsum, cudaStream_t s) {
+    k_bgs_slotsum<<<ncirc, 64, 0, s>>>(partial, ntiles, nsl, slot_off, nst, slotsum);
+    return cudaGetLastError();
+}
+cudaError_t launch_bgs_finish(const double* epart, uint32_t nblk, const double* slotsum, uint32_t nst,
+                              const uint32_t* pidx, const uint32_t* plist, uint32_t np, const uint32_t* pofs,
+                              const uint32_t* outidx, uint32_t ncirc, double* expval, double* grad, cudaStream_t s) {
+    k_bgs_finish<<<ncirc, 128, 0, s>>>(epart, nblk, slotsum, nst, pidx, plist, np, pofs, outidx, expval, grad);
+    return cudaGetLastError();
+}
+
 }  // namespace svk

@@ -45,8 +45,10 @@ struct Kernel {
 namespace {
 
 // argument block layout (generated struct Args): m0 @0, m1 @128 (CUtensorMap, 64-byte
-// aligned), v0 @256, v1 @264, partial @272, flag @280, q[] @288
-constexpr size_t kArgV0 = 256, kArgV1 = 264, kArgPartial = 272, kArgFlag = 280, kArgQ = 288;
+// aligned), v0 @256, v1 @264, partial @272, flag @280, params @288, pofs @296,
+// ncirc @304, q[] @312
+constexpr size_t kArgV0 = 256, kArgV1 = 264, kArgPartial = 272, kArgFlag = 280, kArgParams = 288, kArgPofs = 296,
+                 kArgNcirc = 304, kArgQ = 312;
 
 std::mutex g_mu;
 std::unordered_map<std::string, Kernel*> g_cache;   // source -> kernel (never freed: process lifetime)
@@ -142,6 +144,9 @@ class Gen {
     int NS = 2;               // TMA ring slots
     uint32_t swz(uint32_t e) const { return tma ? (e ^ (((e >> 4) & 7u) << 1)) : svk::swizzle8(e); }
     std::vector<std::vector<int>> tbo;   // per group: tile bit of each thread bit
+    int BM = 0, ZI = 0;       // batched over circuits; first stage starts from |0...0>
+    struct Bind { int fi, type, kind, param; };
+    std::vector<Bind> binds;  // batched: bound ops whose constants the kernel forms per circuit
     std::vector<int> slot_thr;   // per phase slot: first u[] index of its J[i] (or -1)
     int perm[32];             // logical register index -> variable holding it
     std::string fixvar;       // name of the current group's fixed-index variable ("" = none)
@@ -257,6 +262,7 @@ std::string Gen::dense(const svk::DevOp<float>& o, int gi) {
         }
     } else if (o.type == svk::OP_UR) {
         const int m0 = A.F(o.m[0]), m2 = A.F(o.m[2]), m4 = A.F(o.m[4]), m6 = A.F(o.m[6]);
+        if (o.flags & svk::F_BIND) binds.push_back({m0, svk::OP_UR, o.u, (int)o.term_off});
         for (int k = 0; k < K; ++k)
             if (selected(k))
                 for (int v = 0; v < NV; ++v)
@@ -265,6 +271,7 @@ std::string Gen::dense(const svk::DevOp<float>& o, int gi) {
     } else {   // OP_U
         int m[8];
         for (int i = 0; i < 8; ++i) m[i] = A.F(o.m[i]);
+        if (o.flags & svk::F_BIND) binds.push_back({m[0], svk::OP_U, o.u, (int)o.term_off});
         for (int k = 0; k < K; ++k)
             if (selected(k))
                 for (int v = 0; v < NV; ++v)
@@ -417,8 +424,11 @@ std::string Gen::run() {
     const int n = V.n, NG = n - T;
     if (R < 1 || R > 5 || TR < 0 || TR > 9 || T > svk::kMaxT) return "jit: unsupported tile shape";
     if (st.tile_pos[0] != 0) return "jit: the tile must hold physical bit 0";
-    for (uint32_t i = 0; i < st.n_ops; ++i)
-        if (V.ops[i].flags & svk::F_BIND) return "jit: bound (device-formed) ops are not generated";
+    BM = V.batched;
+    ZI = V.zero_init;
+    if (!BM)
+        for (uint32_t i = 0; i < st.n_ops; ++i)
+            if (V.ops[i].flags & svk::F_BIND) return "jit: bound (device-formed) ops need a batched stage";
     const size_t tile_b = (size_t)8 << T;
     // double-buffer the tiles when that still leaves the target residency
     // resident threads per SM the register budget is sized for (64 registers per thread
@@ -438,13 +448,17 @@ std::string Gen::run() {
     if (const char* e = getenv("SVGB_JIT_CBANK_OPS")) cbank_ops = atoi(e);
     cbank = NV == 1 && (int)st.n_ops <= cbank_ops;
     if (const char* e = getenv("SVGB_JIT_CBANK")) cbank = atoi(e) != 0;
+    if (BM) {   // the per-circuit constants are written into the shared-memory copy
+        cbank = false;
+        NB = 1;
+    }
 
     // ---- TMA eligibility: the tile holds physical bits 0..3, the tile is at least 1 KiB
     // (the 128-byte swizzle repeats every 1 KiB), and the runs of local / global physical
     // bits (local runs cut into pieces of at most 8 bits, the first piece exactly bits 0..3)
     // form at most 5 dimensions ----
     std::vector<Run> dims;
-    tma = tma_runs(st, n, NV, &dims);
+    tma = !V.batched && tma_runs(st, n, NV, &dims);
     if (const char* e = getenv("SVGB_JIT_NS")) NS = std::max(2, std::min(4, atoi(e)));
     if (tma) {   // coordinates of a tile along each dimension: (tile index >> shift) & mask
         B->tma = true;
@@ -553,7 +567,8 @@ std::string Gen::run() {
     std::string pre;
     pre += fmt("const u32 tid = threadIdx.x;\n");
     pre += fmt("const u64 ntiles = 1ull << %d;\n", NG);
-    pre += "u64 t = blockIdx.x;\nif (t >= ntiles) return;\n";
+    if (!BM) pre += "u64 t = blockIdx.x;\nif (t >= ntiles) return;\n";
+    else pre += "u64 t = 0;\n";
     pre += "u64 base = 0, pstep = 0, gmask = 0;\n";
     if (NG > 0)
         pre += fmt("#pragma unroll 1\nfor (int i = 0; i < %d; ++i) {\nconst u64 b = a.q[%d + i];\ngmask |= b;\n"
@@ -679,6 +694,54 @@ std::string Gen::run() {
                          NB, buf, T, chs[i], v, bexpr, chp[i].c_str());
         return r + "svj_cp_commit();\n";
     };
+    // the register groups (also collects the bound ops of a batched stage)
+    std::string gcode;
+    for (int g = 0; g < ng; ++g) {
+        const svk::Group& G = V.groups[g];
+        const int K = 1 << R;
+        for (int k = 0; k < K; ++k) perm[k] = k;
+        std::vector<uint32_t> sr(K);
+        for (int k = 0; k < K; ++k) {
+            uint32_t x = 0;
+            for (int j = 0; j < R; ++j)
+                if ((k >> j) & 1) x ^= swz(1u << G.reg_pos[j]);
+            sr[k] = x;
+        }
+        const bool pairs = G.reg_pos[0] == 0;
+        gcode += fmt("{ // group %d\n", g);
+        if (gtab) gcode += fmt("const u32 so%d = gso[%d * %d + tid];\n", g, g, NT);
+        fixvar = "";
+        if (needfix[g]) {
+            if (gtab) gcode += fmt("const u64 fix = base ^ gpf[%d * %d + tid];\n", fixrow[g], NT);
+            else gcode += fmt("const u64 fix = base ^ pf%d;\n", g);
+            fixvar = "fix";
+        }
+        for (int v = 0; v < NV; ++v) {
+            for (int k = 0; k < K; ++k) gcode += fmt("float2 %c%d;\n", v ? 'l' : 'p', k);
+            if (pairs) {
+                for (int k = 0; k < K; k += 2)
+                    gcode += fmt("{ const float4 q = *reinterpret_cast<const float4*>(T%d + (so%d ^ %uu)); %c%d = make_float2(q.x, q.y); %c%d = make_float2(q.z, q.w); }\n",
+                                v, g, sr[k], v ? 'l' : 'p', k, v ? 'l' : 'p', k + 1);
+            } else {
+                for (int k = 0; k < K; ++k) gcode += fmt("%c%d = T%d[so%d ^ %uu];\n", v ? 'l' : 'p', k, v, g, sr[k]);
+            }
+        }
+        pend.clear();
+        zgen = -1;
+        for (uint32_t oi = 0; oi < G.n_ops; ++oi) gcode += op(V.ops[G.op_off + oi], g);
+        gcode += reduce_pending();
+        for (int v = 0; v < NV; ++v) {
+            if (pairs) {
+                for (int k = 0; k < K; k += 2)
+                    gcode += fmt("*reinterpret_cast<float4*>(T%d + (so%d ^ %uu)) = make_float4(%s.x, %s.y, %s.x, %s.y);\n", v, g,
+                                sr[k], amp(v, k).c_str(), amp(v, k).c_str(), amp(v, k + 1).c_str(), amp(v, k + 1).c_str());
+            } else {
+                for (int k = 0; k < K; ++k) gcode += fmt("T%d[so%d ^ %uu] = %s;\n", v, g, sr[k], amp(v, k).c_str());
+            }
+        }
+        // the last group's writes become visible to the tile's TMA store
+        gcode += (tma && g == ng - 1) ? "}\nsvj_fence_async_smem();\n__syncthreads();\n" : "}\n__syncthreads();\n";
+    }
     std::string body;
     // TMA: a tile is one box of the 5-D view; its coordinates come from the tile index
     auto crd = [&](const char* tt) {
@@ -692,110 +755,130 @@ std::string Gen::run() {
             r += fmt("svj_tma_load(tl + ((%s * %d + %d) << %d), &a.m%d, %s, &bars[%s]);\n", slot, NV, v, T, v, crd(tt).c_str(), slot);
         return r;
     };
-    if (tma) {
-        body += "if (tid == 0) {\n";
-        for (int sl = 0; sl < NS; ++sl)
-            body += fmt("if (t + %du * (u64)gridDim.x < ntiles) {\nconst u64 tt = t + %du * (u64)gridDim.x;\n", sl, sl) +
-                    tma_load(std::to_string(sl).c_str(), "tt") + "}\n";
-        body += "}\n";
-    } else {
-        body += load("0", "base");
-    }
-    if (tma) body += "u32 brk = 0xffffffffu;   // iteration whose tile wait gave up\n";
-    body += "#pragma unroll 1\nfor (u32 it = 0; t < ntiles; t += gridDim.x, ++it) {\n";
-    body += "const u64 bn = ((base | ~gmask) + pstep) & gmask;\n";
-    if (tma) {
-        body += fmt("const u32 cb = it %% %du;\n", NS);
-        body += fmt("if (!__syncthreads_and(svj_mbar_wait(&bars[cb], (it / %du) & 1u, a.flag))) {\nbrk = it;\nbreak;\n}\n", NS);
-    } else if (NB == 2) {
-        body += "const u32 cb = it & 1u;\n";
-        body += "if (t + gridDim.x < ntiles) {\n" + load("cb ^ 1u", "bn") + "svj_cp_wait1();\n} else {\nsvj_cp_wait0();\n}\n";
-    } else {
-        body += "const u32 cb = 0u;\n";
-        body += "if (it > 0) {\n" + load("0", "base") + "}\nsvj_cp_wait0();\n";
-    }
-    if (NPH) {   // per-tile slot angles: the constant plus the global-bit terms set in this tile
-        body += fmt("#pragma unroll 1\nfor (u32 p = tid; p < %du; p += %du) {\nu32 x = S.u[%d + 3 * p];\nconst u32 ng = S.u[%d + 3 * p + 1], q0 = S.u[%d + 3 * p + 2];\n",
-                    NPH, NT, slot_u, slot_u, slot_u);
-        body += fmt("#pragma unroll 1\nfor (u32 i = 0; i < ng; ++i)\nif (base & S.q[q0 + i]) x += S.u[%d + (q0 - %d) + i];\nsang[p] = x;\n}\n",
-                    slot_ang_u, slot_q0);
-    }
-    body += "__syncthreads();\n";
-    for (int v = 0; v < NV; ++v) {
-        if (tma) body += fmt("float2* const T%d = tl + ((cb * %d + %d) << %d);\n", v, NV, v, T);
-        else body += fmt("float2* const T%d = tl + ((%d * %d + cb) << %d);\n", v, v, NB, T);
-    }
-    for (int g = 0; g < ng; ++g) {
-        const svk::Group& G = V.groups[g];
-        const int K = 1 << R;
-        for (int k = 0; k < K; ++k) perm[k] = k;
-        std::vector<uint32_t> sr(K);
-        for (int k = 0; k < K; ++k) {
-            uint32_t x = 0;
-            for (int j = 0; j < R; ++j)
-                if ((k >> j) & 1) x ^= swz(1u << G.reg_pos[j]);
-            sr[k] = x;
+    if (BM) {
+        // ---- batched: work items w = (circuit << NG) | tile, a contiguous range per CTA;
+        // a new circuit rebinds the parametric matrices and restarts the tile walk ----
+        const int bt = (int)A.u.size();
+        for (const Bind& b : binds) {
+            A.U((uint32_t)b.fi);
+            A.U((uint32_t)((b.type << 8) | b.kind));
+            A.U((uint32_t)b.param);
         }
-        const bool pairs = G.reg_pos[0] == 0;
-        body += fmt("{ // group %d\n", g);
-        if (gtab) body += fmt("const u32 so%d = gso[%d * %d + tid];\n", g, g, NT);
-        fixvar = "";
-        if (needfix[g]) {
-            if (gtab) body += fmt("const u64 fix = base ^ gpf[%d * %d + tid];\n", fixrow[g], NT);
-            else body += fmt("const u64 fix = base ^ pf%d;\n", g);
-            fixvar = "fix";
+        const int nbind = (int)binds.size();
+        body += fmt("Args& Sw = *reinterpret_cast<Args*>(smem + %zu);\n", o_args);
+        body += fmt("const u64 W = a.ncirc << %d;\n", NG);
+        body += "const u64 w0 = (W * blockIdx.x) / gridDim.x, w1 = (W * ((u64)blockIdx.x + 1)) / gridDim.x;\n";
+        body += "u32 cc = 0xffffffffu;\nu64 tfirst = 0;\n";
+        auto flush = [&]() {
+            if (!NSL) return std::string();
+            return fmt("if (cc != 0xffffffffu)\nfor (u32 sl = tid; sl < %du; sl += %du) {\ndouble x = 0.0;\n"
+                       "for (int wv = 0; wv < %d; ++wv) {\nx += gsm[sl * %d + wv];\ngsm[sl * %d + wv] = 0.0;\n}\n"
+                       "a.partial[(((u64)cc << %d) | tfirst) * %d + sl] = x;\n}\n", NSL, NT, NW, NW, NW, NG, NSL);
+        };
+        body += "#pragma unroll 1\nfor (u64 w = w0; w < w1; ++w) {\n";
+        body += fmt("const u32 c = (u32)(w >> %d);\nconst u64 tt = w & (ntiles - 1ull);\n", NG);
+        body += "if (c != cc) {\n" + flush() + "cc = c;\ntfirst = tt;\n__syncthreads();\n";
+        if (nbind) {
+            body += fmt("{\nconst double* pp = a.params + a.pofs[c];\n#pragma unroll 1\nfor (u32 i = tid; i < %du; i += %du) {\n"
+                        "const u32 fi = Sw.u[%d + 3 * i], kd = Sw.u[%d + 3 * i + 1], pi = Sw.u[%d + 3 * i + 2];\n"
+                        "double sd, cd;\nsincos(0.5 * pp[pi], &sd, &cd);\n"
+                        "const float cs = (float)cd, sn = (kd & 4u) ? -(float)sd : (float)sd;\nfloat* f = Sw.f + fi;\n"
+                        "if ((kd >> 8) == %du) {\nf[0] = cs; f[1] = -sn; f[2] = sn; f[3] = cs;\n} else {\n"
+                        "f[0] = cs; f[1] = 0.f; f[2] = 0.f; f[3] = 0.f; f[4] = 0.f; f[5] = 0.f; f[6] = cs; f[7] = 0.f;\n"
+                        "const u32 k = kd & 3u;\nif (k == 1u) { f[3] = -sn; f[5] = -sn; }\n"
+                        "else if (k == 2u) { f[2] = -sn; f[4] = sn; }\nelse { f[1] = -sn; f[7] = sn; }\n}\n}\n}\n",
+                        nbind, NT, bt, bt, bt, (unsigned)svk::OP_UR);
         }
-        for (int v = 0; v < NV; ++v) {
-            for (int k = 0; k < K; ++k) body += fmt("float2 %c%d;\n", v ? 'l' : 'p', k);
-            if (pairs) {
-                for (int k = 0; k < K; k += 2)
-                    body += fmt("{ const float4 q = *reinterpret_cast<const float4*>(T%d + (so%d ^ %uu)); %c%d = make_float2(q.x, q.y); %c%d = make_float2(q.z, q.w); }\n",
-                                v, g, sr[k], v ? 'l' : 'p', k, v ? 'l' : 'p', k + 1);
-            } else {
-                for (int k = 0; k < K; ++k) body += fmt("%c%d = T%d[so%d ^ %uu];\n", v ? 'l' : 'p', k, v, g, sr[k]);
-            }
+        body += fmt("base = 0;\n#pragma unroll 1\nfor (int i = 0; i < %d; ++i)\nif ((tt >> i) & 1ull) base |= a.q[%d + i];\n", NG, QG);
+        body += "__syncthreads();\n}\n";
+        for (int v = 0; v < NV; ++v) body += fmt("float2* const g%d = a.v%d + ((u64)c << %d);\n", v, v, n);
+        if (ZI) {   // |0...0> restricted to this tile: element 0 (storage 0) of the tile with base 0
+            for (int i = 0; i < NCH; ++i)
+                body += fmt("*reinterpret_cast<float4*>(tl + (stid ^ %uu)) = make_float4((base == 0ull && tid == 0u && %d == 0) ? 1.f : 0.f, 0.f, 0.f, 0.f);\n",
+                            chs[i], i);
+        } else {
+            for (int i = 0; i < NCH; ++i)
+                for (int v = 0; v < NV; ++v)
+                    body += fmt("svj_cp_async16(tl + ((%d << %d) + (stid ^ %uu)), g%d + (base | ptid | %s));\n", v, T, chs[i], v,
+                                chp[i].c_str());
+            body += "svj_cp_commit();\nsvj_cp_wait0();\n";
         }
-        pend.clear();
-        zgen = -1;
-        for (uint32_t oi = 0; oi < G.n_ops; ++oi) body += op(V.ops[G.op_off + oi], g);
-        body += reduce_pending();
-        for (int v = 0; v < NV; ++v) {
-            if (pairs) {
-                for (int k = 0; k < K; k += 2)
-                    body += fmt("*reinterpret_cast<float4*>(T%d + (so%d ^ %uu)) = make_float4(%s.x, %s.y, %s.x, %s.y);\n", v, g,
-                                sr[k], amp(v, k).c_str(), amp(v, k).c_str(), amp(v, k + 1).c_str(), amp(v, k + 1).c_str());
-            } else {
-                for (int k = 0; k < K; ++k) body += fmt("T%d[so%d ^ %uu] = %s;\n", v, g, sr[k], amp(v, k).c_str());
-            }
+        if (NPH) {
+            body += fmt("#pragma unroll 1\nfor (u32 p = tid; p < %du; p += %du) {\nu32 x = S.u[%d + 3 * p];\nconst u32 ng = S.u[%d + 3 * p + 1], q0 = S.u[%d + 3 * p + 2];\n",
+                        NPH, NT, slot_u, slot_u, slot_u);
+            body += fmt("#pragma unroll 1\nfor (u32 i = 0; i < ng; ++i)\nif (base & S.q[q0 + i]) x += S.u[%d + (q0 - %d) + i];\nsang[p] = x;\n}\n",
+                        slot_ang_u, slot_q0);
         }
-        // the last group's writes become visible to the tile's TMA store
-        body += (tma && g == ng - 1) ? "}\nsvj_fence_async_smem();\n__syncthreads();\n" : "}\n__syncthreads();\n";
-    }
-    if (tma) {
-        // one thread stores the tile (bulk tensor copy) and refills the slot with the tile
-        // NS steps ahead once the store has read it
-        body += "if (tid == 0) {\n";
-        for (int v = 0; v < NV; ++v) body += fmt("svj_tma_store(&a.m%d, %s, T%d);\n", v, crd("t").c_str(), v);
-        body += "svj_bulk_commit();\n";
-        body += fmt("const u64 tn = t + %du * (u64)gridDim.x;\nif (tn < ntiles) {\nsvj_bulk_wait_read0();\n", NS) +
-                tma_load("cb", "tn") + "}\n}\n";
-        body += "base = bn;\n}\n";
-        // a wait that gave up leaves loads in flight: wait for them (bounded) before the
-        // CTA's shared memory goes away; then for the tile stores
-        body += fmt("if (tid == 0) {\nif (brk != 0xffffffffu)\nfor (u32 k = 0; k < %du; ++k) {\nconst u32 i2 = brk + k;\n"
-                    "if ((u64)blockIdx.x + (u64)i2 * gridDim.x < ntiles) svj_mbar_wait(&bars[i2 %% %du], (i2 / %du) & 1u, nullptr);\n}\n"
-                    "svj_bulk_wait0();\n}\n", NS, NS, NS);
-    } else {
-        // write the tile back in place
+        body += "__syncthreads();\n";
+        for (int v = 0; v < NV; ++v) body += fmt("float2* const T%d = tl + (%d << %d);\n", v, v, T);
+        body += gcode;
         for (int i = 0; i < NCH; ++i)
             for (int v = 0; v < NV; ++v)
-                body += fmt("*reinterpret_cast<float4*>(a.v%d + (base | ptid | %s)) = *reinterpret_cast<const float4*>(T%d + (stid ^ %uu));\n",
+                body += fmt("*reinterpret_cast<float4*>(g%d + (base | ptid | %s)) = *reinterpret_cast<const float4*>(T%d + (stid ^ %uu));\n",
                             v, chp[i].c_str(), v, chs[i]);
-        body += "base = bn;\n__syncthreads();\n}\n";
+        body += fmt("base = ((base | ~gmask) + a.q[%d]) & gmask;\n__syncthreads();\n}\n", QG);
+        body += flush();
+    } else {
+        if (tma) {
+            body += "if (tid == 0) {\n";
+            for (int sl = 0; sl < NS; ++sl)
+                body += fmt("if (t + %du * (u64)gridDim.x < ntiles) {\nconst u64 tt = t + %du * (u64)gridDim.x;\n", sl, sl) +
+                        tma_load(std::to_string(sl).c_str(), "tt") + "}\n";
+            body += "}\n";
+        } else {
+            body += load("0", "base");
+        }
+        if (tma) body += "u32 brk = 0xffffffffu;   // iteration whose tile wait gave up\n";
+        body += "#pragma unroll 1\nfor (u32 it = 0; t < ntiles; t += gridDim.x, ++it) {\n";
+        body += "const u64 bn = ((base | ~gmask) + pstep) & gmask;\n";
+        if (tma) {
+            body += fmt("const u32 cb = it %% %du;\n", NS);
+            body += fmt("if (!__syncthreads_and(svj_mbar_wait(&bars[cb], (it / %du) & 1u, a.flag))) {\nbrk = it;\nbreak;\n}\n", NS);
+        } else if (NB == 2) {
+            body += "const u32 cb = it & 1u;\n";
+            body += "if (t + gridDim.x < ntiles) {\n" + load("cb ^ 1u", "bn") + "svj_cp_wait1();\n} else {\nsvj_cp_wait0();\n}\n";
+        } else {
+            body += "const u32 cb = 0u;\n";
+            body += "if (it > 0) {\n" + load("0", "base") + "}\nsvj_cp_wait0();\n";
+        }
+        if (NPH) {   // per-tile slot angles: the constant plus the global-bit terms set in this tile
+            body += fmt("#pragma unroll 1\nfor (u32 p = tid; p < %du; p += %du) {\nu32 x = S.u[%d + 3 * p];\nconst u32 ng = S.u[%d + 3 * p + 1], q0 = S.u[%d + 3 * p + 2];\n",
+                        NPH, NT, slot_u, slot_u, slot_u);
+            body += fmt("#pragma unroll 1\nfor (u32 i = 0; i < ng; ++i)\nif (base & S.q[q0 + i]) x += S.u[%d + (q0 - %d) + i];\nsang[p] = x;\n}\n",
+                        slot_ang_u, slot_q0);
+        }
+        body += "__syncthreads();\n";
+        for (int v = 0; v < NV; ++v) {
+            if (tma) body += fmt("float2* const T%d = tl + ((cb * %d + %d) << %d);\n", v, NV, v, T);
+            else body += fmt("float2* const T%d = tl + ((%d * %d + cb) << %d);\n", v, v, NB, T);
+        }
+        body += gcode;
+        if (tma) {
+            // one thread stores the tile (bulk tensor copy) and refills the slot with the tile
+            // NS steps ahead once the store has read it
+            body += "if (tid == 0) {\n";
+            for (int v = 0; v < NV; ++v) body += fmt("svj_tma_store(&a.m%d, %s, T%d);\n", v, crd("t").c_str(), v);
+            body += "svj_bulk_commit();\n";
+            body += fmt("const u64 tn = t + %du * (u64)gridDim.x;\nif (tn < ntiles) {\nsvj_bulk_wait_read0();\n", NS) +
+                    tma_load("cb", "tn") + "}\n}\n";
+            body += "base = bn;\n}\n";
+            // a wait that gave up leaves loads in flight: wait for them (bounded) before the
+            // CTA's shared memory goes away; then for the tile stores
+            body += fmt("if (tid == 0) {\nif (brk != 0xffffffffu)\nfor (u32 k = 0; k < %du; ++k) {\nconst u32 i2 = brk + k;\n"
+                        "if ((u64)blockIdx.x + (u64)i2 * gridDim.x < ntiles) svj_mbar_wait(&bars[i2 %% %du], (i2 / %du) & 1u, nullptr);\n}\n"
+                        "svj_bulk_wait0();\n}\n", NS, NS, NS);
+        } else {
+            // write the tile back in place
+            for (int i = 0; i < NCH; ++i)
+                for (int v = 0; v < NV; ++v)
+                    body += fmt("*reinterpret_cast<float4*>(a.v%d + (base | ptid | %s)) = *reinterpret_cast<const float4*>(T%d + (stid ^ %uu));\n",
+                                v, chp[i].c_str(), v, chs[i]);
+            body += "base = bn;\n__syncthreads();\n}\n";
+        }
+        if (NSL)
+            body += fmt("for (u32 sl = tid; sl < %du; sl += %du) {\ndouble x = 0.0;\nfor (int w = 0; w < %d; ++w) x += gsm[sl * %d + w];\n"
+                        "a.partial[(u64)blockIdx.x * %d + sl] = x;\n}\n", NSL, NT, NW, NW, NSL);
     }
-    if (NSL)
-        body += fmt("for (u32 sl = tid; sl < %du; sl += %du) {\ndouble x = 0.0;\nfor (int w = 0; w < %d; ++w) x += gsm[sl * %d + w];\n"
-                    "a.partial[(u64)blockIdx.x * %d + sl] = x;\n}\n", NSL, NT, NW, NW, NSL);
 
     // ---- assemble ----
     const int nq = std::max<int>(1, (int)A.q.size()), nu = std::max<int>(1, (int)A.u.size()),
@@ -804,7 +887,7 @@ std::string Gen::run() {
     std::string head;
     head += "#include \"jit_prelude.cuh\"\n";
     head += fmt("struct alignas(64) Args {\nSvjTmap m0;\nSvjTmap m1;\nfloat2* v0;\nfloat2* v1;\ndouble* partial;\nint* flag;\n"
-                "u64 q[%d];\nu32 u[%d];\nfloat f[%d];\n};\n", nq, nu, nf);
+                "const double* params;\nconst u32* pofs;\nu64 ncirc;\nu64 q[%d];\nu32 u[%d];\nfloat f[%d];\n};\n", nq, nu, nf);
     std::string src = head + "extern \"C\" __global__ void __launch_bounds__(" + std::to_string(NT) + ", " +
                       std::to_string(minb) + ") KNAME(const __grid_constant__ Args a) {\n"
                       "extern __shared__ __attribute__((aligned(1024))) unsigned char smem[];\n" + pre + body + "}\n";
@@ -845,6 +928,7 @@ std::string structure_key(const StageView& v) {
     const svk::Stage& st = *v.st;
     put((uint64_t)v.nv);
     put((uint64_t)v.n);
+    put((uint64_t)v.batched << 1 | (uint64_t)v.zero_init);
     put(st.T);
     put(st.R);
     put(st.n_groups);
@@ -1045,8 +1129,9 @@ static cudaError_t encode_map(const Built& b, void* ptr, void* out) {
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t launch(const Built& b, void* v0, void* v1, double* partial, int* flag, cudaStream_t s,
-                   uint32_t* grid_out) {
+// load the kernel's library on first use and (re)size its launch attributes for the
+// current device; returns the resident CTAs per SM in *per_sm
+static cudaError_t ready(const Built& b, int* per_sm) {
     Kernel* k = b.kernel;
     if (!k || !k->err.empty() || k->cubin.empty()) return cudaErrorInvalidDeviceFunction;
     int dev = 0;
@@ -1070,20 +1155,64 @@ cudaError_t launch(const Built& b, void* v0, void* v1, double* partial, int* fla
         k->dev = dev;
         k->smem_set = b.smem;
     }
+    *per_sm = k->per_sm_dev;
+    return cudaSuccess;
+}
+
+cudaError_t preload(const Built& b) {
+    int per_sm = 0;
+    return ready(b, &per_sm);
+}
+
+static uint8_t* fill_args(const Built& b, void* v0, void* v1, double* partial, int* flag) {
+    alignas(64) static thread_local uint8_t argbuf[32768];
+    if (b.args.size() > sizeof(argbuf)) return nullptr;
+    std::memcpy(argbuf, b.args.data(), b.args.size());
+    std::memcpy(argbuf + kArgV0, &v0, 8);
+    std::memcpy(argbuf + kArgV1, &v1, 8);
+    std::memcpy(argbuf + kArgPartial, &partial, 8);
+    std::memcpy(argbuf + kArgFlag, &flag, 8);
+    return argbuf;
+}
+
+cudaError_t launch_batched(const Built& b, void* v0, void* v1, double* partial, int* flag, const double* params,
+                           const uint32_t* pofs, uint32_t ncirc, cudaStream_t s) {
+    int per_sm = 0;
+    cudaError_t e = ready(b, &per_sm);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t W = (uint64_t)ncirc * b.ntiles;
+    if (W == 0) return cudaSuccess;
+    const uint64_t grid = std::min<uint64_t>(W, (uint64_t)per_sm * (uint64_t)nsm);
+    uint8_t* args = fill_args(b, v0, v1, partial, flag);
+    if (!args) return cudaErrorInvalidValue;
+    const uint64_t nc = ncirc;
+    std::memcpy(args + kArgParams, &params, 8);
+    std::memcpy(args + kArgPofs, &pofs, 8);
+    std::memcpy(args + kArgNcirc, &nc, 8);
+    void* p[1] = {args};
+    return cudaLaunchKernel((const void*)b.kernel->fn, dim3((unsigned)grid), dim3(b.nthr), p, b.smem, s);
+}
+
+cudaError_t launch(const Built& b, void* v0, void* v1, double* partial, int* flag, cudaStream_t s,
+                   uint32_t* grid_out) {
+    int per_sm = 0;
+    cudaError_t e = ready(b, &per_sm);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    Kernel* k = b.kernel;
     int nsm = 0;
     e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    const uint64_t grid = std::min<uint64_t>(b.ntiles, (uint64_t)k->per_sm_dev * (uint64_t)nsm);
+    const uint64_t grid = std::min<uint64_t>(b.ntiles, (uint64_t)per_sm * (uint64_t)nsm);
     if (grid_out) *grid_out = (uint32_t)grid;
     // the argument block, 64-byte aligned (the tensor maps inside must be)
-    alignas(64) static thread_local uint8_t argbuf[32768];
-    if (b.args.size() > sizeof(argbuf)) return cudaErrorInvalidValue;
-    uint8_t* args = argbuf;
-    std::memcpy(args, b.args.data(), b.args.size());
-    std::memcpy(args + kArgV0, &v0, 8);
-    std::memcpy(args + kArgV1, &v1, 8);
-    std::memcpy(args + kArgPartial, &partial, 8);
-    std::memcpy(args + kArgFlag, &flag, 8);
+    uint8_t* args = fill_args(b, v0, v1, partial, flag);
+    if (!args) return cudaErrorInvalidValue;
     if (b.tma) {
         e = encode_map(b, v0, args + 0);
         if (e != cudaSuccess) return e;

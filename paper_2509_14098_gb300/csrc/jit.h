@@ -30,6 +30,11 @@ struct StageView {
     const svk::PhaseSlot<float>* slots;  // this stage's phase slots
     int n;                               // state width
     int nv;                              // 1: forward (psi); 2: adjoint (psi and lambda)
+    // batched mode: one launch sweeps the stage of many circuits of the same structure,
+    // circuit c's state at v0 + c 2^n (lambda at v1 + c 2^n); bound ops (F_BIND) take
+    // their angle from params[pofs[c] + index]; gradient partials per circuit segment
+    int batched = 0;
+    int zero_init = 0;                   // batched forward stage 0: tiles start as |0...0>
 };
 
 struct Kernel;
@@ -62,6 +67,15 @@ std::string compile(std::vector<Built*>& kernels);
 // int set to 1 if a bounded wait of the kernel gave up (the caller reports it).
 cudaError_t launch(const Built& b, void* v0, void* v1, double* partial, int* flag, cudaStream_t s,
                    uint32_t* grid_out);
+
+// Batched launch (StageView::batched): ncirc circuits; params / pofs as above.
+// Gradient partials: partial[(c 2^(n-T) + t) * n_slots + s] for the first tile t of each
+// run of tiles a CTA processes for circuit c (other rows untouched: zero them first).
+cudaError_t launch_batched(const Built& b, void* v0, void* v1, double* partial, int* flag, const double* params,
+                           const uint32_t* pofs, uint32_t ncirc, cudaStream_t s);
+
+// Load a compiled kernel and set its launch attributes (before a stream capture).
+cudaError_t preload(const Built& b);
 
 // NVRTC compiles and cache hits since load (diagnostics).
 void stats(uint64_t* compiles, uint64_t* hits, double* compile_ms);

@@ -101,5 +101,15 @@ cudaError_t launch_batch(const BatchArgs& a, int grid, cudaStream_t s);
 // CTAs of the batch kernel that fit on one SM with `smem` bytes of dynamic shared memory
 cudaError_t batch_occupancy(size_t smem, int* per_sm);
 int batch_threads();
+// wide circuits of a batch (batch_kernels.cu): lambda = h psi with E partials; gradient
+// slot sums over tiles; per-circuit E and gradient gather
+struct ObsTerm;
+cudaError_t launch_bgs_obs(const void* psi, void* lam, int n, uint32_t ncirc, const ObsTerm* obs,
+                           const uint32_t* obs_off, double* epart, uint32_t nblk, cudaStream_t s);
+cudaError_t launch_bgs_slotsum(const double* partial, uint32_t ncirc, uint32_t ntiles, uint32_t nsl, uint32_t slot_off,
+                               uint32_t nst, double* slotsum, cudaStream_t s);
+cudaError_t launch_bgs_finish(const double* epart, uint32_t nblk, const double* slotsum, uint32_t nst,
+                              const uint32_t* pidx, const uint32_t* plist, uint32_t np, const uint32_t* pofs,
+                              const uint32_t* outidx, uint32_t ncirc, double* expval, double* grad, cudaStream_t s);
 
 }  // namespace svk

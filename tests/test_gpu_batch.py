@@ -125,7 +125,7 @@ def test_tiled_circuits_vs_plain_path(sv):
     for tune in ({n: (10, 3) for n in range(14, 18)}, {n: (12, 4) for n in range(14, 18)}):
         b = sv.Batch(circs, obs, tune=tune)
         info = b.info()
-        assert info["n_resident"] == 0 and info["workspace_bytes"] > 0
+        assert info["n_resident"] == 0 and info["workspace_bytes"] > 0   # wide groups or HBM-tiled circuits
         e, g = b.run(params)
         off = 0
         for i, (c, p) in enumerate(spec):
@@ -140,6 +140,35 @@ def test_tiled_circuits_vs_plain_path(sv):
     b = sv.Batch([c], [C.zz_chain(c.n_qubits)], tune={c.n_qubits: (10, 3)})
     e, _ = b.run(p)
     assert abs(e[0] - e_ref) <= e_tol(e_ref)
+
+
+def test_wide_groups_vs_oracle(sv):
+    """Circuits of 14 and 15 qubits run as wide groups: every circuit of one structure
+    sweeps each stage together in one generated kernel, each with its own parameters;
+    mixed rotation kinds, fixed gates and SWAP relabels; a small circuit beside them in
+    the persistent kernel.  E against the oracle, gradients against the oracle's
+    parameter shift, on two replays with different parameters."""
+    circs = [mixed_circuit(14, 41), mixed_circuit(14, 41), mixed_circuit(15, 42), mixed_circuit(14, 41),
+             mixed_circuit(9, 43)]
+    obs = [C.Observable(c.n_qubits, [(1.0, "Z" * 2 + "I" * (c.n_qubits - 2)),
+                                      (0.5, "I" * (c.n_qubits - 1) + "Z"),
+                                      (-0.25, "Z" + "I" * (c.n_qubits - 3) + "ZZ")]) for c in circs]
+    b = sv.Batch(circs, obs)
+    info = b.info()
+    assert info["n_programs"] == 3          # two wide structures and the small circuit's
+    rng = np.random.default_rng(8)
+    for rep in range(2):
+        ps = [rng.uniform(-np.pi, np.pi, c.n_params) for c in circs]
+        e, g = b.run(np.concatenate(ps))
+        off = 0
+        for i, c in enumerate(circs):
+            e_ref = O.expval(S.simulate(c, ps[i]), obs[i])
+            assert abs(e[i] - e_ref) <= e_tol(e_ref), (rep, i, e[i], e_ref)
+            if i in (1, 2, 4):
+                g_ref = GR.parameter_shift(c, ps[i], obs[i])
+                assert grad_ok(g[off: off + c.n_params], g_ref), (rep, i)
+            off += c.n_params
+    b.close()
 
 
 def test_replay_and_autotune(sv):
@@ -157,7 +186,9 @@ def test_replay_and_autotune(sv):
     assert np.array_equal(e1, e1b) and np.array_equal(g1, g1b)   # deterministic
     assert not np.allclose(e1, e2)
     table = b.autotune(p1)
-    widths = sorted({c.n_qubits for c in circs})
+    # circuits of 14 or more qubits run as wide groups (tile width 12, register width 4):
+    # only the persistent kernel's widths are tuned
+    widths = sorted({c.n_qubits for c in circs if c.n_qubits < 14})
     assert sorted(table) == widths
     for n, (L, k) in table.items():
         assert 2 <= k <= 4 and (L == n if n <= 13 else 11 <= L <= 13)
