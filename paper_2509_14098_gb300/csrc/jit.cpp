@@ -459,7 +459,7 @@ std::string Gen::run() {
     // form at most 5 dimensions ----
     std::vector<Run> dims;
     tma = !V.batched && tma_runs(st, n, NV, &dims);
-    if (const char* e = getenv("SVGB_JIT_NS")) NS = std::max(2, std::min(4, atoi(e)));
+    if (const char* e = getenv("SVGB_JIT_NS")) NS = std::max(1, std::min(4, atoi(e)));
     if (tma) {   // coordinates of a tile along each dimension: (tile index >> shift) & mask
         B->tma = true;
         int gbits = 0;
