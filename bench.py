@@ -553,15 +553,34 @@ def aux_section(n, reps=3):
     for _ in range(reps):
         st.expval(C.tfim(n))
     ev_ms = (time.perf_counter() - t0) * 1e3 / reps
+    # the QFT alone ends in the bit reversal: its last stage writes through the map
+    qft = C.qft(n)
+    st.run(sv.Plan(qft, L_BUDGET))
+    st.synchronize()
+    st.timing(reset=True)
+    e0.record(st.stream)
+    for _ in range(reps):
+        st.run(sv.Plan(qft, L_BUDGET))
+    e1.record(st.stream)
+    torch.cuda.synchronize()
+    qft_ms = e0.elapsed_time(e1) / reps
+    tq = st.timing(reset=True)
+    qinfo = st.run_info()
     st.timing(False)
     st.close()
     nb = (1 << n) * 8
     perm_ms = tm["permute_ms"] / max(1, tm["permute_launches"])
+    qft_rec = {"what": f"QFT{n} alone (the SWAPs leave the bit reversal; the last stage writes through it "
+                       "out of place, then a copy into the caller's buffer)",
+               "ms": qft_ms, "stage_sweeps": qinfo["stage_sweeps"],
+               "permutation_sweeps": qinfo["permutation_sweeps"],
+               "stage_ms": tq["stage_ms"] / reps}
     return {"n_qubits": n,
             "permutation": {"what": "bit reversal, one out-of-place sweep (kernel time; sv_permute then copies the result back into the caller's buffer)", "ms_per_sweep": perm_ms,
                             "gbs": 2 * nb / (perm_ms * 1e-3) / 1e9, "launches": tm["permute_launches"] / reps},
             "norm": {"what": "||psi||^2 in FP64 (host result)", "ms": norm_ms, "gbs": nb / (norm_ms * 1e-3) / 1e9},
-            "expval_tfim": {"what": "<psi| sum ZZ + 0.7 sum X |psi> (Pauli sweeps, FP64, host result)", "ms": ev_ms}}
+            "expval_tfim": {"what": "<psi| sum ZZ + 0.7 sum X |psi> (Pauli sweeps, FP64, host result)", "ms": ev_ms},
+            "qft_alone": qft_rec}
 
 
 def main_ours(args):
@@ -614,13 +633,21 @@ def main_ours(args):
     partition_ms = (time.perf_counter() - t0) * 1e3
     stages = plan0.stages()
 
-    def step():
+    # ||psi||^2 of each step goes to its own device double (sv_norm_noalloc, enqueued
+    # without a host wait), so the host partitions and lowers step k + 1 while the GPU
+    # still runs step k; every result is read back once the timed steps are done
+    dnorm = torch.zeros(max(1, args.steps), dtype=torch.float64, device=dev)
+    sptr = ctypes.c_void_p(stream.cuda_stream)
+
+    def step(i=0):
         plan = sv.Plan(circ, L)
         st.run(plan)
-        return st.norm()
+        N.check(N.lib.sv_norm_noalloc(ctypes.c_void_p(psi.data_ptr()), n, sv.SV_C64, sptr,
+                                      ctypes.c_void_p(dnorm.data_ptr() + 8 * i)))
 
     for _ in range(args.warmup):
         step()
+    st.synchronize()
     info = st.run_info()
     launches_per_step = info["kernel_launches"] + 2           # + norm and its reduction
     passes = info["stage_sweeps"] + info["permutation_sweeps"]
@@ -639,9 +666,12 @@ def main_ours(args):
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
-    norms = [step() for _ in range(args.steps)]
+    for i in range(args.steps):
+        step(i)
     e1.record(stream)
     torch.cuda.synchronize()
+    st.synchronize()                                  # reports a stage wait that gave up
+    norms = dnorm.cpu().tolist()
     ms_total = e0.elapsed_time(e1)
     tm = st.timing(reset=True)
     st.timing(False)

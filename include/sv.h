@@ -132,7 +132,9 @@ sv_status sv_create(uint32_t n_qubits, sv_dtype dtype, void* dev_state, void* cu
 /* Free the handle and every library-owned buffer (not a borrowed state). */
 sv_status sv_destroy(sv_handle h);
 
-/* Number of qubits, dtype and the device pointer of the state. */
+/* Number of qubits, dtype and the device pointer of the state.  A borrowed buffer
+ * never changes; a library-owned state may move to the handle's second state-sized
+ * buffer after sv_run (see there), so read the pointer again after a run. */
 sv_status sv_info(sv_handle h, uint32_t* n_qubits, sv_dtype* dtype, void** dev_state);
 
 /* Set psi to |0...0>.  Async. */
@@ -276,9 +278,13 @@ sv_status sv_jit_stats(uint64_t* compiles, uint64_t* cache_hits, double* compile
 /* ---------------------------------------------------------------------------
  * Execution
  * ------------------------------------------------------------------------- */
-/* Apply the planned circuit to the handle's state in place: one stage-sweep
- * kernel per partition, then a bit-permutation sweep if the SWAP relabels leave
- * a non-identity qubit map.  params: host array of the circuit's n_params angles
+/* Apply the planned circuit to the handle's state: one stage-sweep kernel per
+ * partition.  If the SWAP relabels leave a non-identity qubit map, the complex64
+ * path writes the last stage's tiles out of place through that map (the data
+ * reshaping of Sec. 4.3 fused into the last stage's write-back; no permutation
+ * sweep) into the handle's second state-sized buffer, which then becomes the state
+ * of a library-owned handle or is copied back into a borrowed one; complex128
+ * stages run in place and then one bit-permutation sweep.  params: host array of the circuit's n_params angles
  * (NULL if n_params == 0).  prec: SV_PREC_CUDACORE, or a tensor-core mode (needs a
  * plan from sv_partition_gemm; one tcgen05 GEMM kernel per partition, then the
  * call synchronises to check the kernels' bounded waits, SV_ERR_TIMEOUT if one gave

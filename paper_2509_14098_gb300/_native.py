@@ -135,17 +135,22 @@ def exported_symbols():
 # ---------------------------------------------------------------------------
 # marshalling helpers
 # ---------------------------------------------------------------------------
+_GATE_DTYPE = np.dtype([("kind", np.uint16), ("nq", np.uint8), ("q", np.uint8, 3), ("reserved", np.uint16),
+                        ("param", np.int32), ("angle", np.float64, 3)], align=True)
+assert _GATE_DTYPE.itemsize == ctypes.sizeof(sv_gate)
+
+
 def gate_array(circuit):
-    arr = (sv_gate * len(circuit.gates))()
-    for i, g in enumerate(circuit.gates):
-        a = arr[i]
-        a.kind = GATE_CODES[g.kind]
-        a.nq = len(g.qubits)
-        for k, q in enumerate(g.qubits):
-            a.q[k] = q
-        a.param = g.param
-        for k, v in enumerate(g.angles):
-            a.angle[k] = v
+    """sv_gate[] of a circuit (filled through one structured numpy array; the ctypes
+    array shares its memory and keeps it alive)."""
+    rows = []
+    for g in circuit.gates:
+        q = tuple(g.qubits) + (0,) * (3 - len(g.qubits))
+        a = tuple(g.angles) + (0.0,) * (3 - len(g.angles))
+        rows.append((GATE_CODES[g.kind], len(g.qubits), q, 0, g.param, a))
+    buf = np.array(rows, dtype=_GATE_DTYPE) if rows else np.zeros(1, dtype=_GATE_DTYPE)
+    arr = (sv_gate * len(buf)).from_buffer(buf)
+    arr._keep = buf
     return arr
 
 

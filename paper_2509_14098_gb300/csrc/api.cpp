@@ -750,8 +750,9 @@ static int rwide_fwd() { return env_int("SVGB_RWIDE_FWD", 0, 0, 5); }
 static std::mutex g_jit_mu;
 static std::unordered_map<std::string, std::shared_ptr<svj::Built>> g_jit_memo;
 
+// dst_last: the last stage writes out of place through this bit map (StageView::dst)
 static sv_status jit_prepare(uint32_t n, const svh::Packed& pk, int nv,
-                             std::vector<std::shared_ptr<svj::Built>>* out) {
+                             std::vector<std::shared_ptr<svj::Built>>* out, const int* dst_last = nullptr) {
     const uint8_t* blob = pk.blob.data();
     const auto* groups = (const svk::Group*)(blob + pk.group_off);
     const auto* ops = (const svk::DevOp<float>*)(blob + pk.op_off);
@@ -762,6 +763,11 @@ static sv_status jit_prepare(uint32_t n, const svh::Packed& pk, int nv,
     for (const svk::Stage& st : pk.stages) {
         svj::StageView v{&st, groups + st.group_off, ops + st.op_off, terms, slots + st.phase_off, (int)n, nv};
         std::string key;
+        if (dst_last && &st == &pk.stages.back()) {
+            v.dst = dst_last;
+            key.append("P");
+            key.append((const char*)dst_last, n * sizeof(int));
+        }
         key.append((const char*)&nv, sizeof(nv));
         key.append((const char*)&n, sizeof(n));
         key.append((const char*)&st, sizeof(st));
@@ -804,7 +810,9 @@ static sv_status run_forward(sv_handle h, const sv_plan* plan, const double* par
     const svh::Plan& P = plan->plan;
     svh::Program prog;
     const bool jit = jit_enabled(h);
-    std::string err = svh::lower(P, params, h->eb, rmax_fwd(h->eb), false, &prog, false, jit ? rwide_fwd() : 0);
+    // generated kernels fuse the final permutation into the last stage's write-back
+    const bool fuse = jit && permute_back && env_int("SVGB_FUSE_PERM", 1, 0, 1) == 1;
+    std::string err = svh::lower(P, params, h->eb, rmax_fwd(h->eb), false, &prog, false, jit ? rwide_fwd() : 0, fuse);
     if (!err.empty()) return fail(SV_ERR_ARG, err);
     for (auto& st : prog.stages)
         if (((size_t)h->eb << st.T) > 227 * 1024) return fail(SV_ERR_UNSUPPORTED, "tile too wide for shared memory at this dtype (use L <= 13 for complex128)");
@@ -814,8 +822,10 @@ static sv_status run_forward(sv_handle h, const sv_plan* plan, const double* par
     if (jit) {
         err = svh::pack(prog, (int)h->n, h->eb, &h->fwd.packed);
         if (!err.empty()) return fail(SV_ERR_ARG, err);
-        s = jit_prepare(h->n, h->fwd.packed, 1, &built);
+        s = jit_prepare(h->n, h->fwd.packed, 1, &built, prog.fused_perm ? prog.dst.data() : nullptr);
         if (!s) s = jflag_device(h, &flag);
+        if (!s && prog.fused_perm && cudaSuccess != h->scratch.ensure(state_bytes(h)))
+            return fail(SV_ERR_CUDA, "could not allocate the permuted stage's output buffer");
     } else {
         s = upload_program(h, prog, &h->fwd, false);
     }
@@ -823,8 +833,9 @@ static sv_status run_forward(sv_handle h, const sv_plan* plan, const double* par
     const auto& stages = h->fwd.packed.stages;
     for (size_t i = 0; i < stages.size(); ++i) {
         cudaEvent_t t0 = tick(h);
+        const bool outp = jit && prog.fused_perm && i + 1 == stages.size();
         if (jit)
-            SV_CUDA(svj::launch(*built[i], h->psi, nullptr, nullptr, flag, h->stream, nullptr));
+            SV_CUDA(svj::launch(*built[i], h->psi, outp ? h->scratch.p : nullptr, nullptr, flag, h->stream, nullptr));
         else
             SV_CUDA(svk::launch_stage_fwd(h->eb, h->fwd.launch(i, h->psi, nullptr, nullptr), stages[i], h->stream));
         tock(h, t0, TK_STAGE);
@@ -832,7 +843,16 @@ static sv_status run_forward(sv_handle h, const sv_plan* plan, const double* par
         h->info.kernel_launches += 1;
         h->info.hbm_bytes += 2.0 * (double)state_bytes(h);
     }
-    if (permute_back && !prog.identity_map) {
+    if (prog.fused_perm) {
+        // the permuted state is in the second buffer: a handle that owns its state takes
+        // that buffer as the state, a caller's buffer receives a copy
+        if (h->owns) {
+            std::swap(h->psi, h->scratch.p);
+        } else {
+            SV_CUDA(cudaMemcpyAsync(h->psi, h->scratch.p, state_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
+            h->info.hbm_bytes += 2.0 * (double)state_bytes(h);
+        }
+    } else if (permute_back && !prog.identity_map) {
         std::vector<uint32_t> m(P.n);
         for (int q = 0; q < P.n; ++q) m[q] = (uint32_t)P.final_map[q];
         s = do_permute(h, m.data());
@@ -889,13 +909,14 @@ sv_status sv_plan_compile(const sv_plan* plan, const double* params, uint32_t wh
     for (int d = 0; d < 2; ++d) {
         if (!((which >> d) & 1)) continue;
         svh::Program prog;
-        std::string err = svh::lower(P, params, 8, d ? rmax_bwd(8) : rmax_fwd(8), d == 1, &prog, false, d ? 0 : rwide_fwd());
+        const bool fuse = d == 0 && env_int("SVGB_FUSE_PERM", 1, 0, 1) == 1;   // as sv_run lowers it
+        std::string err = svh::lower(P, params, 8, d ? rmax_bwd(8) : rmax_fwd(8), d == 1, &prog, false, d ? 0 : rwide_fwd(), fuse);
         if (!err.empty()) return fail(err.find("not supported") != std::string::npos ? SV_ERR_UNSUPPORTED : SV_ERR_ARG, err);
         svh::Packed pk;
         err = svh::pack(prog, P.n, 8, &pk);
         if (!err.empty()) return fail(SV_ERR_ARG, err);
         std::vector<std::shared_ptr<svj::Built>> built;
-        sv_status s = jit_prepare((uint32_t)P.n, pk, d + 1, &built);
+        sv_status s = jit_prepare((uint32_t)P.n, pk, d + 1, &built, prog.fused_perm ? prog.dst.data() : nullptr);
         if (s) return s;
         count += (uint32_t)built.size();
     }

@@ -458,7 +458,9 @@ std::string Gen::run() {
     // bits (local runs cut into pieces of at most 8 bits, the first piece exactly bits 0..3)
     // form at most 5 dimensions ----
     std::vector<Run> dims;
-    tma = !V.batched && tma_runs(st, n, NV, &dims);
+    const bool OUTP = V.dst != nullptr;
+    if (OUTP && (NV != 1 || V.batched)) return "jit: an out-of-place permuted write-back needs a forward stage";
+    tma = !V.batched && !OUTP && tma_runs(st, n, NV, &dims);
     if (const char* e = getenv("SVGB_JIT_NS")) NS = std::max(1, std::min(4, atoi(e)));
     if (tma) {   // coordinates of a tile along each dimension: (tile index >> shift) & mask
         B->tma = true;
@@ -867,6 +869,43 @@ std::string Gen::run() {
             body += fmt("if (tid == 0) {\nif (brk != 0xffffffffu)\nfor (u32 k = 0; k < %du; ++k) {\nconst u32 i2 = brk + k;\n"
                         "if ((u64)blockIdx.x + (u64)i2 * gridDim.x < ntiles) svj_mbar_wait(&bars[i2 %% %du], (i2 / %du) & 1u, nullptr);\n}\n"
                         "svj_bulk_wait0();\n}\n", NS, NS, NS);
+        } else if (OUTP) {
+            // out of place through the bit map: output element e enumerates the tile bits in
+            // order of their destination bits (o[0] lowest), so a thread writes the pair
+            // e, e + 1 and consecutive threads consecutive pairs of the destination
+            std::vector<std::pair<int, int>> od;
+            for (int b = 0; b < T; ++b) od.push_back({V.dst[st.tile_pos[b]], b});
+            std::sort(od.begin(), od.end());
+            const int QD = (int)A.q.size();
+            for (int i = 0; i < NG; ++i) A.Q(1ull << V.dst[st.glob_pos[i]]);
+            for (int k = 0; k < T; ++k) A.Q(1ull << od[k].first);
+            pre += "u64 dtid = 0;\nu32 otid = 0;\n";
+            for (int j = 0; j < TR; ++j)
+                pre += fmt("if ((tid >> %d) & 1u) { dtid |= a.q[%d]; otid ^= %uu; }\n", j, QD + NG + 1 + j,
+                           swz(1u << od[1 + j].second));
+            const bool rd4 = od[0].second == 0, wr4 = od[0].first == 0;
+            const uint32_t s1 = swz(1u << od[0].second);
+            body += fmt("{\nu64 dbase = 0;\n#pragma unroll 1\nfor (int i = 0; i < %d; ++i)\nif ((t >> i) & 1ull) dbase |= S.q[%d + i];\n",
+                        NG, QD);
+            for (int i = 0; i < NCH; ++i) {
+                uint32_t so = 0;
+                std::string pe = "dbase | dtid";
+                for (int b = 0; (1 << b) < NCH; ++b)
+                    if ((i >> b) & 1) {
+                        so ^= swz(1u << od[1 + TR + b].second);
+                        pe += fmt(" | S.q[%d]", QD + NG + 1 + TR + b);
+                    }
+                body += "{\n";
+                if (rd4) body += fmt("const float4 x = *reinterpret_cast<const float4*>(T0 + (otid ^ %uu));\n", so);
+                else body += fmt("const float2 x0 = T0[otid ^ %uu], x1 = T0[otid ^ %uu];\n", so, so ^ s1);
+                body += fmt("float2* const d = a.v1 + (%s);\n", pe.c_str());
+                if (wr4) body += rd4 ? "*reinterpret_cast<float4*>(d) = x;\n"
+                                     : "*reinterpret_cast<float4*>(d) = make_float4(x0.x, x0.y, x1.x, x1.y);\n";
+                else if (rd4) body += fmt("d[0] = make_float2(x.x, x.y);\nd[S.q[%d]] = make_float2(x.z, x.w);\n", QD + NG);
+                else body += fmt("d[0] = x0;\nd[S.q[%d]] = x1;\n", QD + NG);
+                body += "}\n";
+            }
+            body += "}\nbase = bn;\n__syncthreads();\n}\n";
         } else {
             // write the tile back in place
             for (int i = 0; i < NCH; ++i)
@@ -939,7 +978,16 @@ std::string structure_key(const StageView& v) {
     put(st.R);
     {
         std::vector<Run> dims;
-        put(tma_runs(st, v.n, v.nv, &dims) ? 1 : 0);
+        put(!v.dst && tma_runs(st, v.n, v.nv, &dims) ? 1 : 0);
+    }
+    if (v.dst) {   // the write-back order: tile bits by destination, and whether it starts at bit 0
+        std::vector<std::pair<int, int>> od;
+        for (uint32_t b = 0; b < st.T; ++b) od.push_back({v.dst[st.tile_pos[b]], (int)b});
+        std::sort(od.begin(), od.end());
+        put(2 + (od[0].first == 0 ? 1 : 0));
+        for (auto& x : od) put((uint64_t)x.second);
+    } else {
+        put(0);
     }
     for (const char* e : {"SVGB_JIT_TMA", "SVGB_JIT_NS", "SVGB_JIT_NB", "SVGB_JIT_THR", "SVGB_JIT_THR_BWD", "SVGB_JIT_CBANK", "SVGB_JIT_CBANK_OPS", "SVGB_JIT_GTAB"}) {
         const char* x = getenv(e);

@@ -35,6 +35,9 @@ struct StageView {
     // their angle from params[pofs[c] + index]; gradient partials per circuit segment
     int batched = 0;
     int zero_init = 0;                   // batched forward stage 0: tiles start as |0...0>
+    // forward, not batched: write the tile out of place (to v1) through a bit map,
+    // dst[physical bit] = destination bit (the final qubit order); nullptr = in place
+    const int* dst = nullptr;
 };
 
 struct Kernel;

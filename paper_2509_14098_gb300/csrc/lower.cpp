@@ -36,16 +36,19 @@ struct Pend {
 
 class Lowerer {
   public:
-    Lowerer(const Plan& p, const double* params, int eb, int rmax, bool bwd, bool bind, Program* out, int rwide)
-        : P_(p), params_(params), eb_(eb), rmax_(rmax), rwide_(rwide), bwd_(bwd), bind_(bind), out_(out) {}
+    Lowerer(const Plan& p, const double* params, int eb, int rmax, bool bwd, bool bind, Program* out, int rwide,
+            bool fuse_perm)
+        : P_(p), params_(params), eb_(eb), rmax_(rmax), rwide_(rwide), bwd_(bwd), bind_(bind), fuse_perm_(fuse_perm),
+          out_(out) {}
 
     std::string run();
 
   private:
+    uint64_t output_tile(int s, uint64_t tile) const;
     const Plan& P_;
     const double* params_;
     int eb_, rmax_, rwide_;
-    bool bwd_, bind_;
+    bool bwd_, bind_, fuse_perm_;
     Program* out_;
     std::map<uint64_t, Pend> pending_;
     double gphase_ = 0.0;
@@ -347,11 +350,38 @@ std::string Lowerer::gate(const GateRec& g, const PGate& pg) {
     return "";
 }
 
+// The last forward stage of a plan whose final map is not the identity writes its tile
+// out of place through that map (the data reshaping of Sec. 4.3 fused into the stage's
+// write-back).  Destination addresses are contiguous over the tile bits whose
+// destinations are the lowest qubits, so local bits that no gate of the stage touches
+// (the partitioner's fill, Sec. 4.2) are traded for the physical bits that land on
+// qubits 0, 1, 2, ...: more local bits never make a stage wrong.
+uint64_t Lowerer::output_tile(int s, uint64_t tile) const {
+    const int n = P_.n;
+    uint64_t keep = (eb_ == 8 ? 1ull : 0ull);
+    for (int b = 0; b < P_.n_fixed && b < n; ++b) keep |= 1ull << b;
+    for (uint32_t i : P_.top.ids[s]) {
+        const GateRec& g = P_.gates[i];
+        if (g.kind == K_SWAP) continue;   // a relabel: no op
+        for (int k = 0; k < P_.phys[i].nq; ++k) keep |= 1ull << P_.phys[i].p[k];
+    }
+    uint64_t freeb = tile & ~keep;
+    for (int q = 0; q < n && freeb; ++q) {
+        const uint64_t want = 1ull << P_.final_map[q];   // physical bit that becomes qubit q
+        if (tile & want) continue;
+        const uint64_t drop = freeb & (~freeb + 1);      // lowest free bit
+        tile = (tile & ~drop) | want;
+        freeb &= ~drop;
+    }
+    return tile;
+}
+
 std::string Lowerer::stage(int s) {
     // complex64 tiles are staged in 16-byte chunks of two amplitudes, so the tile
     // always holds physical bit 0 (a plan without reserved low bits may not)
-    const uint64_t tile = P_.top.local[s] | (eb_ == 8 ? 1ull : 0ull);
+    uint64_t tile = P_.top.local[s] | (eb_ == 8 ? 1ull : 0ull);
     const int n = P_.n;
+    if (fuse_perm_ && s == (int)P_.top.local.size() - 1) tile = output_tile(s, tile);
     svk::Stage st;
     std::memset(&st, 0, sizeof(st));
     int T = 0;
@@ -455,6 +485,13 @@ std::string Lowerer::run() {
     out_->identity_map = true;
     for (int q = 0; q < P_.n; ++q)
         if (P_.final_map[q] != q) out_->identity_map = false;
+    out_->fused_perm = false;
+    out_->dst.clear();
+    if (fuse_perm_ && !out_->identity_map) {
+        out_->fused_perm = true;
+        out_->dst.assign(P_.n, 0);
+        for (int q = 0; q < P_.n; ++q) out_->dst[P_.final_map[q]] = q;
+    }
     return "";
 }
 
@@ -625,9 +662,10 @@ std::string pack(const Program& p, int n, int elem_bytes, Packed* out) {
 }
 
 std::string lower(const Plan& plan, const double* params, int elem_bytes, int rmax, bool backward,
-                  Program* out, bool bind, int rwide) {
+                  Program* out, bool bind, int rwide, bool fuse_perm) {
     if (plan.n_params > 0 && params == nullptr && !bind) return "circuit has parameters but params is NULL";
-    Lowerer L(plan, params, elem_bytes, rmax, backward, bind, out, rwide);
+    if (fuse_perm && backward) return "internal: a fused output permutation needs a forward program";
+    Lowerer L(plan, params, elem_bytes, rmax, backward, bind, out, rwide, fuse_perm);
     return L.run();
 }
 

@@ -82,6 +82,10 @@ struct Program {
     std::vector<svk::Term> terms;
     std::vector<int> slot_param;   // backward: global gradient slot -> parameter
     bool identity_map = true;
+    // fuse_perm: the last stage writes out of place through the final map;
+    // dst[physical bit] = the qubit it becomes
+    bool fused_perm = false;
+    std::vector<int> dst;
 };
 
 // Device blob of a lowered program for one precision: Stage[] | Group[] |
@@ -104,7 +108,10 @@ std::string pack(const Program& p, int n, int elem_bytes, Packed* out);
 // rejected in this mode.
 // rwide > rmax: a stage that needs 4 or more register groups at rmax is lowered with
 // rwide register bits instead when that needs fewer groups (0: never).
+// fuse_perm (forward only): when the final map is not the identity, the last stage's
+// tile trades its untouched fill bits for the bits that become the lowest qubits, and
+// the program is marked for an out-of-place write-back through the map (Program::dst).
 std::string lower(const Plan& plan, const double* params, int elem_bytes, int rmax, bool backward,
-                  Program* out, bool bind = false, int rwide = 0);
+                  Program* out, bool bind = false, int rwide = 0, bool fuse_perm = false);
 
 }  // namespace svh

@@ -62,14 +62,46 @@ def test_brick16_config(sv):
     assert abs(st.norm() - 1) < 1e-6
 
 
+@pytest.mark.parametrize("dtype", [0, 1])
 @pytest.mark.parametrize("n,L", [(6, 4), (10, 6), (14, 11), (17, 11), (18, 13)])
-def test_qft_matches_oracle_and_fft(sv, n, L):
+def test_qft_matches_oracle_and_fft(sv, n, L, dtype):
     psi0 = C.random_state(n, 2)
-    got, st, _ = run_gpu(sv, C.qft(n), L, psi0)
+    got, st, _ = run_gpu(sv, C.qft(n), L, psi0, dtype)
     ref = S.simulate(C.qft(n), None, psi0)
-    assert np.linalg.norm(got - ref) <= 2e-5
-    assert np.linalg.norm(got - np.fft.ifft(psi0, norm="ortho")) <= 2e-5
-    assert st.run_info()["permutation_sweeps"] == 1      # bit reversal left by the SWAPs
+    assert np.linalg.norm(got - ref) <= TOL[dtype]
+    assert np.linalg.norm(got - np.fft.ifft(psi0, norm="ortho")) <= TOL[dtype]
+    # the bit reversal left by the SWAPs: complex64 stages write it in the last stage's
+    # write-back, complex128 runs one permutation sweep
+    assert st.run_info()["permutation_sweeps"] == (0 if dtype == 0 else 1)
+
+
+@pytest.mark.parametrize("n,L", [(12, 6), (16, 11)])
+def test_fused_permutation_on_an_owned_state(sv, n, L):
+    """A handle that owns its state (sv_create with no buffer): the permuted last stage
+    leaves the state in the handle's second buffer, which sv_info then reports."""
+    import ctypes
+    from paper_2509_14098_gb300 import _native as N
+    psi0 = C.random_state(n, 4).astype(np.complex64)
+    h = ctypes.c_void_p()
+    N.check(N.lib.sv_create(n, 0, None, None, ctypes.byref(h)))
+    try:
+        N.check(N.lib.sv_set_state_host(h, psi0.ctypes.data_as(ctypes.c_void_p)))
+        plan = sv.Plan(C.qft(n), L)
+        N.check(N.lib.sv_run(h, plan.handle, None, 0))
+        out = np.empty_like(psi0)
+        N.check(N.lib.sv_get_state_host(h, out.ctypes.data_as(ctypes.c_void_p)))
+        ref = S.simulate(C.qft(n), None, psi0.astype(np.complex128))
+        assert np.linalg.norm(out - ref) <= 2e-5
+        info = N.sv_run_info()
+        N.check(N.lib.sv_last_run_info(h, ctypes.byref(info)))
+        assert info.permutation_sweeps == 0
+        # a second run (the inverse transform) from the moved state restores the input
+        inv = sv.Plan(C.inverse(C.qft(n)), L)
+        N.check(N.lib.sv_run(h, inv.handle, None, 0))
+        N.check(N.lib.sv_get_state_host(h, out.ctypes.data_as(ctypes.c_void_p)))
+        assert np.linalg.norm(out - psi0) <= 4e-5
+    finally:
+        N.lib.sv_destroy(h)
 
 
 @pytest.mark.parametrize("dtype", [0, 1])
