@@ -2,6 +2,8 @@
 #pragma once
 #include <stdint.h>
 
+#include <complex>
+
 #include <string>
 #include <vector>
 
@@ -56,4 +58,15 @@ struct GemmProgram {
 };
 // prec: 1 = TF32x3, 2 = BF16x3.  Returns "" or an error.
 std::string plan_gemm(const Plan& plan, const double* params, int prec, GemmProgram* out);
+
+// The fused unitary of the gates ids (plan gate indices, in order) over the physical
+// bits lp[0..k-1] (index bit j <-> lp[j]), formed in FP64, column-major
+// (U[col * 2^k + row]).  Returns "" or an error (a gate outside those bits).
+std::string fuse_unitary(const Plan& P, const std::vector<uint32_t>& ids, const int* lp, int k, const double* params,
+                         std::vector<std::complex<double>>* U);
+// The B operand of U: its real embedding (N = 2^(k+1) rows), split into rounded hi / lo
+// halves, per K chunk of 128 bytes per row (32 TF32 / 64 BF16 elements) one hi block of
+// N x 128 bytes then one lo block, 128-byte-swizzled K-major; (2^(k+1) / chunk elements)
+// x 2 N x 128 bytes written at dst.
+void emit_b(const std::vector<std::complex<double>>& U, int k, bool tf32, uint8_t* dst);
 }  // namespace svh

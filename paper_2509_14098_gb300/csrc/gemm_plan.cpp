@@ -94,6 +94,90 @@ static size_t sw128(uint32_t r, uint32_t b) {
     return (size_t)(r >> 3) * 1024 + (r & 7) * 128 + ((((b >> 4) ^ (r & 7)) & 7) << 4) + (b & 15);
 }
 
+std::string fuse_unitary(const Plan& P, const std::vector<uint32_t>& ids, const int* lp, int k, const double* params,
+                         std::vector<cd>* Uout) {
+    const int D = 1 << k;
+    int lidx[64];
+    for (int b = 0; b < 64; ++b) lidx[b] = -1;
+    for (int j = 0; j < k; ++j) lidx[lp[j]] = j;
+    std::vector<cd>& U = *Uout;
+    U.assign((size_t)D * D, 0.0);
+    for (int c = 0; c < D; ++c) U[(size_t)c * D + c] = 1.0;   // column-major: U[col][row]
+    for (uint32_t gi : ids) {
+        const GateRec& g = P.gates[gi];
+        const PGate& pg = P.phys[gi];
+        if (g.kind == K_SWAP) continue;   // relabel
+        int nq;
+        cd m[16];
+        gate_full(g, params, &nq, m);
+        if (nq == 1) {
+            const int q = lidx[pg.p[0]];
+            if (q < 0) return "internal: gate outside the local set";
+            for (int c = 0; c < D; ++c) {
+                cd* col = &U[(size_t)c * D];
+                for (int i = 0; i < D; ++i)
+                    if (!((i >> q) & 1)) {
+                        cd a0 = col[i], a1 = col[i | (1 << q)];
+                        col[i] = m[0] * a0 + m[1] * a1;
+                        col[i | (1 << q)] = m[2] * a0 + m[3] * a1;
+                    }
+            }
+        } else {
+            const int q0 = lidx[pg.p[0]], q1 = lidx[pg.p[1]];
+            if (q0 < 0 || q1 < 0) return "internal: gate outside the local set";
+            for (int c = 0; c < D; ++c) {
+                cd* col = &U[(size_t)c * D];
+                for (int i = 0; i < D; ++i) {
+                    if ((i >> q0) & 1 || (i >> q1) & 1) continue;
+                    int idx[4] = {i, i | (1 << q1), i | (1 << q0), i | (1 << q0) | (1 << q1)};
+                    cd v[4] = {col[idx[0]], col[idx[1]], col[idx[2]], col[idx[3]]};
+                    for (int r = 0; r < 4; ++r) {
+                        cd acc = 0;
+                        for (int q = 0; q < 4; ++q) acc += m[r * 4 + q] * v[q];
+                        col[idx[r]] = acc;
+                    }
+                }
+            }
+        }
+    }
+    return "";
+}
+
+// Real embedding Ut[n][kk] (n = 2i + a output float, kk = 2j + b input float), split
+// into rounded hi / lo halves, one 128-byte K chunk per row per block: chunk c at
+// c * 2 * (N x 128 bytes), hi block then lo block.
+void emit_b(const std::vector<cd>& U, int k, bool tf32, uint8_t* base) {
+    const int D = 1 << k;
+    const uint32_t Nn = 2u << k;
+    const size_t block = (size_t)Nn * 128;
+    const size_t bcb = 2 * block;
+    const uint32_t kc = tf32 ? 32u : 64u;   // K elements per chunk
+    for (uint32_t r = 0; r < Nn; ++r) {
+        const int i = (int)(r >> 1), a = (int)(r & 1);
+        for (uint32_t kk = 0; kk < Nn; ++kk) {
+            const int j = (int)(kk >> 1), b = (int)(kk & 1);
+            const cd u = U[(size_t)j * D + i];
+            const double v = (a == b) ? u.real() : (a == 1 ? u.imag() : -u.imag());
+            const float x = (float)v;
+            uint8_t* ch = base + (size_t)(kk / kc) * bcb;
+            const uint32_t kl = kk % kc;
+            if (tf32) {
+                float hi, lo;
+                split_tf32(x, &hi, &lo);
+                const size_t off = sw128(r, kl * 4);
+                std::memcpy(ch + off, &hi, 4);
+                std::memcpy(ch + block + off, &lo, 4);
+            } else {
+                const uint16_t hi = to_bf16(x);
+                const uint16_t lo = to_bf16(x - from_bf16(hi));
+                const size_t off = sw128(r, kl * 2);
+                std::memcpy(ch + off, &hi, 2);
+                std::memcpy(ch + block + off, &lo, 2);
+            }
+        }
+    }
+}
+
 std::string plan_gemm(const Plan& P, const double* params, int prec, GemmProgram* out) {
     out->stages.clear();
     out->ublob.clear();
@@ -180,52 +264,9 @@ std::string plan_gemm(const Plan& P, const double* params, int prec, GemmProgram
             for (int v : left) perm.push_back(v);
             for (size_t i = 0; i < perm.size(); ++i) st.pperm[i] = (uint8_t)perm[i];
         }
-        // fused unitary over the local qubits (index bit j <-> lp[j])
-        const int D = 1 << k;
-        int lidx[64];
-        for (int b = 0; b < 64; ++b) lidx[b] = -1;
-        for (int j = 0; j < k; ++j) lidx[lp[j]] = j;
-        std::vector<cd> U((size_t)D * D, 0.0);
-        for (int c = 0; c < D; ++c) U[(size_t)c * D + c] = 1.0;   // column-major: U[col][row]
-        for (uint32_t gi : P.top.ids[s]) {
-            const GateRec& g = P.gates[gi];
-            const PGate& pg = P.phys[gi];
-            if (g.kind == K_SWAP) continue;   // relabel
-            int nq;
-            cd m[16];
-            gate_full(g, params, &nq, m);
-            if (nq == 1) {
-                const int q = lidx[pg.p[0]];
-                if (q < 0) return "internal: gate outside the local set";
-                for (int c = 0; c < D; ++c) {
-                    cd* col = &U[(size_t)c * D];
-                    for (int i = 0; i < D; ++i)
-                        if (!((i >> q) & 1)) {
-                            cd a0 = col[i], a1 = col[i | (1 << q)];
-                            col[i] = m[0] * a0 + m[1] * a1;
-                            col[i | (1 << q)] = m[2] * a0 + m[3] * a1;
-                        }
-                }
-            } else {
-                const int q0 = lidx[pg.p[0]], q1 = lidx[pg.p[1]];
-                if (q0 < 0 || q1 < 0) return "internal: gate outside the local set";
-                for (int c = 0; c < D; ++c) {
-                    cd* col = &U[(size_t)c * D];
-                    for (int i = 0; i < D; ++i) {
-                        if ((i >> q0) & 1 || (i >> q1) & 1) continue;
-                        int idx[4] = {i, i | (1 << q1), i | (1 << q0), i | (1 << q0) | (1 << q1)};
-                        cd v[4] = {col[idx[0]], col[idx[1]], col[idx[2]], col[idx[3]]};
-                        for (int r = 0; r < 4; ++r) {
-                            cd acc = 0;
-                            for (int q = 0; q < 4; ++q) acc += m[r * 4 + q] * v[q];
-                            col[idx[r]] = acc;
-                        }
-                    }
-                }
-            }
-        }
-        // Real embedding Ut[n][kk] (n = 2i + a output float, kk = 2j + b input float),
-        // split into rounded hi / lo halves, one 128-byte K chunk per row per block.
+        std::vector<cd> U;
+        std::string ferr = fuse_unitary(P, P.top.ids[s], lp, k, params, &U);
+        if (!ferr.empty()) return ferr;
         const uint32_t Nn = st.N;
         const size_t block = (size_t)Nn * 128;
         st.b_chunk_bytes = (uint32_t)(2 * block);
@@ -237,32 +278,7 @@ std::string plan_gemm(const Plan& P, const double* params, int prec, GemmProgram
         st.nslot = (fixed + 3 * slot <= 224 * 1024) ? 3u : 2u;
         st.b_off = (uint64_t)((out->ublob.size() + 1023) & ~(size_t)1023);
         out->ublob.resize(st.b_off + (size_t)st.nchunk * st.b_chunk_bytes, 0);
-        uint8_t* base = out->ublob.data() + st.b_off;
-        const uint32_t kc = tf32 ? 32u : 64u;   // K elements per chunk
-        for (uint32_t r = 0; r < Nn; ++r) {
-            const int i = (int)(r >> 1), a = (int)(r & 1);
-            for (uint32_t kk = 0; kk < Nn; ++kk) {
-                const int j = (int)(kk >> 1), b = (int)(kk & 1);
-                const cd u = U[(size_t)j * D + i];
-                const double v = (a == b) ? u.real() : (a == 1 ? u.imag() : -u.imag());
-                const float x = (float)v;
-                uint8_t* ch = base + (size_t)(kk / kc) * st.b_chunk_bytes;
-                const uint32_t kl = kk % kc;
-                if (tf32) {
-                    float hi, lo;
-                    split_tf32(x, &hi, &lo);
-                    const size_t off = sw128(r, kl * 4);
-                    std::memcpy(ch + off, &hi, 4);
-                    std::memcpy(ch + block + off, &lo, 4);
-                } else {
-                    const uint16_t hi = to_bf16(x);
-                    const uint16_t lo = to_bf16(x - from_bf16(hi));
-                    const size_t off = sw128(r, kl * 2);
-                    std::memcpy(ch + off, &hi, 2);
-                    std::memcpy(ch + block + off, &lo, 2);
-                }
-            }
-        }
+        emit_b(U, k, tf32, out->ublob.data() + st.b_off);
         out->stages.push_back(st);
     }
     out->identity_map = true;

@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "gemm.h"
+#include "hier.h"
 #include "planner.h"
 
 using namespace svh;
@@ -294,6 +295,125 @@ static void run_gemm(const GemmProgram& gp, int prec, int n, std::vector<cd>& ps
     }
 }
 
+
+// The hierarchical tensor-core stage, emulated byte for byte: every tile's amplitudes are
+// split into (hi, lo) halves and stored at the A-operand offsets the layout tables give,
+// the operands are read back through the 128-byte-swizzled K-major layout, each
+// sub-partition's three products are summed in double, and the epilogue stores through
+// the next layout (the last one into the FP32 output tile, read back by its own table).
+static float emu_tf32(float x) {
+    uint32_t b;
+    memcpy(&b, &x, 4);
+    b = (b + 0x0FFFu + ((b >> 13) & 1u)) & 0xFFFFE000u;
+    memcpy(&x, &b, 4);
+    return x;
+}
+static float emu_bf16(float x) {
+    uint32_t b;
+    memcpy(&b, &x, 4);
+    b = (b + 0x7FFFu + ((b >> 16) & 1u)) & 0xFFFF0000u;
+    memcpy(&x, &b, 4);
+    return x;
+}
+static void run_hier(const HierProgram& hp, int prec, std::vector<cd>& psi) {
+    const bool tf32 = prec == 1;
+    auto sw = [](uint32_t r, uint32_t b) -> size_t {
+        return (size_t)(r / 8) * 1024 + (r % 8) * 128 + ((((b / 16) ^ (r % 8)) % 8) * 16) + b % 16;
+    };
+    auto rnd = [&](float x) { return tf32 ? emu_tf32(x) : emu_bf16(x); };
+    const uint32_t esz = tf32 ? 4 : 2, kc = tf32 ? 32u : 64u;
+    for (const HierStage& st : hp.launches) {
+        const uint32_t T = st.T, N = st.N, K = N, D2 = 1u << st.k;
+        auto off = [&](int layout, uint32_t x) {
+            uint32_t o = 0;
+            for (uint32_t b = 0; b < T; ++b)
+                if ((x >> b) & 1) o ^= st.ao[layout][b];
+            return o;
+        };
+        // operand element store / load (byte images of hi / lo halves)
+        std::vector<uint8_t> A(st.a_bytes);
+        auto put = [&](uint32_t o, float v) {   // v at A offset o: hi there, lo 16384 above
+            const float hi = rnd(v), lo = rnd(v - hi);
+            if (tf32) {
+                memcpy(&A[o], &hi, 4);
+                memcpy(&A[o + 16384], &lo, 4);
+            } else {
+                uint32_t bh, bl;
+                memcpy(&bh, &hi, 4);
+                memcpy(&bl, &lo, 4);
+                const uint16_t h = (uint16_t)(bh >> 16), l = (uint16_t)(bl >> 16);
+                memcpy(&A[o], &h, 2);
+                memcpy(&A[o + 16384], &l, 2);
+            }
+        };
+        auto get = [&](const uint8_t* p) -> double {
+            if (tf32) {
+                float x;
+                memcpy(&x, p, 4);
+                return x;
+            }
+            uint16_t h;
+            memcpy(&h, p, 2);
+            const uint32_t b = (uint32_t)h << 16;
+            float x;
+            memcpy(&x, &b, 4);
+            return x;
+        };
+        std::vector<double> Ah(128 * K), Al(128 * K), Bh((size_t)N * K), Bl((size_t)N * K), Dm(128 * N);
+        std::vector<double> outre(1u << T), outim(1u << T);
+        for (uint64_t g = 0; g < (1ull << st.n_glob); ++g) {
+            const uint64_t base = deposit(g, st.glob_pos, (int)st.n_glob);
+            for (uint32_t x = 0; x < (1u << T); ++x) {   // load: pair element x at layout 0
+                const cd a = psi[base | deposit(x, st.tile_pos, (int)T)];
+                const uint32_t o = off(0, x);
+                put(o, (float)a.real());
+                put(o + esz, (float)a.imag());
+            }
+            for (uint32_t s = 0; s < st.n_sub; ++s) {
+                const uint8_t* B = hp.ublob.data() + st.b_off + (size_t)s * st.b_bytes;
+                for (uint32_t r = 0; r < 128; ++r)
+                    for (uint32_t kk = 0; kk < K; ++kk) {
+                        const size_t o = (size_t)(kk / kc) * 32768 + sw(r, (kk % kc) * esz);
+                        Ah[r * K + kk] = get(&A[o]);
+                        Al[r * K + kk] = get(&A[o + 16384]);
+                    }
+                for (uint32_t r = 0; r < N; ++r)
+                    for (uint32_t kk = 0; kk < K; ++kk) {
+                        const size_t o = (size_t)(kk / kc) * 2 * N * 128 + sw(r, (kk % kc) * esz);
+                        Bh[r * K + kk] = get(B + o);
+                        Bl[r * K + kk] = get(B + o + (size_t)N * 128);
+                    }
+                for (uint32_t m = 0; m < 128; ++m)
+                    for (uint32_t c = 0; c < N; ++c) {
+                        double acc = 0;
+                        for (uint32_t kk = 0; kk < K; ++kk)
+                            acc += Ah[m * K + kk] * Bh[c * K + kk] + Al[m * K + kk] * Bh[c * K + kk] +
+                                   Ah[m * K + kk] * Bl[c * K + kk];
+                        Dm[m * N + c] = (float)acc;   // the accumulator is FP32
+                    }
+                for (uint32_t m = 0; m < 128; ++m)
+                    for (uint32_t j = 0; j < D2; ++j) {
+                        const uint32_t x = (uint32_t)(deposit(m, st.col_bits[s], 7) | deposit(j, st.amp_bits[s], (int)st.k));
+                        const double re = Dm[m * N + 2 * j], im = Dm[m * N + 2 * j + 1];
+                        if (s + 1 < st.n_sub) {
+                            const uint32_t o = off((int)s + 1, x);
+                            put(o, (float)re);
+                            put(o + esz, (float)im);
+                        } else {
+                            const uint32_t o = off((int)st.n_sub, x) / 8;
+                            outre[o] = re;
+                            outim[o] = im;
+                        }
+                    }
+            }
+            for (uint32_t x = 0; x < (1u << T); ++x) {
+                const uint32_t o = off((int)st.n_sub, x) / 8;
+                psi[base | deposit(x, st.tile_pos, (int)T)] = cd(outre[o], outim[o]);
+            }
+        }
+    }
+}
+
 template <typename T>
 static T rd(FILE* f) {
     T v;
@@ -306,12 +426,14 @@ static T rd(FILE* f) {
 
 int main(int argc, char** argv) {
     if (argc != 4 || (strcmp(argv[1], "fwd") != 0 && strcmp(argv[1], "grad") != 0 && strcmp(argv[1], "bind") != 0 &&
-                      strcmp(argv[1], "gemm") != 0)) {
-        fprintf(stderr, "usage: stage_emu fwd|grad|bind|gemm in.bin out.bin\n");
+                      strcmp(argv[1], "gemm") != 0 && strcmp(argv[1], "fuse") != 0 && strcmp(argv[1], "hier") != 0)) {
+        fprintf(stderr, "usage: stage_emu fwd|grad|bind|gemm|fuse|hier in.bin out.bin\n");
         return 1;
     }
     const bool bind = strcmp(argv[1], "bind") == 0;
-    const bool gemm = strcmp(argv[1], "gemm") == 0;
+    const bool hier = strcmp(argv[1], "hier") == 0;   // L = k + 7, strict, qubits 0..3 fixed
+    const bool gemm = hier || strcmp(argv[1], "gemm") == 0;
+    const bool fuse = strcmp(argv[1], "fuse") == 0;   // forward with the output-permutation retile
     const bool want_grad = bind || strcmp(argv[1], "grad") == 0;
     FILE* f = fopen(argv[2], "rb");
     if (!f) return 1;
@@ -355,11 +477,34 @@ int main(int argc, char** argv) {
     if (bind)   // a bound RZ is a dense op: its qubit must be local
         for (size_t g = 0; g < P.gates.size(); ++g)
             if (P.gates[g].kind == K_RZ && P.gates[g].param >= 0) P.phys[g].bound = true;
-    const uint64_t fixed = (nf && !gemm) ? ((1ull << nf) - 1) : 0;
+    const uint64_t fixed = (nf && (!gemm || hier)) ? ((1ull << nf) - 1) : 0;
     std::string err = partition_core(n, P.phys, L, fixed, (1ull << n) - 1, &P.top, &P.cc, gemm);
     if (!err.empty()) {
         fprintf(stderr, "partition: %s\n", err.c_str());
         return 2;
+    }
+    if (hier) {
+        P.n_fixed = nf;
+        HierProgram hp;
+        err = plan_hier(P, np ? params.data() : nullptr, rmax, &hp);
+        if (!err.empty()) {
+            fprintf(stderr, "plan_hier: %s\n", err.c_str());
+            return 2;
+        }
+        run_hier(hp, rmax, psi);
+        FILE* o = fopen(argv[3], "wb");
+        if (!o) return 1;
+        const double nst = (double)hp.n_sub;
+        fwrite(&nst, sizeof(double), 1, o);
+        for (uint64_t y = 0; y < psi.size(); ++y) {   // physical -> canonical order
+            uint64_t x = 0;
+            for (int q = 0; q < n; ++q)
+                if ((y >> q) & 1) x |= 1ull << P.final_map[q];
+            const double v[2] = {psi[x].real(), psi[x].imag()};
+            fwrite(v, sizeof(double), 2, o);
+        }
+        fclose(o);
+        return 0;
     }
     if (gemm) {
         P.gemm_k = L;
@@ -387,7 +532,7 @@ int main(int argc, char** argv) {
     Program prog;
     const double* lp = (np && !bind) ? params.data() : nullptr;   // bind: parameters stay symbolic
     const double* bp = (np && bind) ? params.data() : nullptr;
-    err = lower(P, lp, eb, rmax, false, &prog, bind);
+    err = lower(P, lp, eb, rmax, false, &prog, bind, 0, fuse);
     if (!err.empty()) {
         fprintf(stderr, "lower: %s\n", err.c_str());
         return 2;

@@ -35,12 +35,13 @@ def emu(tmp_path_factory):
     cmd = ["g++", "-O2", "-std=c++17", "-I", CSRC, "-I", os.path.join(ROOT, "include"),
            os.path.join(ROOT, "tests", "host_emu", "stage_emu.cpp"),
            os.path.join(CSRC, "partition.cpp"), os.path.join(CSRC, "lower.cpp"),
-           os.path.join(CSRC, "gemm_plan.cpp"), "-o", exe]
+           os.path.join(CSRC, "gemm_plan.cpp"), os.path.join(CSRC, "hier_plan.cpp"), "-o", exe]
     subprocess.run(cmd, check=True, capture_output=True)
     return exe
 
 
-def run_emu(exe, tmp_path, circ, L, n_fixed, params, psi0, elem_bytes, rmax=4, obs=None, bind=False, gemm=False):
+def run_emu(exe, tmp_path, circ, L, n_fixed, params, psi0, elem_bytes, rmax=4, obs=None, bind=False, gemm=False,
+            fuse=False, hier=False):
     n = circ.n_qubits
     params = [] if params is None else list(params)
     buf = [struct.pack("<7i", n, L, n_fixed, len(params), len(circ.gates), elem_bytes, rmax)]
@@ -56,11 +57,11 @@ def run_emu(exe, tmp_path, circ, L, n_fixed, params, psi0, elem_bytes, rmax=4, o
             buf.append(struct.pack("<d", c) + bytes("IXYZ".index(ch) for ch in ps))
     fin, fout = tmp_path / "in.bin", tmp_path / "out.bin"
     fin.write_bytes(b"".join(buf))
-    mode = "gemm" if gemm else ("bind" if bind else ("grad" if obs is not None else "fwd"))
+    mode = "hier" if hier else ("gemm" if gemm else ("bind" if bind else ("grad" if obs is not None else ("fuse" if fuse else "fwd"))))
     r = subprocess.run([exe, mode, str(fin), str(fout)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
     raw = fout.read_bytes()
-    if gemm:
+    if gemm or hier:
         return int(np.frombuffer(raw[:8], dtype=np.float64)[0]), np.frombuffer(raw[8:], dtype=np.complex128)
     if obs is None:
         return np.frombuffer(raw, dtype=np.complex128)
@@ -192,3 +193,43 @@ def test_tensor_core_plan(emu, tmp_path, prec, k, n, seed):
     ref = S.simulate(circ, None, psi0)
     assert nst >= 1
     assert np.linalg.norm(got - ref) <= (2e-7 if prec == 1 else 2e-6) * nst
+
+
+@pytest.mark.parametrize("case", ["qft", "random_swaps"])
+@pytest.mark.parametrize("n,L", [(9, 5), (12, 7), (13, 11)])
+def test_fused_output_permutation_lowering(emu, tmp_path, case, n, L):
+    """Lowering for a last stage that writes through the final map (Sec. 4.3 reshaping
+    fused into the write-back): its tile trades untouched fill bits for the bits that
+    become the lowest qubits; the program must still compute the circuit."""
+    if case == "qft":
+        circ = C.qft(n)
+    else:
+        circ = C.random_circuit(n, 80, n + L)
+        rng = np.random.default_rng(n * L)
+        for _ in range(4):
+            a, b = (int(x) for x in rng.choice(n, 2, replace=False))
+            circ.gates.append(C.Gate("SWAP", (a, b), -1, ()))
+    psi0 = C.random_state(n, 9)
+    ref = S.simulate(circ, None, psi0)
+    got = run_emu(emu, tmp_path, circ, L, min(4, L - 1), None, psi0, 8, fuse=True)
+    assert np.linalg.norm(got - ref) <= TOL[8]
+
+
+@pytest.mark.parametrize("prec,k", [(2, 5), (2, 6), (1, 5)])
+@pytest.mark.parametrize("case", ["brick", "qft", "random"])
+def test_hierarchical_plan(emu, tmp_path, prec, k, case):
+    """Tiles of k + 7 qubits, each stage partitioned again into k-qubit sub-partitions
+    applied as split-precision GEMMs (Sec. 4.2's recursive partitioning): the emulated
+    operand layouts, splits and products must reproduce the oracle, within the derived
+    bound of the sub-partitions' GEMMs (3 (K / 8) 2^-23 each, K = 2^(k+1)); two global
+    qubits give four tiles per stage."""
+    n = k + 9
+    circ = {"brick": lambda: C.brickwork(n, 8, 3), "qft": lambda: C.qft(n),
+            "random": lambda: C.random_circuit(n, 150, 11)}[case]()
+    psi0 = C.random_state(n, 5)
+    ref = S.simulate(circ, None, psi0)
+    n_sub, got = run_emu(emu, tmp_path, circ, k + 7, 4, None, psi0, 8, rmax=prec, hier=True)
+    bound = n_sub * 3 * (2 ** (k + 1) / 8) * 2.0 ** -23
+    err = np.linalg.norm(got - ref)
+    assert err <= bound, (n_sub, err, bound)
+    print(case, prec, k, n_sub, err, bound)
