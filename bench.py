@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--gemm-k", default="5,6,7")
     ap.add_argument("--gemm-prec", default="1,2", help="1 = TF32x3, 2 = BF16x3")
     ap.add_argument("--no-c128", action="store_true", help="gemm section without the complex128 reference")
+    ap.add_argument("--gemm-hier", default="2:5,2:6,1:5",
+                    help="hierarchical tensor-core runs, prec:k pairs ('' for none)")
     ap.add_argument("--batch-count", type=int, default=2048)
     ap.add_argument("--no-autotune", action="store_true", help="batch section with the default (L, k) table")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
@@ -410,9 +412,8 @@ def gemm_section(args):
     st = sv.StateVector(n, tensor=psi)
     bytes_pass = 2.0 * (1 << n) * 8
     rows = []
-    cfgs = [(int(k), int(p)) for p in args.gemm_prec.split(",") for k in args.gemm_k.split(",")] + [(11, 0)]
-    for k, prec in cfgs:
-        plan = sv.Plan(circ, k, gemm=(prec != 0))
+    for k, prec, hier in gemm_configs(args):
+        plan = sv.Plan(circ, k, gemm=(prec != 0 and not hier), hier=hier)
         psi.copy_(psi0)
         st.run(plan, None, prec)              # warm-up (and the result compared below)
         st.synchronize()
@@ -427,9 +428,11 @@ def gemm_section(args):
         tm = st.timing(reset=True)
         st.timing(False)
         per = tm["stage_ms"] / max(1, tm["stage_launches"])
-        rows.append({"k": k, "prec": {0: "cudacore_c64_L11", 1: "tf32x3", 2: "bf16x3"}[prec],
-                     "stages": tm["stage_launches"], "ms_circuit": wall, "ms_per_stage": per,
-                     "gbs_per_stage": bytes_pass / (per * 1e-3) / 1e9, "err_l2_vs_c128": err})
+        row = {"k": k, "prec": prec_name(prec, hier), "stages": tm["stage_launches"], "ms_circuit": wall,
+               "ms_per_stage": per, "gbs_per_stage": bytes_pass / (per * 1e-3) / 1e9, "err_l2_vs_c128": err}
+        if hier:
+            row["sub_partitions"] = plan.hier_info(prec)[1]
+        rows.append(row)
     st.close()
     out = {"workload": f"brickwork n={n}, depth 24, seed 3, random complex64 input", "runs": rows,
            "reference": "complex128 CUDA-core run (L=11)" if ref is not None else None,
@@ -442,10 +445,27 @@ def gemm_section(args):
     return out
 
 
-def derived_gemm_bound(plan):
-    """Per fused stage 3 (K / 8) 2^-23 (K = 2^(k_eff + 1) FP32 accumulation terms,
-    k_eff = max(k, 6)), summed over the stages."""
-    return sum(3 * (2 ** (max(6, bin(m).count("1")) + 1) / 8) * 2.0 ** -23 for m, _ in plan.stages())
+def gemm_configs(args):
+    """(k, prec, hierarchical) runs of the tensor-core sections: flat stages per --gemm-k x
+    --gemm-prec, hierarchical ones per --gemm-hier, and the CUDA-core L = 11 plan."""
+    cfgs = [(int(k), int(p), False) for p in args.gemm_prec.split(",") for k in args.gemm_k.split(",")]
+    cfgs += [(int(pk.split(":")[1]), int(pk.split(":")[0]), True) for pk in args.gemm_hier.split(",") if pk]
+    return cfgs + [(11, 0, False)]
+
+
+def prec_name(prec, hier):
+    return {0: "cudacore_c64_L11", 1: "tf32x3", 2: "bf16x3"}[prec] + ("_hier" if hier else "")
+
+
+def gemm_eps(K, prec):
+    """Per split-precision GEMM on a norm-1 state: FP32 accumulation 3 (K / 8) 2^-23 plus
+    the state operand's split u = 2^-16 (BF16x3) / 2^-22 (TF32x3)."""
+    return 3 * (K / 8) * 2.0 ** -23 + (2.0 ** -16 if prec == 2 else 2.0 ** -22)
+
+
+def derived_gemm_bound(plan, prec):
+    """gemm_eps summed over the fused stages (K = 2^(k_eff + 1), k_eff = max(k, 6))."""
+    return sum(gemm_eps(2 ** (max(6, bin(m).count("1")) + 1), prec) for m, _ in plan.stages())
 
 
 def gemm_oracle26(args):
@@ -477,18 +497,19 @@ def gemm_oracle26(args):
     psi = torch.empty_like(x)
     st = sv.StateVector(n, tensor=psi)
     rows = []
-    for prec in [int(q) for q in args.gemm_prec.split(",")] + [0]:
-        for k in ([int(q) for q in args.gemm_k.split(",")] if prec else [11]):
-            plan = sv.Plan(circ, k, gemm=(prec != 0))
-            psi.copy_(x)
-            st.run(plan, None, prec)
-            st.synchronize()
-            err = float(torch.linalg.vector_norm(psi.to(torch.complex128) - r).item())
-            samp = float((psi[idx].to(torch.complex128) - amp).abs().max().item())
-            rows.append({"k": k, "prec": {0: "cudacore_c64_L11", 1: "tf32x3", 2: "bf16x3"}[prec],
-                         "stages": len(plan.stages()), "err_l2_vs_c128": err, "max_err_vs_oracle_samples": samp,
-                         "derived_bound": derived_gemm_bound(plan) if prec else 2e-5,
-                         "meets_target_2e-5": err <= 2e-5})
+    for k, prec, hier in gemm_configs(args):
+        plan = sv.Plan(circ, k, gemm=(prec != 0 and not hier), hier=hier)
+        psi.copy_(x)
+        st.run(plan, None, prec)
+        st.synchronize()
+        err = float(torch.linalg.vector_norm(psi.to(torch.complex128) - r).item())
+        samp = float((psi[idx].to(torch.complex128) - amp).abs().max().item())
+        if hier:
+            bound = plan.hier_info(prec)[1] * gemm_eps(2 ** (k + 1), prec)
+        else:
+            bound = derived_gemm_bound(plan, prec) if prec else 2e-5
+        rows.append({"k": k, "prec": prec_name(prec, hier), "stages": len(plan.stages()), "err_l2_vs_c128": err,
+                     "max_err_vs_oracle_samples": samp, "derived_bound": bound, "meets_target_2e-5": err <= 2e-5})
     st.close()
     del r, x, psi
     torch.cuda.empty_cache()

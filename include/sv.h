@@ -221,6 +221,27 @@ sv_status sv_partition_gemm(const sv_circuit* circuit, uint32_t k, sv_plan** out
 sv_status sv_gemm_plan_info(const sv_plan* plan, const double* params, sv_prec prec, uint32_t* n_stages,
                             uint32_t* keff, uint32_t* resident, uint32_t* nslot, uint8_t* lane_roles);
 
+/* Partition for the hierarchical tensor-core stages (Sec. 4.2: the partitioner invoked
+ * again inside each partition, for the next memory level; Sec. 5.2's multi-level
+ * fusion).  Level 1: the same DAG, closeness and frontier pass without exemptions, with
+ * L = k + 7 local qubits and qubits 0..3 reserved, one tile of a CTA in shared memory;
+ * level 2 (formed at sv_run): each stage's gates partitioned again with budget k inside
+ * its tile, each sub-partition one fused 2^k x 2^k unitary applied by the tensor cores
+ * to the tile's 128 columns, so a stage is one HBM pass however many sub-partitions it
+ * holds.  Run with sv_run and SV_PREC_BF16X3 (k = 5 or 6) or SV_PREC_TF32X3 (k = 5);
+ * complex64 states of at least k + 7 qubits.  Such a plan also runs on the CUDA cores.
+ * Errors: SV_ERR_ARG (k not 5 or 6, null argument), SV_ERR_UNSUPPORTED (fewer than
+ * k + 7 qubits), SV_ERR_PARTITION. */
+sv_status sv_partition_hier(const sv_circuit* circuit, uint32_t k, sv_plan** out);
+
+/* Shape of a hierarchical plan for prec, computed on the host (no GPU; introspection
+ * with no counterpart in the paper): *n_launches = stage launches (a stage of more than
+ * 24 sub-partitions takes several), *n_sub = sub-partitions (GEMMs per tile) in all.
+ * Either pointer may be NULL.  params as for sv_run.  Errors: SV_ERR_ARG,
+ * SV_ERR_UNSUPPORTED (not a hierarchical plan, or a combination the kernel lacks). */
+sv_status sv_hier_plan_info(const sv_plan* plan, const double* params, sv_prec prec, uint32_t* n_launches,
+                            uint32_t* n_sub);
+
 /* Partition summary.  local_masks[s] = physical-bit mask of stage s's local set
  * (after SWAP relabelling); gate_counts[s] = gates in stage s.  Either array may be
  * NULL; each must hold n_stages entries (query n_stages first with both NULL). */

@@ -55,14 +55,18 @@ def parse_qasm(text):
 class Plan:
     """Host-side partition of a circuit (sv_partition / sv_partition_ex)."""
 
-    def __init__(self, circuit, L, n_fixed=None, gemm=False):
-        """gemm=True: partition for tensor-core stages (sv_partition_gemm, L = fusion width k)."""
+    def __init__(self, circuit, L, n_fixed=None, gemm=False, hier=False):
+        """gemm=True: partition for tensor-core stages (sv_partition_gemm, L = fusion width k);
+        hier=True: hierarchical tensor-core stages (sv_partition_hier, L = sub-partition
+        width k, tiles of k + 7 qubits)."""
         self.circuit = circuit
         self.L = L
         c, self._gates = N.circuit_struct(circuit)
         self._c = c
         h = ctypes.c_void_p()
-        if gemm:
+        if hier:
+            N.check(N.lib.sv_partition_hier(ctypes.byref(c), L, ctypes.byref(h)))
+        elif gemm:
             N.check(N.lib.sv_partition_gemm(ctypes.byref(c), L, ctypes.byref(h)))
         elif n_fixed is None:
             N.check(N.lib.sv_partition(ctypes.byref(c), L, ctypes.byref(h)))
@@ -75,6 +79,13 @@ class Plan:
         if h is not None and h.value:
             N.lib.sv_plan_destroy(h)
             self.handle = None
+
+    def hier_info(self, prec, params=None):
+        """(stage launches, sub-partitions in all) of a hierarchical plan (sv_hier_plan_info)."""
+        p = None if params is None else np.ascontiguousarray(params, dtype=np.float64)
+        nl, ns = ctypes.c_uint32(), ctypes.c_uint32()
+        N.check(N.lib.sv_hier_plan_info(self.handle, N.as_double_ptr(p), prec, ctypes.byref(nl), ctypes.byref(ns)))
+        return nl.value, ns.value
 
     def stages(self):
         """[(local physical-bit mask, gate count)] per stage."""

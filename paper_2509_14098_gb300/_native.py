@@ -90,6 +90,9 @@ _SIGS = {
     "sv_partition_ex": ([ctypes.POINTER(sv_circuit), _u32, _u32, ctypes.POINTER(_vp)], ctypes.c_int),
     "sv_partition_gemm": ([ctypes.POINTER(sv_circuit), _u32, ctypes.POINTER(_vp)], ctypes.c_int),
     "sv_plan_stages": ([_vp, ctypes.POINTER(_u32), ctypes.POINTER(_u64), ctypes.POINTER(_u32)], ctypes.c_int),
+    "sv_partition_hier": ([ctypes.POINTER(sv_circuit), _u32, ctypes.POINTER(_vp)], ctypes.c_int),
+    "sv_hier_plan_info": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.POINTER(_u32), ctypes.POINTER(_u32)],
+                          ctypes.c_int),
     "sv_gemm_plan_info": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.POINTER(_u32),
                            ctypes.POINTER(_u32), ctypes.POINTER(_u32), ctypes.POINTER(_u32),
                            ctypes.POINTER(ctypes.c_uint8)], ctypes.c_int),

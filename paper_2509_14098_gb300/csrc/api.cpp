@@ -13,6 +13,7 @@
 #include <unordered_map>
 
 #include "gemm.h"
+#include "hier.h"
 #include "jit.h"
 #include "kernels.h"
 #include "planner.h"
@@ -656,6 +657,31 @@ sv_status sv_partition_gemm(const sv_circuit* circuit, uint32_t k, sv_plan** out
     return build_plan(circuit, k, 0, out, true);
 }
 
+sv_status sv_partition_hier(const sv_circuit* circuit, uint32_t k, sv_plan** out) {
+    if (k != 5 && k != 6) return fail(SV_ERR_ARG, "sub-partition width k must be 5 or 6");
+    if (!circuit || !out) return fail(SV_ERR_ARG, "null argument");
+    if (circuit->n_qubits < k + 7) return fail(SV_ERR_UNSUPPORTED, "hierarchical stages need at least k + 7 qubits");
+    sv_status s = build_plan(circuit, k + 7, 4, out, true);
+    if (s) return s;
+    (*out)->plan.gemm_k = 0;
+    (*out)->plan.hier_k = (int)k;
+    return SV_OK;
+}
+
+sv_status sv_hier_plan_info(const sv_plan* plan, const double* params, sv_prec prec, uint32_t* n_launches,
+                            uint32_t* n_sub) {
+    if (!plan) return fail(SV_ERR_ARG, "null argument");
+    if (prec != SV_PREC_TF32X3 && prec != SV_PREC_BF16X3) return fail(SV_ERR_ARG, "bad precision");
+    if (plan->plan.hier_k == 0) return fail(SV_ERR_UNSUPPORTED, "not a plan from sv_partition_hier");
+    if (plan->plan.n_params > 0 && !params) return fail(SV_ERR_ARG, "params is NULL");
+    svh::HierProgram hp;
+    std::string err = svh::plan_hier(plan->plan, params, prec == SV_PREC_TF32X3 ? 1 : 2, &hp);
+    if (!err.empty()) return fail(SV_ERR_UNSUPPORTED, err);
+    if (n_launches) *n_launches = (uint32_t)hp.launches.size();
+    if (n_sub) *n_sub = hp.n_sub;
+    return SV_OK;
+}
+
 sv_status sv_gemm_plan_info(const sv_plan* plan, const double* params, sv_prec prec, uint32_t* n_stages,
                             uint32_t* keff, uint32_t* resident, uint32_t* nslot, uint8_t* lane_roles) {
     if (!plan || !n_stages) return fail(SV_ERR_ARG, "null argument");
@@ -861,6 +887,44 @@ static sv_status run_forward(sv_handle h, const sv_plan* plan, const double* par
     return SV_OK;
 }
 
+// hierarchical tensor-core stages: one launch per run of sub-partitions of a stage
+static sv_status run_hier(sv_handle h, const sv_plan* plan, const double* params, int prec) {
+    const svh::Plan& P = plan->plan;
+    svh::HierProgram hp;
+    std::string err = svh::plan_hier(P, params, prec, &hp);
+    if (!err.empty()) return fail(SV_ERR_UNSUPPORTED, err);
+    const size_t sb = hp.launches.size() * sizeof(svk::HierStage);
+    const size_t aoff = (sb + 1023) & ~(size_t)1023;
+    const size_t total = aoff + hp.ublob.size();
+    SV_CUDA(h->gemm.ensure(total));
+    SV_CUDA(h->status.ensure(sizeof(int)));
+    h->gemm_host.assign(total, 0);
+    std::memcpy(h->gemm_host.data(), hp.launches.data(), sb);
+    std::memcpy(h->gemm_host.data() + aoff, hp.ublob.data(), hp.ublob.size());
+    SV_CUDA(cudaMemcpyAsync(h->gemm.p, h->gemm_host.data(), total, cudaMemcpyHostToDevice, h->stream));
+    SV_CUDA(cudaMemsetAsync(h->status.p, 0, sizeof(int), h->stream));
+    for (size_t i = 0; i < hp.launches.size(); ++i) {
+        cudaEvent_t t0 = tick(h);
+        SV_CUDA(svk::launch_hier_stage(prec, h->psi, (const svk::HierStage*)h->gemm.p + i, hp.launches[i],
+                                       (const uint8_t*)h->gemm.p + aoff, (int*)h->status.p, h->stream));
+        tock(h, t0, TK_STAGE);
+        h->info.stage_sweeps += 1;
+        h->info.kernel_launches += 1;
+        h->info.hbm_bytes += 2.0 * (double)state_bytes(h);
+    }
+    if (!hp.identity_map) {
+        std::vector<uint32_t> m(P.n);
+        for (int q = 0; q < P.n; ++q) m[q] = (uint32_t)P.final_map[q];
+        sv_status s = do_permute(h, m.data());
+        if (s) return s;
+    }
+    int st = 0;
+    SV_CUDA(cudaMemcpyAsync(&st, h->status.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    SV_CUDA(cudaStreamSynchronize(h->stream));
+    if (st) return fail(SV_ERR_TIMEOUT, "a hierarchical tensor-core stage gave up waiting for its copies or MMAs");
+    return SV_OK;
+}
+
 static sv_status run_gemm(sv_handle h, const sv_plan* plan, const double* params, int prec) {
     const svh::Plan& P = plan->plan;
     svh::GemmProgram gp;
@@ -935,8 +999,10 @@ sv_status sv_run(sv_handle h, const sv_plan* plan, const double* params, sv_prec
     if (plan->plan.n_params > 0 && !params) return fail(SV_ERR_ARG, "params is NULL");
     h->info = sv_run_info{};
     if (prec == SV_PREC_TF32X3 || prec == SV_PREC_BF16X3) {
-        if (plan->plan.gemm_k == 0) return fail(SV_ERR_UNSUPPORTED, "tensor-core precision needs a plan from sv_partition_gemm");
+        if (plan->plan.gemm_k == 0 && plan->plan.hier_k == 0)
+            return fail(SV_ERR_UNSUPPORTED, "tensor-core precision needs a plan from sv_partition_gemm or sv_partition_hier");
         if (h->dt != SV_C64) return fail(SV_ERR_UNSUPPORTED, "tensor-core stages operate on complex64 states");
+        if (plan->plan.hier_k) return run_hier(h, plan, params, prec == SV_PREC_TF32X3 ? 1 : 2);
         return run_gemm(h, plan, params, prec == SV_PREC_TF32X3 ? 1 : 2);
     }
     if (prec != SV_PREC_CUDACORE) return fail(SV_ERR_ARG, "bad precision");

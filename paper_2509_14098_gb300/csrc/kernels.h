@@ -95,6 +95,12 @@ size_t gemm_smem_bytes(const GemmStage& st);
 cudaError_t launch_gemm_stage(int prec, void* psi, const GemmStage* d_stage, const GemmStage& hst,
                               const uint8_t* d_ablob, int* d_status, cudaStream_t s);
 
+// hierarchical tensor-core stage (hier.h): prec 1 = TF32x3 (k = 5), 2 = BF16x3 (k = 5, 6);
+// d_status receives 1 if a bounded wait gave up
+struct HierStage;
+cudaError_t launch_hier_stage(int prec, void* psi, const HierStage* d_st, const HierStage& hst, const uint8_t* d_ublob,
+                              int* d_status, cudaStream_t s);
+
 // batched circuits (batch.h): one persistent launch of `grid` CTAs
 struct BatchArgs;
 cudaError_t launch_batch(const BatchArgs& a, int grid, cudaStream_t s);

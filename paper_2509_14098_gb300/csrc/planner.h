@@ -67,6 +67,7 @@ struct Plan {
     int L = 0;
     int n_fixed = 0;
     int gemm_k = 0;             // > 0: partitioned without exemptions for tensor-core stages
+    int hier_k = 0;             // > 0: hierarchical tensor-core stages (tiles of hier_k + 7 qubits)
     std::vector<GateRec> gates;
     std::vector<PGate> phys;
     std::vector<int> final_map;

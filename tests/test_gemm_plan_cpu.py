@@ -109,3 +109,33 @@ def test_not_a_tensor_core_plan(N):
         assert N.lib.sv_gemm_plan_info(plan, None, 0, ctypes.byref(ns), None, None, None, None) == N.SV_ERR_ARG
     finally:
         N.lib.sv_plan_destroy(plan)
+
+
+def test_hierarchical_plan_shape(N):
+    """sv_partition_hier: level-1 stages of k + 7 qubits holding 0..3; level 2 packs a
+    stage's gates into k-qubit sub-partitions, so brick32 needs far fewer HBM passes
+    than the flat tensor-core plan (one pass per fused unitary)."""
+    import paper_2509_14098_gb300 as sv
+    circ = C.brickwork(32, 24, 3)
+    for k in (5, 6):
+        plan = sv.Plan(circ, k, hier=True)
+        st = plan.stages()
+        assert all(bin(m).count("1") == k + 7 and m & 15 == 15 for m, _ in st)
+        nl, ns = plan.hier_info(2)
+        flat = sv.Plan(circ, k, gemm=True)
+        assert nl == len(st) < len(flat.stages()) <= ns
+    nl, ns = sv.Plan(circ, 5, hier=True).hier_info(1)
+    assert ns > nl > 0
+
+
+def test_hierarchical_plan_errors(N):
+    import paper_2509_14098_gb300 as sv
+    with pytest.raises(N.SvError):
+        sv.Plan(C.brickwork(16, 2, 1), 7, hier=True)      # k must be 5 or 6
+    with pytest.raises(N.SvError):
+        sv.Plan(C.brickwork(11, 2, 1), 5, hier=True)      # narrower than one tile
+    plan = sv.Plan(C.brickwork(14, 2, 1), 6, hier=True)
+    with pytest.raises(N.SvError):
+        plan.hier_info(1)                                 # TF32x3 needs k = 5
+    with pytest.raises(N.SvError):
+        sv.Plan(C.brickwork(14, 2, 1), 8).hier_info(2)    # not a hierarchical plan
