@@ -38,6 +38,8 @@ struct HierStage {
     uint32_t a_bytes;       // A operand region (nchunk x 32768), also holds the FP32 output tile
     uint64_t b_off;         // byte offset of sub-partition 0's B operand in the blob
     uint8_t tile_pos[16];   // physical position of tile bit b, ascending (bits 0..3 first)
+    uint8_t ld_bits[16];    // load / store: bit i of a thread's 16-byte pair index (thread bits 0..6,
+                            // then round bits) is tile bit ld_bits[i] (tile bits 1..3 first)
     uint8_t glob_pos[kMaxQ];
     uint8_t amp_bits[kHierMaxSub][8];   // sub-partition s: tile bit of amplitude-index bit i
     uint8_t col_bits[kHierMaxSub][8];   // tile bit of row bit i (7 bits)

@@ -18,6 +18,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 
 #include "hier.h"
 #include "tc_util.cuh"
@@ -88,22 +90,24 @@ __global__ void __launch_bounds__(kHT)
         uint32_t a = 0, t = 0;
         for (uint32_t b = 0; b + 8 < T; ++b)
             if ((tid >> b) & 1) {
-                g |= 1ull << st.tile_pos[8 + b];
-                a ^= st.ao[0][8 + b];
-                t ^= st.ao[nsub][8 + b];
+                const uint32_t tb = st.ld_bits[7 + b];
+                g |= 1ull << st.tile_pos[tb];
+                a ^= st.ao[0][tb];
+                t ^= st.ao[nsub][tb];
             }
         s_gr[tid] = g;
         s_ar[tid] = a;
         s_tr[tid] = t;
     }
-    // this thread's part of a pair index: tile bits 1..7 <- thread bits 0..6
+    // this thread's part of a pair index: thread bit b <- tile bit ld_bits[b]
     uint64_t gthr = 0;
     uint32_t athr = 0, tthr = 0;
     for (uint32_t b = 0; b < 7; ++b)
         if ((tid >> b) & 1) {
-            gthr |= 1ull << st.tile_pos[1 + b];
-            athr ^= st.ao[0][1 + b];
-            tthr ^= st.ao[nsub][1 + b];
+            const uint32_t tb = st.ld_bits[b];
+            gthr |= 1ull << st.tile_pos[tb];
+            athr ^= st.ao[0][tb];
+            tthr ^= st.ao[nsub][tb];
         }
     const uint32_t a0b = st.ao[0][0];   // the pair's second amplitude (tile bit 0) in layout 0
     if (tid == 0) {
@@ -290,16 +294,37 @@ cudaError_t launch_one(float2* psi, const HierStage* d_st, const HierStage& hst,
         cudaError_t e = cudaFuncSetAttribute(k_hier_stage<PREC, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              200 * 1024);
         if (e != cudaSuccess) return e;
+        // the whole unified L1 / shared array as shared memory: several CTAs per SM
+        e = cudaFuncSetAttribute(k_hier_stage<PREC, KS>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
         cfg = true;
     }
     if (smem > 200 * 1024) return cudaErrorInvalidConfiguration;
-    int nb = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_hier_stage<PREC, KS>, kHT, smem);
-    if (e != cudaSuccess) return e;
-    const int per_sm = std::max(1, std::min(nb, (int)(512 / (2u << KS))));   // tensor-memory columns: 512 per SM
+    // CTAs per SM from the SM's shared memory (each CTA: dynamic + static + the 1 KB the
+    // driver reserves), registers and threads, capped by tensor memory (512 columns per
+    // SM, N per CTA).  (The occupancy calculator answers 1 here once the kernel's dynamic
+    // shared-memory limit is raised above what one launch uses.)
+    static int smem_sm = 0, reserved = 0, static_smem = 0, regs = 0;
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (!smem_sm) {
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, k_hier_stage<PREC, KS>);
+        if (e != cudaSuccess) return e;
+        static_smem = (int)fa.sharedSizeBytes;
+        regs = std::max(1, fa.numRegs);
+    }
+    int per_sm = smem_sm / (int)(smem + (size_t)static_smem + (size_t)reserved);
+    per_sm = std::min(per_sm, 65536 / (regs * kHT));
+    per_sm = std::min(per_sm, 2048 / kHT);
+    per_sm = std::max(1, std::min(per_sm, (int)(512 / (2u << KS))));
+    if (const char* v = getenv("SVGB_HIER_CTAS")) per_sm = std::max(1, std::min(atoi(v), (int)(512 / (2u << KS))));
+    if (getenv("SVGB_HIER_VERBOSE"))
+        fprintf(stderr, "k_hier_stage<%d,%d>: smem %zu + %d static, CTAs per SM %d\n", PREC, KS, smem, static_smem, per_sm);
     const uint64_t ntiles = 1ull << hst.n_glob;
     const unsigned grid = (unsigned)std::min<uint64_t>(ntiles, (uint64_t)nsm * (uint64_t)per_sm);
     k_hier_stage<PREC, KS><<<grid, kHT, smem, s>>>(psi, d_st, d_ublob, d_status);

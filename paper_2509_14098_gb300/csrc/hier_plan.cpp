@@ -7,6 +7,7 @@
 // each amplitude of the tile goes in every sub-partition's A operand.
 #include <algorithm>
 #include <cstring>
+#include <functional>
 
 #include "gemm.h"
 #include "hier.h"
@@ -89,37 +90,110 @@ std::string plan_hier(const Plan& P, const double* params, int prec, HierProgram
             st.n_glob = (uint32_t)ng;
             st.b_off = (uint64_t)((out->ublob.size() + 1023) & ~(size_t)1023);
             out->ublob.resize(st.b_off + (size_t)st.n_sub * b_bytes, 0);
-            for (size_t g = g0; g < g1; ++g) {
-                const int sl = (int)(g - g0);
-                uint64_t loc = groups.local[g];
+            const int S = (int)st.n_sub;
+            std::vector<std::vector<int>> cols(S);
+            for (int sl = 0; sl < S; ++sl) {
+                uint64_t loc = groups.local[g0 + (size_t)sl];
                 // widen to exactly k qubits with identity qubits of the tile
                 for (int t = 0; t < T && __builtin_popcountll(loc) < k; ++t) loc |= 1ull << tpos[t];
-                int lp[8], na = 0, nc = 0;
+                int na = 0;
                 for (int t = 0; t < T; ++t) {
-                    if ((loc >> tpos[t]) & 1) {
-                        lp[na] = tpos[t];
-                        st.amp_bits[sl][na++] = (uint8_t)t;
-                    } else {
-                        st.col_bits[sl][nc++] = (uint8_t)t;
+                    if ((loc >> tpos[t]) & 1) st.amp_bits[sl][na++] = (uint8_t)t;
+                    else cols[sl].push_back(t);
+                }
+                if (na != k || cols[sl].size() != 7) return "internal: sub-partition shape";
+                // layout sl: amplitude bit i -> (K chunk, position in the row)
+                for (int i = 0; i < k; ++i)
+                    st.ao[sl][st.amp_bits[sl][i]] = i < camp ? a_offset(tf32, 1u << i, 0) : (32768u << (i - camp));
+            }
+            // the output tile's layout (pairs adjacent, bits 5.. folded onto 1..3)
+            for (int t = 0; t < T; ++t) {
+                const uint32_t x = 1u << t;
+                st.ao[S][t] = 8u * (x ^ (((x >> 4) ^ (x >> 8)) & 14u));
+            }
+            // Row order of each layout, last to first.  The epilogue of sub-partition s has
+            // thread m write row m's amplitudes into layout s + 1, so the lanes of a warp
+            // are rows 0..4 of layout s: they take the column bits whose shared-memory bank
+            // images in layout s + 1 are independent (4-byte stores: bank bits 0..4 over 32
+            // lanes; 8-byte stores: bits 1..4 over a half warp), so the stores do not
+            // conflict where the sub-partitions allow it.
+            for (int sl = S - 1; sl >= 0; --sl) {
+                const int L = sl + 1;
+                const bool wide = tf32 || L == S;   // 8-byte stores into layout L
+                const uint32_t bmask = wide ? 0x1Eu : 0x1Fu;
+                const int nl = wide ? 4 : 5;
+                std::vector<int> order, rest = cols[sl];
+                std::vector<uint32_t> basis;
+                auto reduce = [&](uint32_t x) {
+                    for (uint32_t bv : basis) x = std::min(x, x ^ bv);
+                    return x;
+                };
+                for (int lane = 0; lane < nl; ++lane) {
+                    size_t pick = rest.size();
+                    for (size_t i = 0; i < rest.size(); ++i)
+                        if (reduce((st.ao[L][rest[i]] >> 2) & bmask)) {
+                            pick = i;
+                            break;
+                        }
+                    if (pick == rest.size()) break;
+                    basis.push_back(reduce((st.ao[L][rest[pick]] >> 2) & bmask));
+                    std::sort(basis.begin(), basis.end(), std::greater<uint32_t>());
+                    order.push_back(rest[pick]);
+                    rest.erase(rest.begin() + (long)pick);
+                }
+                order.insert(order.end(), rest.begin(), rest.end());
+                for (int i = 0; i < 7; ++i) {
+                    st.col_bits[sl][i] = (uint8_t)order[i];
+                    st.ao[sl][order[i]] = a_offset(tf32, 0, 1u << i);
+                }
+            }
+            // Load / store mapping: pair-index bits 0..2 are tile bits 1..3 (a warp's loads
+            // cover 128-byte runs); bits 3, 4 (the other lanes of a warp) take the tile bits
+            // whose layout-0 bank images extend those of tile bits 1..3, so the split
+            // amplitudes' stores into sub-partition 0's operand conflict as little as they can.
+            {
+                const uint32_t bmask = tf32 ? 0x1Eu : 0x1Fu;
+                std::vector<uint32_t> basis;
+                auto reduce = [&](uint32_t x) {
+                    for (uint32_t bv : basis) x = std::min(x, x ^ bv);
+                    return x;
+                };
+                std::vector<int> order = {1, 2, 3}, rest;
+                for (int t = 4; t < T; ++t) rest.push_back(t);
+                for (int t : order) {
+                    const uint32_t r = reduce((st.ao[0][t] >> 2) & bmask);
+                    if (r) {
+                        basis.push_back(r);
+                        std::sort(basis.begin(), basis.end(), std::greater<uint32_t>());
                     }
                 }
-                if (na != k || nc != 7) return "internal: sub-partition shape";
-                // layout sl: amplitude bit i -> (chunk, position in the row), row bit i -> row
-                for (int i = 0; i < k; ++i)
-                    st.ao[sl][st.amp_bits[sl][i]] =
-                        i < camp ? a_offset(tf32, 1u << i, 0) : (32768u << (i - camp));
-                for (int i = 0; i < 7; ++i) st.ao[sl][st.col_bits[sl][i]] = a_offset(tf32, 0, 1u << i);
+                for (int lane = 3; lane < 5; ++lane) {
+                    size_t pick = 0;
+                    for (size_t i = 0; i < rest.size(); ++i)
+                        if (reduce((st.ao[0][rest[i]] >> 2) & bmask)) {
+                            pick = i;
+                            break;
+                        }
+                    const uint32_t r = reduce((st.ao[0][rest[pick]] >> 2) & bmask);
+                    if (r) {
+                        basis.push_back(r);
+                        std::sort(basis.begin(), basis.end(), std::greater<uint32_t>());
+                    }
+                    order.push_back(rest[pick]);
+                    rest.erase(rest.begin() + (long)pick);
+                }
+                order.insert(order.end(), rest.begin(), rest.end());
+                for (int i = 0; i < T - 1; ++i) st.ld_bits[i] = (uint8_t)order[i];
+            }
+            for (int sl = 0; sl < S; ++sl) {
+                int lp[8];
+                for (int i = 0; i < k; ++i) lp[i] = tpos[st.amp_bits[sl][i]];
                 std::vector<uint32_t> gid;
-                for (uint32_t x : groups.ids[g]) gid.push_back(ids[x]);
+                for (uint32_t x : groups.ids[g0 + (size_t)sl]) gid.push_back(ids[x]);
                 std::vector<std::complex<double>> U;
                 err = fuse_unitary(P, gid, lp, k, params, &U);
                 if (!err.empty()) return err;
                 emit_b(U, k, tf32, out->ublob.data() + st.b_off + (size_t)sl * b_bytes);
-            }
-            // the output tile's layout
-            for (int t = 0; t < T; ++t) {
-                const uint32_t x = 1u << t;
-                st.ao[st.n_sub][t] = 8u * (x ^ (((x >> 4) ^ (x >> 8)) & 14u));
             }
             out->n_sub += st.n_sub;
             out->launches.push_back(st);
