@@ -36,6 +36,8 @@ struct HierStage {
     uint32_t n_glob;        // tile-index bits
     uint32_t b_bytes;       // B operand of one sub-partition: nchunk x (hi, lo) blocks of N x 128 bytes
     uint32_t a_bytes;       // A operand region (nchunk x 32768), also holds the FP32 output tile
+    uint32_t b_slots;       // B operand buffers in shared memory (1 or 2)
+    uint32_t reserved;
     uint64_t b_off;         // byte offset of sub-partition 0's B operand in the blob
     uint8_t tile_pos[16];   // physical position of tile bit b, ascending (bits 0..3 first)
     uint8_t ld_bits[16];    // load / store: bit i of a thread's 16-byte pair index (thread bits 0..6,

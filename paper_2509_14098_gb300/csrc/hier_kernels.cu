@@ -1,6 +1,6 @@
 // hier_kernels.cu — the hierarchical tensor-core stage (hier.h), sm_103a.
 //
-// One CTA of 128 threads per tile of T = k + 7 qubits, persistent over the tiles, several
+// One CTA of 256 threads per tile of T = k + 7 qubits, persistent over the tiles, several
 // CTAs per SM (their phases interleave on the SM's tensor core and memory pipes):
 //  1. the tile's 2^T amplitudes are read from HBM once (16-byte pairs: qubits 0..3 are
 //     tile bits, so a warp reads whole 128-byte runs), split into hi / lo halves and
@@ -8,8 +8,8 @@
 //  2. per sub-partition s: one thread issues the 3 x (K / 32 bytes) tcgen05.mma of
 //     D = Ahi Bhi + Alo Bhi + Ahi Blo into tensor memory and commits them; the B operand
 //     (the fused unitary, pre-split by the host) arrives by one bulk copy that is issued
-//     as soon as the previous sub-partition's MMAs are done; every thread then reads its
-//     row of D (tcgen05.ld) and stores it, split again, as sub-partition s + 1's A
+//     as soon as the previous sub-partition's MMAs are done; every thread then reads half
+//     a row of D (tcgen05.ld) and stores it, split again, as sub-partition s + 1's A
 //     operand, or after the last one into the FP32 output tile (same shared memory);
 //  3. the tile is written back to HBM once.
 // Every wait is bounded: on time-out the kernel raises the status flag, waits (bounded)
@@ -28,7 +28,7 @@ namespace svk {
 
 namespace {
 
-constexpr int kHT = 128;                 // threads: one per A row / tensor-memory lane
+constexpr int kHT = 256;                 // threads: two per A row / tensor-memory lane (each half the columns)
 constexpr uint32_t kHWait = 1u << 22;    // polls of a bounded wait
 
 // an amplitude (re, im) split into hi / lo halves at A offset o (lo 16384 bytes above)
@@ -47,19 +47,19 @@ __device__ __forceinline__ void put_amp(unsigned char* A, uint32_t o, float re, 
 }
 
 template <int PREC, int KS>
-__global__ void __launch_bounds__(kHT)
+__global__ void __launch_bounds__(kHT, 4)
     k_hier_stage(float2* __restrict__ psi, const HierStage* __restrict__ stp, const uint8_t* __restrict__ ublob,
                  int* __restrict__ status) {
     constexpr uint32_t T = KS + 7, N = 2u << KS, K2 = 1u << KS;
     constexpr uint32_t CAMP = PREC == 1 ? 4 : 5;                 // log2 amplitudes per K chunk
     constexpr uint32_t NCHUNK = 1u << (KS - CAMP);
-    constexpr uint32_t NROUND = 1u << (T - 8);                  // 16-byte pairs per thread
+    constexpr uint32_t NROUND = 1u << (T - 9);                  // 16-byte pairs per thread
     constexpr uint32_t A_BYTES = NCHUNK * 32768, B_BYTES = NCHUNK * 2 * N * 128;
     extern __shared__ unsigned char sm_raw[];
     __shared__ HierStage s_st;
-    __shared__ uint64_t s_gr[NROUND];                           // round -> physical offset (tile bits 8..)
+    __shared__ uint64_t s_gr[NROUND];                           // round -> physical offset
     __shared__ uint32_t s_ar[NROUND], s_tr[NROUND];             // round -> layout-0 / output-tile offset
-    __shared__ __align__(8) uint64_t bar_b, bar_mma, bar_fin;
+    __shared__ __align__(8) uint64_t bar_b[2], bar_mma, bar_fin;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int s_fail;
     static_assert(sizeof(HierStage) % 4 == 0, "stage copy");
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(kHT)
     const uint32_t sbase = (smem_u32(sm_raw) + 1023u) & ~1023u;
     unsigned char* const Ab = sm_raw + (sbase - smem_u32(sm_raw));
     const uint32_t Aaddr = sbase, Baddr = sbase + A_BYTES;
-    uint32_t* const oj = reinterpret_cast<uint32_t*>(Ab + A_BYTES + B_BYTES);   // [nsub][2^k]
+    uint32_t* const oj = reinterpret_cast<uint32_t*>(Ab + A_BYTES + st.b_slots * B_BYTES);   // [nsub][2^k]
 
     // amplitude-offset tables: oj[s][j] = XOR over the bits of j of the next layout's term
     // of sub-partition s's amplitude bit
@@ -88,9 +88,9 @@ __global__ void __launch_bounds__(kHT)
     if (tid < NROUND) {
         uint64_t g = 0;
         uint32_t a = 0, t = 0;
-        for (uint32_t b = 0; b + 8 < T; ++b)
+        for (uint32_t b = 0; b + 9 < T; ++b)
             if ((tid >> b) & 1) {
-                const uint32_t tb = st.ld_bits[7 + b];
+                const uint32_t tb = st.ld_bits[8 + b];
                 g |= 1ull << st.tile_pos[tb];
                 a ^= st.ao[0][tb];
                 t ^= st.ao[nsub][tb];
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kHT)
     // this thread's part of a pair index: thread bit b <- tile bit ld_bits[b]
     uint64_t gthr = 0;
     uint32_t athr = 0, tthr = 0;
-    for (uint32_t b = 0; b < 7; ++b)
+    for (uint32_t b = 0; b < 8; ++b)
         if ((tid >> b) & 1) {
             const uint32_t tb = st.ld_bits[b];
             gthr |= 1ull << st.tile_pos[tb];
@@ -111,7 +111,8 @@ __global__ void __launch_bounds__(kHT)
         }
     const uint32_t a0b = st.ao[0][0];   // the pair's second amplitude (tile bit 0) in layout 0
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_b)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_b[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_b[1])));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_mma)));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_fin)));
     }
@@ -128,19 +129,25 @@ __global__ void __launch_bounds__(kHT)
     const uint32_t tmem = tmem_slot;
     const uint64_t ntiles = 1ull << st.n_glob;
 
-    // B operand of sub-partition s: one bulk copy completing on bar_b (thread 0 only)
-    uint32_t nb = 0;          // bulk copies issued
-    bool b_pending = false;   // a copy whose completion the MMA issue has not yet seen
-    int b_loaded = -1;        // sub-partition whose B operand the buffer holds
-    auto load_b = [&](uint32_t s) {
-        const uint32_t bar = smem_u32(&bar_b);
+    // B operands in st.b_slots buffers (thread 0 manages them).  When the launch's
+    // sub-partitions fit, each keeps its own buffer for the whole launch (one copy per
+    // CTA).  Otherwise MMA group g (sub-partition g mod n_sub) uses buffer g mod b_slots:
+    // with two buffers the copy for group g + 1 is issued just before group g's MMAs (its
+    // buffer's previous group has completed), with one after group g's MMAs complete.
+    const uint32_t NBS = st.b_slots;
+    const bool resident = nsub <= NBS;
+    uint32_t nload0 = 0, nload1 = 0;   // copies issued per buffer
+    uint32_t pendm = 0;                // buffers with a copy not yet waited for (bit mask)
+    auto load_b = [&](uint32_t slot, uint32_t s) {
+        const uint32_t bar = smem_u32(&bar_b[slot]);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(B_BYTES) : "memory");
         asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                     ::"r"(Baddr), "l"(ublob + st.b_off + (size_t)s * B_BYTES), "r"(B_BYTES), "r"(bar)
+                     ::"r"(Baddr + slot * B_BYTES), "l"(ublob + st.b_off + (size_t)s * B_BYTES), "r"(B_BYTES),
+                     "r"(bar)
                      : "memory");
-        ++nb;
-        b_pending = true;
-        b_loaded = (int)s;
+        if (slot) ++nload1;
+        else ++nload0;
+        pendm |= 1u << slot;
     };
     // bounded wait; gives up at once when another thread already failed
     auto wait = [&](uint64_t& bar, uint32_t parity) -> bool {
@@ -153,7 +160,12 @@ __global__ void __launch_bounds__(kHT)
         return false;
     };
     uint32_t nm = 0;          // MMA groups committed (every thread counts them)
-    if (tid == 0 && (uint64_t)blockIdx.x < ntiles) load_b(0);
+    if (tid == 0 && (uint64_t)blockIdx.x < ntiles) {
+        if (resident)
+            for (uint32_t s = 0; s < nsub; ++s) load_b(s, s);
+        else
+            load_b(0, 0);
+    }
 
     bool ok = true;
     for (uint64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
@@ -178,12 +190,12 @@ __global__ void __launch_bounds__(kHT)
         for (uint32_t s = 0; s < nsub; ++s) {
             if (tid == 0) {
                 bool go = !s_fail;
-                if (go && b_loaded != (int)s) {   // only a single-sub-partition launch keeps B across tiles
-                    load_b(s);
-                }
-                if (go && b_pending) {
-                    go = wait(bar_b, (nb - 1) & 1u);
-                    b_pending = false;
+                const uint32_t slot = resident ? s : nm % NBS;
+                if (go && !resident && NBS == 2 && (s + 1 < nsub || t + gridDim.x < ntiles))
+                    load_b((nm + 1) % NBS, (s + 1) % nsub);   // the next group's operand
+                if (go && ((pendm >> slot) & 1u)) {
+                    go = wait(bar_b[slot], ((slot ? nload1 : nload0) - 1) & 1u);
+                    pendm &= ~(1u << slot);
                 }
                 if (go) {
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -193,7 +205,7 @@ __global__ void __launch_bounds__(kHT)
 #pragma unroll
                         for (int p = 0; p < 3; ++p) {   // hi*hi, lo*hi, hi*lo
                             const uint32_t As = Aaddr + c * 32768u + (p == 1 ? 16384u : 0u);
-                            const uint32_t Bs = Baddr + c * (2u * N * 128u) + (p == 2 ? N * 128u : 0u);
+                            const uint32_t Bs = Baddr + slot * B_BYTES + c * (2u * N * 128u) + (p == 2 ? N * 128u : 0u);
 #pragma unroll
                             for (int q = 0; q < 4; ++q) {
                                 const uint64_t da = mdesc(As + 32u * q), db = mdesc(Bs + 32u * q);
@@ -220,23 +232,24 @@ __global__ void __launch_bounds__(kHT)
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            // the next B operand streams in while this one's results are read out (after the
-            // last sub-partition: sub-partition 0's, for this CTA's next tile)
-            if (tid == 0) {
-                if (s + 1 < nsub) load_b(s + 1);
-                else if (nsub > 1 && t + gridDim.x < ntiles) load_b(0);
-            }
-            // epilogue: row m = tid of D, stored through the next layout
+            // one buffer: the next group's operand streams in while this one's results are
+            // read out
+            if (tid == 0 && !resident && NBS == 1 && (s + 1 < nsub || t + gridDim.x < ntiles)) load_b(0, (s + 1) % nsub);
+            // epilogue: row m of D (warp w reads tensor-memory lanes 32 (w & 3) ..; warps
+            // 0..3 take the first half of the columns, 4..7 the second), stored through the
+            // next layout
             const bool last = s + 1 == nsub;
             const uint32_t L = s + 1;
+            const uint32_t m = 32u * (warp & 3u) + (tid & 31u), nh = (warp >> 2) * (N / 2);
             uint32_t om = 0;
             for (uint32_t i = 0; i < 7; ++i)
-                if ((tid >> i) & 1) om ^= st.ao[L][st.col_bits[s][i]];
+                if ((m >> i) & 1) om ^= st.ao[L][st.col_bits[s][i]];
             const uint32_t* ojs = oj + s * K2;
 #pragma unroll
-            for (uint32_t n0 = 0; n0 < N; n0 += 32) {
+            for (uint32_t n1 = 0; n1 < N / 2; n1 += 32) {
+                const uint32_t n0 = nh + n1;
                 uint32_t r[32];
-                const uint32_t taddr = tmem + ((32u * warp) << 16) + n0;
+                const uint32_t taddr = tmem + ((32u * (warp & 3u)) << 16) + n0;
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
                     "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
@@ -274,9 +287,11 @@ __global__ void __launch_bounds__(kHT)
         mma_commit(smem_u32(&bar_fin));
         for (uint32_t it = 0; it < kHWait && !mbar_test(smem_u32(&bar_fin), 0); ++it) {
         }
-        if (b_pending)
-            for (uint32_t it = 0; it < kHWait && !mbar_test(smem_u32(&bar_b), (nb - 1) & 1u); ++it) {
-            }
+        for (uint32_t sl = 0; sl < 2; ++sl)
+            if ((pendm >> sl) & 1u)
+                for (uint32_t it = 0; it < kHWait && !mbar_test(smem_u32(&bar_b[sl]), ((sl ? nload1 : nload0) - 1) & 1u);
+                     ++it) {
+                }
         atomicExch(status, 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -292,7 +307,7 @@ cudaError_t launch_one(float2* psi, const HierStage* d_st, const HierStage& hst,
     static bool cfg = false;
     if (!cfg) {
         cudaError_t e = cudaFuncSetAttribute(k_hier_stage<PREC, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             200 * 1024);
+                                             220 * 1024);
         if (e != cudaSuccess) return e;
         // the whole unified L1 / shared array as shared memory: several CTAs per SM
         e = cudaFuncSetAttribute(k_hier_stage<PREC, KS>, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -300,7 +315,7 @@ cudaError_t launch_one(float2* psi, const HierStage* d_st, const HierStage& hst,
         if (e != cudaSuccess) return e;
         cfg = true;
     }
-    if (smem > 200 * 1024) return cudaErrorInvalidConfiguration;
+    if (smem > 220 * 1024) return cudaErrorInvalidConfiguration;
     // CTAs per SM from the SM's shared memory (each CTA: dynamic + static + the 1 KB the
     // driver reserves), registers and threads, capped by tensor memory (512 columns per
     // SM, N per CTA).  (The occupancy calculator answers 1 here once the kernel's dynamic

@@ -28,8 +28,8 @@ uint32_t a_offset(bool tf32, uint32_t jj, uint32_t m) {
 }  // namespace
 
 size_t hier_smem_bytes(const svk::HierStage& st) {
-    // 1024 (alignment) + A region + B operand + per-sub-partition amplitude-offset tables
-    return 1024 + (size_t)st.a_bytes + st.b_bytes + (size_t)st.n_sub * (1u << st.k) * 4;
+    // 1024 (alignment) + A region + B buffers + per-sub-partition amplitude-offset tables
+    return 1024 + (size_t)st.a_bytes + (size_t)st.b_slots * st.b_bytes + (size_t)st.n_sub * (1u << st.k) * 4;
 }
 
 std::string plan_hier(const Plan& P, const double* params, int prec, HierProgram* out) {
@@ -83,6 +83,10 @@ std::string plan_hier(const Plan& P, const double* params, int prec, HierProgram
             st.n_sub = (uint32_t)(g1 - g0);
             st.b_bytes = b_bytes;
             st.a_bytes = nchunk * 32768;
+            // one B buffer: a second one (the next operand's copy overlapping this one's
+            // GEMM) measured no faster at BF16x3 k = 5 (it costs a CTA per SM) and slower
+            // at TF32x3 k = 5
+            st.b_slots = 1;
             for (int t = 0; t < T; ++t) st.tile_pos[t] = (uint8_t)tpos[t];
             int ng = 0;
             for (int b = 0; b < n; ++b)
@@ -117,8 +121,23 @@ std::string plan_hier(const Plan& P, const double* params, int prec, HierProgram
             // images in layout s + 1 are independent (4-byte stores: bank bits 0..4 over 32
             // lanes; 8-byte stores: bits 1..4 over a half warp), so the stores do not
             // conflict where the sub-partitions allow it.
+            // Amplitude order of a layout: amplitude bits 0..4 are the only terms that reach
+            // bank bits 0 and 1, so the amplitude bits that are lanes of the writing epilogue
+            // (column bits of the sub-partition before) come first.
+            auto amp_first = [&](int L, const std::vector<int>& pref) {
+                std::vector<int> a(st.amp_bits[L], st.amp_bits[L] + k), o;
+                for (int t : a)
+                    if (std::find(pref.begin(), pref.end(), t) != pref.end()) o.push_back(t);
+                for (int t : a)
+                    if (std::find(pref.begin(), pref.end(), t) == pref.end()) o.push_back(t);
+                for (int i = 0; i < k; ++i) {
+                    st.amp_bits[L][i] = (uint8_t)o[i];
+                    st.ao[L][o[i]] = i < camp ? a_offset(tf32, 1u << i, 0) : (32768u << (i - camp));
+                }
+            };
             for (int sl = S - 1; sl >= 0; --sl) {
                 const int L = sl + 1;
+                if (L < S) amp_first(L, cols[sl]);
                 const bool wide = tf32 || L == S;   // 8-byte stores into layout L
                 const uint32_t bmask = wide ? 0x1Eu : 0x1Fu;
                 const int nl = wide ? 4 : 5;
@@ -147,6 +166,7 @@ std::string plan_hier(const Plan& P, const double* params, int prec, HierProgram
                     st.ao[sl][order[i]] = a_offset(tf32, 0, 1u << i);
                 }
             }
+            amp_first(0, {1, 2, 3});   // the loads' lanes 0..2 are tile bits 1..3
             // Load / store mapping: pair-index bits 0..2 are tile bits 1..3 (a warp's loads
             // cover 128-byte runs); bits 3, 4 (the other lanes of a warp) take the tile bits
             // whose layout-0 bank images extend those of tile bits 1..3, so the split
