@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--L", type=int, default=L_BUDGET)
     ap.add_argument("--n", type=int, default=N_QUBITS)
     ap.add_argument("--grad-n", type=int, default=28)
-    ap.add_argument("--grad-L", type=int, default=12)
+    ap.add_argument("--grad-L", type=int, default=11)
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, grad ratio, batch and CPU baseline")
     ap.add_argument("--part", default="all", choices=["all", "batch", "gemm", "aux", "grad"],
                     help="batch / gemm / aux: only that section (for profiling)")

@@ -141,7 +141,7 @@ class Gen {
     bool ttab = false;        // per-(slot, thread) thread-bit angle table in shared memory
     bool cbank = false;       // per-op constants read from the parameter bank (else shared memory)
     bool tma = false;         // tiles staged by TMA (128-byte swizzle) instead of cp.async (software swizzle)
-    int NS = 2;               // TMA ring slots
+    int NS = 2;               // TMA ring slots (set in run())
     uint32_t swz(uint32_t e) const { return tma ? (e ^ (((e >> 4) & 7u) << 1)) : svk::swizzle8(e); }
     std::vector<std::vector<int>> tbo;   // per group: tile bit of each thread bit
     int BM = 0, ZI = 0;       // batched over circuits; first stage starts from |0...0>
@@ -461,6 +461,10 @@ std::string Gen::run() {
     const bool OUTP = V.dst != nullptr;
     if (OUTP && (NV != 1 || V.batched)) return "jit: an out-of-place permuted write-back needs a forward stage";
     tma = !V.batched && !OUTP && tma_runs(st, n, NV, &dims);
+    // ring depth: one slot per CTA for the adjoint (psi and lambda tiles: a second slot
+    // would take the shared memory of the SM's second CTA; measured HEA28 backward 92.3 ->
+    // 82.5 ms), two otherwise
+    NS = NV == 2 ? 1 : 2;
     if (const char* e = getenv("SVGB_JIT_NS")) NS = std::max(1, std::min(4, atoi(e)));
     if (tma) {   // coordinates of a tile along each dimension: (tile index >> shift) & mask
         B->tma = true;
