@@ -1,12 +1,15 @@
 """sv_norm_noalloc: the norm reduction for callers that cannot allocate device memory
 (their memory belongs to their own allocator, or an allocation's implicit device
 synchronisation is not acceptable where they call).  Its partial sums live in a static
-device array; it must agree with sv_norm, the allocating entry point, on consecutive
-calls (the shared array keeps the previous call's contents)."""
+device array; it must agree with the oracle's ||psi||^2 (complex128, on the host copy of
+the same state) and with sv_norm, the allocating entry point, on consecutive calls (the
+shared array keeps the previous call's contents)."""
 import ctypes
 
 import numpy as np
 import pytest
+
+from oracle import observables as O
 
 pytestmark = pytest.mark.gpu
 
@@ -42,11 +45,13 @@ def test_noalloc_norm_matches_sv_norm(sv, dtype):
         psi = _state(n, dtype, seed, scale)
         st = sv.StateVector(n, dtype, tensor=psi)
         ref = st.norm()
+        oref = O.norm2(psi.cpu().numpy().astype(np.complex128))
         N.check(N.lib.sv_norm_noalloc(ctypes.c_void_p(psi.data_ptr()), n, dtype, ctypes.c_void_p(stream),
                                       ctypes.c_void_p(out.data_ptr())))
         torch.cuda.synchronize()
         got = float(out.item())
         assert abs(got - ref) <= tol * max(1.0, abs(ref)), (n, got, ref)
+        assert abs(got - oref) <= tol * max(1.0, abs(oref)), (n, got, oref)
         st.close()
 
 
