@@ -139,3 +139,12 @@ def test_hierarchical_plan_errors(N):
         plan.hier_info(1)                                 # TF32x3 needs k = 5
     with pytest.raises(N.SvError):
         sv.Plan(C.brickwork(14, 2, 1), 8).hier_info(2)    # not a hierarchical plan
+
+
+def test_hierarchical_long_stage_takes_several_launches(N):
+    """A stage with more than 24 sub-partitions is split into launches of at most 24."""
+    import paper_2509_14098_gb300 as sv
+    circ = C.Circuit(14, C.random_circuit(12, 700, 3).gates)
+    plan = sv.Plan(circ, 5, hier=True)
+    nl, ns = plan.hier_info(2)
+    assert len(plan.stages()) == 1 and ns > 24 and nl == (ns + 23) // 24

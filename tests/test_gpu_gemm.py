@@ -296,3 +296,16 @@ def test_brick26_vs_oracle_hier(sv, brick26, brick26_c128, prec, k):
           f"max_sample_err={samp:.3e} max_Z_err={zerr:.3e} bound={bound:.3e} target=2e-5")
     assert err <= bound, (err, bound)
     assert samp <= bound and zerr <= 2 * bound
+
+
+@pytest.mark.parametrize("prec,k", [(2, 5), (1, 5)])
+def test_hier_stage_over_several_launches(sv, prec, k):
+    """One stage of 12 qubits holding more than 24 sub-partitions (700 random gates on
+    qubits 0..11 of a 14-qubit state) runs as two launches over the same tiles."""
+    n = 14
+    circ = C.Circuit(n, C.random_circuit(12, 700, 3).gates)
+    psi0 = C.random_state(n, 12)
+    got, plan, st = _run_hier(sv, circ, k, prec, psi0.astype(np.complex64))
+    assert len(plan.stages()) == 1 and plan.hier_info(prec)[0] == 2
+    ref = S.simulate(circ, None, psi0.astype(np.complex64).astype(np.complex128))
+    assert np.linalg.norm(got - ref) <= hier_bound(plan, prec, k)

@@ -216,7 +216,7 @@ def test_fused_output_permutation_lowering(emu, tmp_path, case, n, L):
 
 
 @pytest.mark.parametrize("prec,k", [(2, 5), (2, 6), (1, 5)])
-@pytest.mark.parametrize("case", ["brick", "qft", "random"])
+@pytest.mark.parametrize("case", ["brick", "qft", "random", "long"])
 def test_hierarchical_plan(emu, tmp_path, prec, k, case):
     """Tiles of k + 7 qubits, each stage partitioned again into k-qubit sub-partitions
     applied as split-precision GEMMs (Sec. 4.2's recursive partitioning): the emulated
@@ -226,7 +226,8 @@ def test_hierarchical_plan(emu, tmp_path, prec, k, case):
     give four tiles per stage."""
     n = k + 9
     circ = {"brick": lambda: C.brickwork(n, 8, 3), "qft": lambda: C.qft(n),
-            "random": lambda: C.random_circuit(n, 150, 11)}[case]()
+            "random": lambda: C.random_circuit(n, 150, 11),
+            "long": lambda: C.Circuit(n, C.random_circuit(12, 700, 3).gates)}[case]()   # > 24 sub-partitions
     psi0 = C.random_state(n, 5)
     ref = S.simulate(circ, None, psi0)
     n_sub, got = run_emu(emu, tmp_path, circ, k + 7, 4, None, psi0, 8, rmax=prec, hier=True)
