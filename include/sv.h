@@ -320,10 +320,11 @@ sv_status sv_run(sv_handle h, const sv_plan* plan, const double* params, sv_prec
 sv_status sv_permute(sv_handle h, const uint32_t* phys_of_qubit);
 
 /* <psi|O|psi> for a Pauli sum (Sec. 4.2's observable, evaluated by Pauli sweeps:
- * one read of psi per group of X/Y-carrying terms whose X/Y qubits fit one 12-qubit
- * tile together with qubits 0..3; the diagonal terms join the first sweep).  Each
- * term's X/Y factors must fit such a tile: for states of more than 12 qubits at most
- * 8 X/Y factors outside qubits 0..3 (physical positions), else SV_ERR_UNSUPPORTED.  Reduction: complex64 states sum in FP32 over
+ * one read of psi per group of X/Y-carrying terms whose X/Y qubits fit one tile of 13
+ * (complex64) or 12 (complex128) qubits together with qubits 0..3; the diagonal terms
+ * join the first sweep).  Each term's X/Y factors must fit such a tile: for wider states
+ * at most 9 (complex64) or 8 (complex128) X/Y factors outside qubits 0..3 (physical
+ * positions), else SV_ERR_UNSUPPORTED.  Reduction: complex64 states sum in FP32 over
  * one thread's 16 amplitudes per tile, compensated FP32 across its tiles, FP64 across
  * threads and CTAs in a fixed order; complex128 states sum in FP64.  Result written
  * to *out (host); synchronises.  Errors: SV_ERR_ARG (width mismatch, null or invalid

@@ -315,7 +315,8 @@ static sv_status plan_pauli(int n, int eb, const sv_observable* obs, const std::
         if (__builtin_popcountll(x & z) & 1) { fr = -fr; fi = -fi; }   // (-1)^{|x & z|}
         (x ? off : diag).push_back(Raw{x, z, fr, fi});
     }
-    const int T = std::min(n, 12);
+    // tiles of 13 qubits for complex64 (512 threads x 16 amplitudes), 12 for complex128
+    const int T = std::min(n, eb == 8 ? 13 : 12);
     const int L = std::min(4, T - 1);
     const int R = std::min(eb == 8 ? 4 : 3, T - L);
     std::vector<char> used(off.size(), 0);

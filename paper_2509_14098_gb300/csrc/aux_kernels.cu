@@ -195,8 +195,10 @@ __device__ __forceinline__ void pauli_diag(const PauliTerm* __restrict__ tl, uin
 
 // L4: the tile's low part is 4 bits (every state of 5 or more qubits); otherwise L is
 // read from the sweep (tiny states, one register bit)
-template <typename Real, int R, bool L4>
-__global__ void __launch_bounds__(sizeof(Real) == 4 ? 256 : 512, sizeof(Real) == 4 ? 2 : 1) k_pauli(
+// NT: threads per CTA at most (256: two CTAs per SM; 512: one, for complex128 and for
+// complex64 tiles of 13 qubits)
+template <typename Real, int R, bool L4, int NT>
+__global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) k_pauli(
     const typename CT<Real>::C* __restrict__ psi, typename CT<Real>::C* __restrict__ lam, int accumulate,
     const PauliSweep* __restrict__ sp, const PauliTerm* __restrict__ terms, double* __restrict__ partial,
     uint64_t ntiles) {
@@ -218,7 +220,7 @@ __global__ void __launch_bounds__(sizeof(Real) == 4 ? 256 : 512, sizeof(Real) ==
     C* buf0 = reinterpret_cast<C*>(smem_raw);
     C* buf1 = buf0 + telems;
     // static diagonal, [k][thread] with a fixed row stride (the widest CTA)
-    constexpr uint32_t WS = sizeof(Real) == 4 ? 256 : 512;
+    constexpr uint32_t WS = NT;
     Real* wtab = reinterpret_cast<Real*>(buf1 + telems);
     auto phys = [&](uint32_t e) -> uint64_t {
         uint64_t p = 0;
@@ -406,28 +408,29 @@ __global__ void __launch_bounds__(sizeof(Real) == 4 ? 256 : 512, sizeof(Real) ==
     }
 }
 
-template <typename Real, int R, bool L4>
+template <typename Real, int R, bool L4, int NT>
 struct PauliCfg {
     // two tile buffers and the static-diagonal table
     static size_t smem(int T) {
-        return ((size_t)sizeof(typename CT<Real>::C) << (T + 1)) + (size_t)sizeof(Real) * (1u << R) * (sizeof(Real) == 4 ? 256 : 512);
+        return ((size_t)sizeof(typename CT<Real>::C) << (T + 1)) + (size_t)sizeof(Real) * (1u << R) * NT;
     }
     static uint32_t grid(int T, uint64_t ntiles) {
-        static int per_sm[13] = {0};
+        static int per_sm[14] = {0};
         static int nsm = 0;
         if (!nsm) {
             int dev = 0, m = 0;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, dev);
             // the widest tile's two buffers (the kernel's static shared memory comes on top)
-            if (cudaFuncSetAttribute(k_pauli<Real, R, L4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem(12)) !=
+            if (cudaFuncSetAttribute(k_pauli<Real, R, L4, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem(NT == 512 && sizeof(Real) == 4 ? 13 : 12)) !=
                 cudaSuccess)
                 return 0;
             nsm = m;
         }
         if (!per_sm[T]) {
             int nb = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pauli<Real, R, L4>, 1 << (T - R), smem(T));
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pauli<Real, R, L4, NT>, 1 << (T - R), smem(T));
             per_sm[T] = nb > 0 ? nb : 1;
         }
         const uint64_t g = (uint64_t)nsm * (uint64_t)per_sm[T];
@@ -441,7 +444,7 @@ struct PauliCfg {
         const uint32_t g = grid(T, ntiles);
         *grid_out = g;
         if (g == 0) return ntiles ? cudaGetLastError() : cudaSuccess;
-        k_pauli<Real, R, L4><<<g, 1u << (T - R), smem(T), s>>>((const C*)psi, (C*)lam, acc ? 1 : 0, d_sweep, d_terms,
+        k_pauli<Real, R, L4, NT><<<g, 1u << (T - R), smem(T), s>>>((const C*)psi, (C*)lam, acc ? 1 : 0, d_sweep, d_terms,
                                                                 partial, ntiles);
         return cudaGetLastError();
     }
@@ -451,21 +454,28 @@ struct PauliCfg {
 // L < 4 only with one register bit
 template <typename Real, typename F>
 static auto pauli_dispatch(const PauliSweep& sw, F&& f) {
-    if (sw.L != 4) return f(PauliCfg<Real, 1, false>{});
+    constexpr int NT = sizeof(Real) == 4 ? 256 : 512;
+    if (sw.L != 4) return f(PauliCfg<Real, 1, false, NT>{});
     switch (sw.R) {
-        case 1: return f(PauliCfg<Real, 1, true>{});
-        case 2: return f(PauliCfg<Real, 2, true>{});
-        default: return f(PauliCfg<Real, 3, true>{});
+        case 1: return f(PauliCfg<Real, 1, true, NT>{});
+        case 2: return f(PauliCfg<Real, 2, true, NT>{});
+        default: return f(PauliCfg<Real, 3, true, NT>{});
         case 4:
-            if constexpr (sizeof(Real) == 4) return f(PauliCfg<Real, 4, true>{});
-            else return f(PauliCfg<Real, 3, true>{});
+            if constexpr (sizeof(Real) == 4) {
+                if (sw.T == 13) return f(PauliCfg<Real, 4, true, 512>{});
+                return f(PauliCfg<Real, 4, true, 256>{});
+            } else {
+                return f(PauliCfg<Real, 3, true, NT>{});
+            }
     }
 }
 
 static bool pauli_shape_ok(int elem_bytes, const PauliSweep& sw) {
     const uint32_t rmax = elem_bytes == 8 ? 4u : 3u;
-    if (sw.R < 1 || sw.R > rmax || sw.T > 12 || sw.L + sw.R > sw.T) return false;
-    if (sw.T - sw.R > (elem_bytes == 8 ? 8u : 9u)) return false;
+    if (sw.R < 1 || sw.R > rmax || sw.T > (elem_bytes == 8 ? 13u : 12u) || sw.L + sw.R > sw.T) return false;
+    if (sw.T - sw.R > 9u) return false;
+    if (elem_bytes == 8 && sw.T == 13 && sw.R != 4) return false;
+    if (elem_bytes == 8 && sw.T < 13 && sw.T - sw.R > 8u) return false;
     return sw.L == 4 || sw.R == 1;
 }
 

@@ -286,14 +286,14 @@ def test_grad_term_classes(sv):
 
 @pytest.mark.parametrize("dtype", [0, 1])
 def test_expval_wide_tiles(sv, dtype):
-    """21 qubits carrying X: TFIM takes three sweeps (12 + 8 + 1 X qubits: tiles hold
-    qubits 0..3 plus up to 8 others after the first), the last one nearly empty; then a
-    mixed observable on the same state.  Both precisions."""
+    """21 qubits carrying X: TFIM takes two complex64 sweeps (13 + 8 X qubits: tiles hold
+    qubits 0..3 plus up to 9 others after the first) and three complex128 ones (12 + 8 +
+    1, the last nearly empty); then a mixed observable on the same state."""
     n = 21
     psi = C.random_state(n, 61)
     st = sv.StateVector(n, dtype)
     st.set_host(psi)
-    for obs, sweeps in ((C.tfim(n), 3), (C.Observable(n, C.tfim(n).terms + _term_class_observable(n, 5).terms), None)):
+    for obs, sweeps in ((C.tfim(n), 2 if dtype == 0 else 3), (C.Observable(n, C.tfim(n).terms + _term_class_observable(n, 5).terms), None)):
         e_ref = O.expval(psi, obs)
         tol = 1e-6 * max(1.0, abs(e_ref)) if dtype == 0 else 1e-11 * max(1.0, abs(e_ref))
         before = st.run_info()["reduction_sweeps"]

@@ -1,6 +1,7 @@
 """Host logic of the Pauli-sum sweeps (no GPU): the grouping sv_expval and sv_grad run,
-read back through sv_pauli_plan_info.  A sweep's tile holds 12 qubits (the whole state
-below that): qubits 0..3 (128-byte runs) and the X/Y qubits of its terms; each thread
+read back through sv_pauli_plan_info.  A sweep's tile holds 13 qubits for complex64 and
+12 for complex128 (the whole state below that): qubits 0..3 (128-byte runs) and the X/Y
+qubits of its terms; each thread
 holds 16 (complex64) or 8 (complex128) elements on register qubits chosen among them.
 Every term is evaluated exactly once, the diagonal ones in the first sweep."""
 import ctypes
@@ -36,10 +37,14 @@ def _xmask(s):
     return sum(1 << q for q, c in enumerate(s) if c in "XY")
 
 
+def _tile(dtype):
+    return 13 if dtype == 0 else 12
+
+
 def _check_invariants(obs, plan, dtype):
     tiles, regs, nterms = plan
     n = obs.n_qubits
-    T = min(n, 12)
+    T = min(n, _tile(dtype))
     full = (1 << n) - 1
     assert sum(nterms) == len(obs.terms)
     for t, r in zip(tiles, regs):
@@ -64,12 +69,13 @@ def test_tfim_sweep_count(N, n, dtype):
     obs = C.tfim(n)
     st, plan = _plan(N, obs, dtype)
     assert st == N.SV_OK
-    expect = 1 if n <= 12 else 1 + math.ceil((n - 12) / 8)
+    tw = _tile(dtype)
+    expect = 1 if n <= tw else 1 + math.ceil((n - tw) / (tw - 4))
     assert len(plan[0]) == expect
     _check_invariants(obs, plan, dtype)
-    # the first sweep holds the 12 lowest qubits and every ZZ term
-    assert plan[0][0] == (1 << min(n, 12)) - 1
-    assert plan[2][0] == (n - 1) + min(n, 12)
+    # the first sweep holds the lowest qubits and every ZZ term
+    assert plan[0][0] == (1 << min(n, tw)) - 1
+    assert plan[2][0] == (n - 1) + min(n, tw)
 
 
 @pytest.mark.parametrize("seed", range(6))
@@ -92,8 +98,9 @@ def test_random_observables(N, seed):
 
 
 def test_register_qubits_follow_the_x_qubits(N):
-    # X on qubits 20..27 only, plus the ZZ chain: one sweep whose tile is qubits 0..3 and
-    # the X qubits, with the register qubits among the X qubits
+    # X on qubits 20..27 only, plus the ZZ chain: one sweep whose tile is qubits 0..3, the
+    # X qubits and one filler qubit (complex64 tiles hold 13), with the register qubits
+    # among the X qubits
     n = 28
     terms = [(1.0, "".join("X" if q == j else "I" for q in range(n))) for j in range(20, 28)]
     terms += C.tfim(n, 0.0).terms[: n - 1]
@@ -102,7 +109,7 @@ def test_register_qubits_follow_the_x_qubits(N):
     assert st == N.SV_OK
     tiles, regs, nterms = plan
     xq = sum(1 << j for j in range(20, 28))
-    assert tiles == [0xF | xq] and nterms == [n - 1 + 8]
+    assert tiles == [0xF | xq | 0x10] and nterms == [n - 1 + 8]
     assert regs[0] & ~xq == 0 and bin(regs[0]).count("1") == 4
     # X on 18..29 of 30 qubits (12 X qubits besides 0..3): two sweeps, each X qubit in a tile
     n = 30
@@ -112,16 +119,17 @@ def test_register_qubits_follow_the_x_qubits(N):
     _check_invariants(obs, plan, 0)
 
 
-def test_term_too_wide_is_rejected(N):
-    n = 20
-    fits = "".join("X" if 4 <= q < 12 else "I" for q in range(n))      # 8 X outside qubits 0..3
-    wide = "".join("X" if 4 <= q < 13 else "I" for q in range(n))      # 9
-    st, plan = _plan(N, C.Observable(n, [(1.0, fits)]))
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_term_too_wide_is_rejected(N, dtype):
+    n, tw = 20, _tile(dtype)
+    fits = "".join("X" if 4 <= q < tw else "I" for q in range(n))      # tw - 4 X outside qubits 0..3
+    wide = "".join("X" if 4 <= q < tw + 1 else "I" for q in range(n))  # one more
+    st, plan = _plan(N, C.Observable(n, [(1.0, fits)]), dtype)
     assert st == N.SV_OK and len(plan[0]) == 1
-    st, _ = _plan(N, C.Observable(n, [(1.0, wide)]))
+    st, _ = _plan(N, C.Observable(n, [(1.0, wide)]), dtype)
     assert st == N.SV_ERR_UNSUPPORTED
-    # qubits 0..3 count toward the tile: 4 + 8 fit
-    st, _ = _plan(N, C.Observable(n, [(1.0, "".join("X" if q < 12 else "I" for q in range(n)))]))
+    # qubits 0..3 count toward the tile: 4 + (tw - 4) fit
+    st, _ = _plan(N, C.Observable(n, [(1.0, "".join("X" if q < tw else "I" for q in range(n)))]), dtype)
     assert st == N.SV_OK
 
 
