@@ -296,6 +296,16 @@ sv_status sv_plan_compile(const sv_plan* plan, const double* params, uint32_t wh
  * be NULL).  Host only. */
 sv_status sv_jit_stats(uint64_t* compiles, uint64_t* cache_hits, double* compile_ms);
 
+/* Generate and compile ahead of time (host only, no GPU) the kernels sv_expval uses for
+ * this observable (Sec. 4.2's Pauli-sum observable; code generation as in Sec. 4.3) on a
+ * complex64 state of n_qubits: one expectation-only kernel per
+ * Pauli sweep with the sweep's terms compiled in (sv_expval generates them on first use
+ * otherwise; they are cached by source for the process).  *n_kernels (may be NULL) =
+ * kernels made ready; 0 for complex128, whose sweeps run the generic sweep kernel.
+ * Errors: SV_ERR_ARG (bad width, dtype or observable), SV_ERR_UNSUPPORTED (a term wider
+ * than a sweep's tile), SV_ERR_CUDA (run-time compilation failed). */
+sv_status sv_pauli_compile(uint32_t n_qubits, sv_dtype dtype, const sv_observable* obs, uint32_t* n_kernels);
+
 /* ---------------------------------------------------------------------------
  * Execution
  * ------------------------------------------------------------------------- */

@@ -316,7 +316,9 @@ static sv_status plan_pauli(int n, int eb, const sv_observable* obs, const std::
         (x ? off : diag).push_back(Raw{x, z, fr, fi});
     }
     // tiles of 13 qubits for complex64 (512 threads x 16 amplitudes), 12 for complex128
-    const int T = std::min(n, eb == 8 ? 13 : 12);
+    int tc64 = 13;
+    if (const char* e = getenv("SVGB_PAULI_T")) tc64 = std::max(9, std::min(13, atoi(e)));
+    const int T = std::min(n, eb == 8 ? tc64 : 12);
     const int L = std::min(4, T - 1);
     const int R = std::min(eb == 8 ? 4 : 3, T - L);
     std::vector<char> used(off.size(), 0);
@@ -429,8 +431,78 @@ static sv_status plan_pauli(int n, int eb, const sv_observable* obs, const std::
 
 // Run the sweeps; lam != nullptr also forms lam = O psi.  Leaves the expectation
 // value (FP64) at red[0] on the device.
+// Expectation-only complex64 sweeps run as kernels generated per sweep (svj::
+// generate_pauli), memoised by the sweep's and its terms' bytes; SVGB_PAULI_JIT=0
+// selects the generic sweep kernel.  Returns false when a sweep has no generated form.
+static std::mutex g_pauli_mu;
+static std::unordered_map<std::string, std::shared_ptr<svj::Built>> g_pauli_memo;
+
+static bool pauli_jit(int n, int eb, const PauliPlan& pp, std::vector<std::shared_ptr<svj::Built>>* out,
+                      sv_status* st) {
+    *st = SV_OK;
+    out->clear();
+    const char* ev = getenv("SVGB_PAULI_JIT");
+    if (eb != 8 || (ev && atoi(ev) == 0)) return false;
+    std::vector<svj::Built*> fresh;
+    for (const svk::PauliSweep& sw : pp.sweeps) {
+        std::string key((const char*)&sw, sizeof(sw));
+        key.append((const char*)(pp.terms.data() + sw.term_off), sw.n_terms * sizeof(svk::PauliTerm));
+        std::shared_ptr<svj::Built> b;
+        {
+            std::lock_guard<std::mutex> lk(g_pauli_mu);
+            auto it = g_pauli_memo.find(key);
+            if (it != g_pauli_memo.end()) b = it->second;
+        }
+        if (!b) {
+            b = std::make_shared<svj::Built>();
+            if (!svj::generate_pauli(sw, pp.terms.data(), n, b.get()).empty()) return false;
+            fresh.push_back(b.get());
+            std::lock_guard<std::mutex> lk(g_pauli_mu);
+            if (g_pauli_memo.size() > 1024) g_pauli_memo.clear();
+            g_pauli_memo[key] = b;
+        }
+        out->push_back(b);
+    }
+    if (!fresh.empty()) {
+        const std::string err = svj::compile(fresh);
+        if (!err.empty()) {
+            *st = fail(SV_ERR_CUDA, "run-time compilation of a Pauli sweep failed: " + err);
+            return true;
+        }
+    }
+    return true;
+}
+
 static sv_status run_pauli(sv_handle h, const PauliPlan& pp, void* lam) {
     const int n = (int)h->n;
+    if (!lam) {
+        std::vector<std::shared_ptr<svj::Built>> built;
+        sv_status js = SV_OK;
+        if (pauli_jit(n, h->eb, pp, &built, &js)) {
+            if (js) return js;
+            int nsm = 0, dev = 0;
+            SV_CUDA(cudaGetDevice(&dev));
+            SV_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+            uint64_t rows = 0;   // at most 32 CTAs per SM per sweep
+            for (auto& b : built) rows += std::min<uint64_t>(b->ntiles, (uint64_t)nsm * 32);
+            SV_CUDA(h->red.ensure((rows + 16) * sizeof(double)));
+            double* part = (double*)h->red.p + 16;
+            uint64_t off = 0;
+            for (auto& b : built) {
+                uint32_t grid = 0;
+                cudaEvent_t t0 = tick(h);
+                SV_CUDA(svj::launch(*b, h->psi, nullptr, part + off, nullptr, h->stream, &grid));
+                tock(h, t0, TK_OBS);
+                off += grid;
+                h->info.reduction_sweeps += 1;
+                h->info.kernel_launches += 1;
+                h->info.hbm_bytes += (double)state_bytes(h);
+            }
+            SV_CUDA(svk::launch_reduce_rows(part, off, 1, (double*)h->red.p, h->stream));
+            h->info.kernel_launches += 1;
+            return SV_OK;
+        }
+    }
     const size_t szs = align16(pp.sweeps.size() * sizeof(svk::PauliSweep));
     const size_t szt = align16(std::max<size_t>(1, pp.terms.size()) * sizeof(svk::PauliTerm));
     SV_CUDA(h->aux.ensure(szs + szt));
@@ -986,6 +1058,21 @@ sv_status sv_plan_compile(const sv_plan* plan, const double* params, uint32_t wh
         count += (uint32_t)built.size();
     }
     if (n_kernels) *n_kernels = count;
+    return SV_OK;
+}
+
+sv_status sv_pauli_compile(uint32_t n_qubits, sv_dtype dtype, const sv_observable* obs, uint32_t* n_kernels) {
+    if (n_qubits < 1 || n_qubits > 40 || (dtype != SV_C64 && dtype != SV_C128)) return fail(SV_ERR_ARG, "bad width or dtype");
+    std::vector<int> ident(n_qubits);
+    for (uint32_t q = 0; q < n_qubits; ++q) ident[q] = (int)q;
+    PauliPlan pp;
+    sv_status s = plan_pauli((int)n_qubits, dtype == SV_C64 ? 8 : 16, obs, ident, &pp);
+    if (s) return s;
+    std::vector<std::shared_ptr<svj::Built>> built;
+    sv_status js = SV_OK;
+    const bool gen = pauli_jit((int)n_qubits, dtype == SV_C64 ? 8 : 16, pp, &built, &js);
+    if (js) return js;
+    if (n_kernels) *n_kernels = gen ? (uint32_t)built.size() : 0u;
     return SV_OK;
 }
 

@@ -27,6 +27,7 @@
 #include <thread>
 #include <unordered_map>
 
+#include "kernels.h"
 #include "jit_prelude_inc.h"   // kJitPrelude: jit_prelude.cuh as a string (generated by the build)
 
 namespace svj {
@@ -1281,6 +1282,168 @@ void stats(uint64_t* compiles, uint64_t* hits, double* compile_ms) {
     if (compiles) *compiles = g_compiles.load();
     if (hits) *hits = g_hits.load();
     if (compile_ms) *compile_ms = g_compile_us.load() / 1000.0;
+}
+
+
+// ---------------------------------------------------------------------------
+// Pauli-sum expectation sweeps (the observable of Sec. 4.2): one sweep's terms compiled
+// into a kernel, expectation only.  Per tile a thread holds 16 amplitudes a_k (register
+// bits = tile bits 4..7 of the sweep's layout) and sums |a_k|^2 times the diagonal weight,
+// plus, for each X / Y term, Re(conj(a_k) f s_k p_k) with p_k the partner amplitude (in a
+// register, or in the tile staged in shared memory).  A Pauli string is Hermitian, so the
+// two amplitudes of a register pair contribute complex-conjugate terms: one is
+// evaluated, twice.  Tiles are double-buffered with cp.async; FP32 per tile, compensated
+// FP32 across a thread's tiles, FP64 across threads.
+// ---------------------------------------------------------------------------
+std::string generate_pauli(const svk::PauliSweep& sw, const svk::PauliTerm* terms, int n, Built* B) {
+    const int T = (int)sw.T, R = (int)sw.R, L = (int)sw.L, NG = (int)sw.n_glob;
+    if (L != 4 || R != 4 || T < 9 || T > 13 || n - T != NG) return "pauli jit: unsupported sweep shape";
+    const int NT = 1 << (T - R), K = 1 << R;
+    // tile buffers per CTA (2: the next tile's copy overlaps this one) and CTAs per SM the
+    // registers are budgeted for; SVGB_PAULI_NB / SVGB_PAULI_MINB override for tuning
+    int NBUF = 2, MINB = 1;
+    if (const char* e = getenv("SVGB_PAULI_NB")) NBUF = std::max(1, std::min(2, atoi(e)));
+    if (const char* e = getenv("SVGB_PAULI_MINB")) MINB = std::max(1, std::min(4, atoi(e)));
+    const svk::PauliTerm* tl = terms + sw.term_off;
+    const uint32_t nterm = sw.n_terms, d0 = sw.n_dstat, d1 = d0 + sw.n_dglob, d2 = d1 + sw.n_dmix;
+    const uint32_t regmask = ((1u << R) - 1u) << L;
+    ArgBuilder A;
+    for (int i = 0; i < NG; ++i) A.Q(1ull << sw.glob_pos[i]);
+    const int QT = NG;
+    for (int b = 0; b < T; ++b) A.Q(sw.ptile[b]);
+    auto tmask = [&](uint64_t z) {
+        uint32_t m = 0;
+        for (int b = 0; b < T; ++b)
+            if (z & sw.ptile[b]) m |= 1u << b;
+        return m;
+    };
+    auto amp = [](int k) { return fmt("x%d", k); };
+    std::string pre, body;
+    pre += "const u32 tid = threadIdx.x;\n";
+    pre += fmt("const u64 ntiles = 1ull << %d;\nu64 t = blockIdx.x;\nif (t >= ntiles) return;\n", NG);
+    pre += fmt("float2* const tb0 = reinterpret_cast<float2*>(smem);\nfloat2* const tb1 = tb0 + %d;\n", NBUF == 2 ? 1 << T : 0);
+    pre += fmt("const u32 te = (tid & 15u) | ((tid >> 4) << %d);\n", L + R);
+    pre += fmt("u64 tphys = 0;\n#pragma unroll\nfor (int b = 0; b < %d; ++b)\nif ((te >> b) & 1u) tphys |= a.q[%d + b];\n", T, QT);
+    const int rounds = (1 << T) / 2 / NT;
+    pre += fmt("u64 ld_tid = 0;\n#pragma unroll\nfor (int b = 1; b < %d; ++b)\nif (((2u * tid) >> b) & 1u) ld_tid |= a.q[%d + b];\n", T, QT);
+    pre += fmt("u64 jp[%d];\n#pragma unroll\nfor (int j = 0; j < %d; ++j) {\nu64 p = 0;\nconst u32 e = %du * (u32)j;\n", rounds, rounds, 2 * NT);
+    pre += fmt("#pragma unroll\nfor (int b = 1; b < %d; ++b)\nif ((e >> b) & 1u) p |= a.q[%d + b];\njp[j] = p;\n}\n", T, QT);
+    pre += "u64 base = 0, pstep = 0, gmask = 0;\n";
+    if (NG > 0)
+        pre += fmt("#pragma unroll 1\nfor (int i = 0; i < %d; ++i) {\nconst u64 b = a.q[i];\ngmask |= b;\nif ((t >> i) & 1ull) base |= b;\n"
+                   "if (((u64)gridDim.x >> i) & 1ull) pstep |= b;\n}\n", NG);
+    // static diagonal weights (Z on tile bits only): w_k = sum c (-1)^(|te & zthr|) (-1)^(|k & zreg|)
+    pre += fmt("float w[%d];\n#pragma unroll\nfor (int k = 0; k < %d; ++k) w[k] = 0.f;\n", K, K);
+    for (uint32_t i = 0; i < d0; ++i) {
+        const svk::PauliTerm& pt = tl[i];
+        const uint32_t zthr = tmask(pt.zmask) & ~regmask;
+        const int c = A.F(pt.fre32);
+        pre += zthr ? fmt("{\nconst float c = (__popc(te & %uu) & 1) ? -a.f[%d] : a.f[%d];\n", zthr, c, c)
+                    : fmt("{\nconst float c = a.f[%d];\n", c);
+        for (int k = 0; k < K; ++k) pre += fmt("w[%d] %s= c;\n", k, (__builtin_popcount((unsigned)k & pt.zreg) & 1) ? "-" : "+");
+        pre += "}\n";
+    }
+    auto issue = [&](const char* bexpr, const char* buf) {
+        std::string r;
+        for (int j = 0; j < rounds; ++j)
+            r += fmt("svj_cp_async16(%s + 2u * (tid + %du), a.v0 + (%s | ld_tid | jp[%d]));\n", buf, j * NT, bexpr, j);
+        return r + "svj_cp_commit();\n";
+    };
+    pre += "float es = 0.f, ec = 0.f;\n";
+    pre += issue("base", "tb0");
+    body += "#pragma unroll 1\nfor (u32 cur = 0; t < ntiles; t += gridDim.x, cur ^= 1u) {\n";
+    body += "const u64 bn = ((base | ~gmask) + pstep) & gmask;\n";
+    if (NBUF == 2)
+        body += "if (t + gridDim.x < ntiles) {\n" + issue("bn", "(cur ? tb0 : tb1)") + "svj_cp_wait1();\n} else {\nsvj_cp_wait0();\n}\n__syncthreads();\n";
+    else
+        body += "svj_cp_wait0();\n__syncthreads();\n";
+    body += "const float2* const tb = cur ? tb1 : tb0;\n";
+    for (int k = 0; k < K; ++k) body += fmt("const float2 %s = tb[te | %du];\n", amp(k).c_str(), (unsigned)k << L);
+    body += "const u64 fix = base | tphys;\n";
+    // diagonal: global-only terms give one weight per tile, mixed terms a signed sum
+    body += "float wc = 0.f;\n";
+    for (uint32_t i = d0; i < d1; ++i) {
+        const int zi = A.Q(tl[i].zmask), c = A.F(tl[i].fre32);
+        body += fmt("wc += (__popcll(base & a.q[%d]) & 1) ? -a.f[%d] : a.f[%d];\n", zi, c, c);
+    }
+    body += "float e = 0.f;\n";
+    for (int k = 0; k < K; ++k)
+        body += fmt("e = fmaf(fmaf(%s.x, %s.x, %s.y * %s.y), w[%d] + wc, e);\n", amp(k).c_str(), amp(k).c_str(), amp(k).c_str(),
+                    amp(k).c_str(), k);
+    for (uint32_t i = d1; i < d2; ++i) {
+        const svk::PauliTerm& pt = tl[i];
+        const int zi = A.Q(pt.zmask), c = A.F(pt.fre32);
+        body += fmt("{\nfloat m = 0.f;\n");
+        for (int k = 0; k < K; ++k)
+            body += fmt("m = fmaf(%s%s.x, %s.x, fmaf(%s%s.y, %s.y, m));\n", ((pt.smask >> k) & 1) ? "-" : "", amp(k).c_str(),
+                        amp(k).c_str(), ((pt.smask >> k) & 1) ? "-" : "", amp(k).c_str(), amp(k).c_str());
+        body += fmt("e = fmaf((__popcll(fix & a.q[%d]) & 1) ? -a.f[%d] : a.f[%d], m, e);\n}\n", zi, c, c);
+    }
+    // X / Y terms
+    for (uint32_t i = d2; i < nterm; ++i) {
+        const svk::PauliTerm& pt = tl[i];
+        const uint32_t xthr = pt.xtile & ~regmask;
+        const bool real = (pt.flags & svk::PT_REAL) != 0, noz = (pt.flags & svk::PT_NOZ) != 0;
+        const int cr = A.F(pt.fre32), ci = real ? -1 : A.F(pt.fim32);
+        body += "{\nfloat ar = 0.f, ai = 0.f;\n";
+        const uint32_t low = pt.xreg & (~pt.xreg + 1u);
+        if (xthr) body += fmt("const float2* const pb = tb + (te ^ %uu);\n", xthr);
+        for (int k = 0; k < K; ++k) {
+            if (!xthr && (k & (int)low)) continue;   // the pair's other amplitude: its conjugate term
+            const std::string p = xthr ? fmt("pb[%du]", (unsigned)((k ^ pt.xreg) << L)) : amp(k ^ pt.xreg);
+            const char* sg = ((pt.smask >> k) & 1) ? "-" : "";
+            if (xthr) body += fmt("{\nconst float2 p = %s;\n", p.c_str());
+            const std::string pp = xthr ? std::string("p") : p;
+            body += fmt("ar = fmaf(%s%s.x, %s.x, fmaf(%s%s.y, %s.y, ar));\n", sg, amp(k).c_str(), pp.c_str(), sg, amp(k).c_str(),
+                        pp.c_str());
+            if (!real)
+                body += fmt("ai = fmaf(%s%s.x, %s.y, fmaf(%s%s.y, %s.x, ai));\n", sg, amp(k).c_str(), pp.c_str(),
+                            ((pt.smask >> k) & 1) ? "" : "-", amp(k).c_str(), pp.c_str());
+            if (xthr) body += "}\n";
+        }
+        const std::string v = real ? fmt("a.f[%d] * ar", cr) : fmt("fmaf(a.f[%d], ar, -a.f[%d] * ai)", cr, ci);
+        const float scale = xthr ? 1.f : 2.f;
+        if (noz) body += fmt("e = fmaf(%.1ff, %s, e);\n", scale, v.c_str());
+        else body += fmt("e = fmaf((__popcll(fix & a.q[%d]) & 1) ? %.1ff : %.1ff, %s, e);\n", A.Q(pt.zmask), -scale, scale, v.c_str());
+        body += "}\n";
+    }
+    body += "{\nconst float y = e - ec, s2 = es + y;\nec = (s2 - es) - y;\nes = s2;\n}\n";
+    body += "base = bn;\n__syncthreads();\n";
+    if (NBUF == 1) body += "if (t + gridDim.x < ntiles) {\n" + issue("bn", "tb0") + "}\n";
+    body += "}\n";
+    // CTA partial in FP64, fixed order
+    body += "double d = (double)es - (double)ec;\n";
+    body += "#pragma unroll\nfor (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);\n";
+    body += "__shared__ double s_w[32];\nif ((tid & 31u) == 0u) s_w[tid >> 5] = d;\n__syncthreads();\n";
+    body += fmt("if (tid == 0) {\ndouble s2 = 0.0;\nfor (int i = 0; i < %d; ++i) s2 += s_w[i];\na.partial[blockIdx.x] = s2;\n}\n", NT / 32);
+    // assemble (the argument block has the stage kernels' layout, so launch() serves both)
+    const int nq = std::max<int>(1, (int)A.q.size()), nu = 1, nf = std::max<int>(1, (int)A.f.size());
+    std::string src = "#include \"jit_prelude.cuh\"\n";
+    src += fmt("struct alignas(64) Args {\nSvjTmap m0;\nSvjTmap m1;\nfloat2* v0;\nfloat2* v1;\ndouble* partial;\nint* flag;\n"
+               "const double* params;\nconst u32* pofs;\nu64 ncirc;\nu64 q[%d];\nu32 u[%d];\nfloat f[%d];\n};\n", nq, nu, nf);
+    src += "extern \"C\" __global__ void __launch_bounds__(" + std::to_string(NT) + ", " + std::to_string(MINB) +
+           ") KNAME(const __grid_constant__ Args a) {\n"
+           "extern __shared__ __attribute__((aligned(16))) unsigned char smem[];\n" + pre + body + "}\n";
+    const std::string name = fmt("svj_pauli_%016llx", (unsigned long long)fnv1a(src));
+    size_t pos;
+    while ((pos = src.find("KNAME")) != std::string::npos) src.replace(pos, 5, name);
+    B->src = src;
+    B->name = name;
+    B->nthr = (uint32_t)NT;
+    B->n_slots = 1;
+    B->ntiles = 1ull << NG;
+    B->tma = false;
+    size_t bytes = kArgQ + 8 * (size_t)nq + 4 * (size_t)nu;
+    bytes = (bytes + 3) & ~(size_t)3;
+    const size_t off_f = bytes;
+    bytes += 4 * (size_t)nf;
+    bytes = (bytes + 63) & ~(size_t)63;
+    if (bytes > 32000) return "pauli jit: terms exceed the kernel argument space";
+    B->smem = (uint32_t)((8u * NBUF) << T);   // tile buffers of 2^T complex64
+    B->args.assign(bytes, 0);
+    std::memcpy(B->args.data() + kArgQ, A.q.data(), 8 * A.q.size());
+    std::memcpy(B->args.data() + off_f, A.f.data(), 4 * A.f.size());
+    return "";
 }
 
 }  // namespace svj

@@ -19,6 +19,11 @@
 
 #include "program.h"
 
+namespace svk {
+struct PauliSweep;
+struct PauliTerm;
+}  // namespace svk
+
 namespace svj {
 
 // One stage of a packed complex64 program (host copies of its blob sections).
@@ -79,6 +84,14 @@ cudaError_t launch_batched(const Built& b, void* v0, void* v1, double* partial, 
 
 // Load a compiled kernel and set its launch attributes (before a stream capture).
 cudaError_t preload(const Built& b);
+
+// A Pauli-sum expectation sweep (complex64, expectation only): the terms of one sweep of
+// the host's Pauli plan (diagonal classes, then X / Y terms; kernels.h) compiled into one
+// kernel.  Launch with launch(b, psi, nullptr, partial, nullptr, s, &grid): every CTA
+// writes partial[blockIdx] = its tiles' sum of Re(conj(psi) (O_sweep psi)) in FP64.
+// Returns "" or an error (a sweep shape the generator does not handle: the caller then
+// runs the generic sweep kernel).
+std::string generate_pauli(const svk::PauliSweep& sw, const svk::PauliTerm* terms, int n, Built* out);
 
 // NVRTC compiles and cache hits since load (diagnostics).
 void stats(uint64_t* compiles, uint64_t* hits, double* compile_ms);

@@ -67,3 +67,25 @@ def test_compile_errors(sv):
     with pytest.raises(sv.SvError) as e:
         sv.Plan(h, 4).compile(None)                  # parametric circuit without params
     assert e.value.status == N.SV_ERR_ARG
+
+
+def test_pauli_expectation_kernels_compile(sv):
+    """The expectation-only Pauli sweeps (one generated kernel per sweep, terms compiled
+    in) are generated and NVRTC-compiled for sm_103a on the host; complex128 keeps the
+    generic sweep kernel; a second call is served from the cache."""
+    import ctypes
+    from paper_2509_14098_gb300 import _native as N
+    for n, sweeps in ((12, 1), (20, 2), (30, 3)):
+        o, keep = N.observable_struct(C.tfim(n))
+        k = ctypes.c_uint32(99)
+        N.check(N.lib.sv_pauli_compile(n, 0, ctypes.byref(o), ctypes.byref(k)))
+        assert k.value == sweeps
+        N.check(N.lib.sv_pauli_compile(n, 1, ctypes.byref(o), ctypes.byref(k)))
+        assert k.value == 0
+    obs = C.Observable(16, C.tfim(16).terms + [(0.3, "XYZ" + "I" * 10 + "ZYX")])
+    o, keep = N.observable_struct(obs)
+    k = ctypes.c_uint32(0)
+    N.check(N.lib.sv_pauli_compile(16, 0, ctypes.byref(o), ctypes.byref(k)))
+    before = _compiles(N)
+    N.check(N.lib.sv_pauli_compile(16, 0, ctypes.byref(o), ctypes.byref(k)))
+    assert k.value >= 1 and _compiles(N) == before
