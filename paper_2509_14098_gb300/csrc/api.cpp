@@ -235,12 +235,22 @@ static sv_status do_permute(sv_handle h, const uint32_t* phys_of_qubit) {
     for (int p = 0; p < n; ++p)
         if (dst[p] != p) ident = false;
     if (ident) return SV_OK;
+    // tile: the input's 4 lowest bits and the input bits that land on output bits 0..3,
+    // then alternately the next input bit above the contiguous input run and the input
+    // bit that lands just above the contiguous output run, so that both the reads and
+    // the writes are runs of at least 512 bytes (2^12 complex64 / 2^11 complex128)
     const int c = std::min(4, n);
     uint64_t B = (1ull << c) - 1;
     for (int p = 0; p < n; ++p)
         if (dst[p] < c) B |= 1ull << p;
-    const int Tp = std::min(n, std::max(12, __builtin_popcountll(B)));
-    for (int p = 0; p < n && __builtin_popcountll(B) < Tp; ++p) B |= 1ull << p;
+    const int Tp = std::min(n, h->eb == 8 ? 12 : 11);
+    for (int turn = 0, ri = 0, ro = 0; __builtin_popcountll(B) < Tp; turn ^= 1) {
+        while (ri < n && ((B >> ri) & 1)) ++ri;
+        while (ro < n && ((B >> phys_of_qubit[ro]) & 1)) ++ro;
+        if (turn == 0 && ri < n) B |= 1ull << ri;
+        else if (ro < n) B |= 1ull << phys_of_qubit[ro];
+        else if (ri < n) B |= 1ull << ri;
+    }
     svk::PermDesc d;
     std::memset(&d, 0, sizeof(d));
     d.T = (uint32_t)Tp;
@@ -267,18 +277,21 @@ static sv_status do_permute(sv_handle h, const uint32_t* phys_of_qubit) {
         d.sig[c2] = d.swbit[outs[c2].second];
     }
     SV_CUDA(h->scratch.ensure(state_bytes(h)));
-    SV_CUDA(h->aux.ensure(sizeof(d)));
-    h->aux_host.assign((uint8_t*)&d, (uint8_t*)&d + sizeof(d));
-    SV_CUDA(cudaMemcpyAsync(h->aux.p, h->aux_host.data(), sizeof(d), cudaMemcpyHostToDevice, h->stream));
     const uint64_t ntiles = 1ull << (n - Tp);
     cudaEvent_t t0 = tick(h);
-    SV_CUDA(svk::launch_permute(h->eb, h->psi, h->scratch.p, (const svk::PermDesc*)h->aux.p, Tp,
-                                ntiles, h->stream));
+    SV_CUDA(svk::launch_permute(h->eb, h->psi, h->scratch.p, d, ntiles, h->stream));
     tock(h, t0, TK_PERM);
-    SV_CUDA(cudaMemcpyAsync(h->psi, h->scratch.p, state_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
+    // a handle that owns its state takes the permuted buffer as the state; a caller's
+    // buffer receives a copy
+    if (h->owns) {
+        std::swap(h->psi, h->scratch.p);
+    } else {
+        SV_CUDA(cudaMemcpyAsync(h->psi, h->scratch.p, state_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
+        h->info.hbm_bytes += 2.0 * (double)state_bytes(h);
+    }
     h->info.permutation_sweeps += 1;
     h->info.kernel_launches += 1;
-    h->info.hbm_bytes += 4.0 * (double)state_bytes(h);
+    h->info.hbm_bytes += 2.0 * (double)state_bytes(h);
     return SV_OK;
 }
 
@@ -348,8 +361,13 @@ static sv_status plan_pauli(int n, int eb, const sv_observable* obs, const std::
         std::vector<int> pos;
         for (int p = 0; p < L; ++p) pos.push_back(p);
         for (int p : reg) pos.push_back(p);
+        // the other tile qubits, fewest X / Y first: the qubits that carry X / Y take the
+        // top tile bits, which the generated sweeps also read as register bits
+        std::vector<int> rest;
         for (int p : cand)
-            if (std::find(reg.begin(), reg.end(), p) == reg.end()) pos.push_back(p);
+            if (std::find(reg.begin(), reg.end(), p) == reg.end()) rest.push_back(p);
+        std::stable_sort(rest.begin(), rest.end(), [&](int u, int v) { return cnt[u] < cnt[v]; });
+        for (int p : rest) pos.push_back(p);
         svk::PauliSweep sw;
         std::memset(&sw, 0, sizeof(sw));
         sw.T = (uint32_t)T;

@@ -8,71 +8,119 @@ namespace svk {
 
 // ---------------------------------------------------------------------------
 // permutation: the tile contains the input's low bits and the input bits that land
-// on the output's low bits, so both the read and the write are contiguous runs.
+// on the output's low bits (the host widens both runs to at least 512 bytes), so both
+// the read and the write are contiguous runs.  Persistent CTAs, two tile buffers: the
+// next tile's copy is in flight while the current one is written out.  Every chunk
+// offset is XOR / OR-linear in the chunk index, so a thread forms its offsets once; a
+// tile's global part is one OR-reduction over the warp (lane i holds global bit i).
 // ---------------------------------------------------------------------------
+constexpr int kPermThreads = 256;
+constexpr int kPermChunks = 8;   // 16-byte chunks per thread and tile (tiles of 2^12 complex64 / 2^11 complex128)
+
+__device__ __forceinline__ uint64_t warp_or64(uint64_t v) {
+    const uint32_t lo = __reduce_or_sync(0xffffffffu, (uint32_t)v);
+    const uint32_t hi = __reduce_or_sync(0xffffffffu, (uint32_t)(v >> 32));
+    return ((uint64_t)hi << 32) | lo;
+}
+
 template <typename C>
-__global__ void __launch_bounds__(256) k_permute(const C* __restrict__ in, C* __restrict__ out,
-                                                 const PermDesc* __restrict__ dp) {
+__global__ void __launch_bounds__(kPermThreads, 3) k_permute(const C* __restrict__ in, C* __restrict__ out,
+                                                          const __grid_constant__ PermDesc d, uint64_t ntiles) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* tile = reinterpret_cast<C*>(smem_raw);
-    const PermDesc& d = *dp;
+    constexpr int APC = 16 / (int)sizeof(C);   // elements per 16-byte chunk
+    const uint32_t tid = threadIdx.x, lane = tid & 31u;
     const int T = (int)d.T;
-    constexpr int APC = 16 / (int)sizeof(C);
-    const uint32_t nch = (1u << T) / APC;
-    uint64_t base = 0, obase = 0;
-    {
-        uint64_t t = blockIdx.x;
-        for (int i = 0; t; ++i, t >>= 1)
-            if (t & 1) {
-                base |= 1ull << d.glob_pos[i];
-                obase |= d.gout[i];
-            }
-    }
-    for (uint32_t c = threadIdx.x; c < nch; c += blockDim.x) {
-        const uint32_t t = c * APC;
-        uint64_t p = base;
-        uint32_t sa = 0;
+    const uint32_t tsz = 1u << T, nch = tsz / APC;
+    C* const buf0 = reinterpret_cast<C*>(smem_raw);
+    C* const buf1 = buf0 + tsz;
+    // this lane's global bit (input and output value), zero past the last one
+    const uint64_t gin = lane < d.n_glob ? 1ull << d.glob_pos[lane] : 0ull;
+    const uint64_t gou = lane < d.n_glob ? d.gout[lane] : 0ull;
+    // per-chunk offsets: chunk c = tid + 256 j holds tile (or output-tile) elements c * APC
+    uint64_t lin[kPermChunks], lout[kPermChunks];
+    uint32_t sin[kPermChunks], sout[kPermChunks];
+#pragma unroll
+    for (int j = 0; j < kPermChunks; ++j) {
+        const uint32_t e = (tid + (uint32_t)j * kPermThreads) * APC;
+        uint64_t pi = 0, po = 0;
+        uint32_t si = 0, so = 0;
         for (int b = 0; b < T; ++b)
-            if ((t >> b) & 1) {
-                p |= d.ptile[b];
-                sa ^= d.swbit[b];
+            if ((e >> b) & 1u) {
+                pi |= d.ptile[b];
+                si ^= d.swbit[b];
+                po |= d.pout[b];
+                so ^= d.sig[b];
             }
-        cp_async16(tile + sa, in + p);
+        lin[j] = pi;
+        sin[j] = si;
+        lout[j] = po;
+        sout[j] = so;
     }
-    cp_async_commit_wait_all();
-    __syncthreads();
-    for (uint32_t c = threadIdx.x; c < nch; c += blockDim.x) {
-        const uint32_t u = c * APC;
-        uint64_t p = obase;
-        uint32_t sa = 0;
-        for (int b = 0; b < T; ++b)
-            if ((u >> b) & 1) {
-                p |= d.pout[b];
-                sa ^= d.sig[b];
-            }
-        if (APC == 2) {
-            const C v0 = tile[sa], v1 = tile[sa ^ d.sig[0]];
-            float4 v;
-            v.x = (float)v0.x; v.y = (float)v0.y; v.z = (float)v1.x; v.w = (float)v1.y;
-            *reinterpret_cast<float4*>(out + p) = v;
+    auto issue = [&](uint64_t t, C* buf) {
+        const uint64_t base = warp_or64(((t >> lane) & 1ull) ? gin : 0ull);
+#pragma unroll
+        for (int j = 0; j < kPermChunks; ++j)
+            if (tid + (uint32_t)j * kPermThreads < nch) cp_async16(buf + sin[j], in + (base | lin[j]));
+        cp_async_commit();
+    };
+    uint64_t t = blockIdx.x;
+    if (t >= ntiles) return;
+    issue(t, buf0);
+#pragma unroll 1
+    for (uint32_t it = 0; t < ntiles; t += gridDim.x, ++it) {
+        const uint64_t tn = t + gridDim.x;
+        C* const cur = (it & 1u) ? buf1 : buf0;
+        if (tn < ntiles) {
+            issue(tn, (it & 1u) ? buf0 : buf1);
+            cp_async_wait1();
         } else {
-            out[p] = tile[sa];
+            cp_async_wait0();
         }
+        __syncthreads();   // every thread's copies of tile t have landed
+        const uint64_t obase = warp_or64(((t >> lane) & 1ull) ? gou : 0ull);
+#pragma unroll
+        for (int j = 0; j < kPermChunks; ++j) {
+            if (tid + (uint32_t)j * kPermThreads >= nch) continue;
+            C* const dst = out + (obase | lout[j]);
+            if constexpr (APC == 2) {
+                const C v0 = cur[sout[j]], v1 = cur[sout[j] ^ d.sig[0]];
+                *reinterpret_cast<float4*>(dst) = make_float4(v0.x, v0.y, v1.x, v1.y);
+            } else {
+                *dst = cur[sout[j]];
+            }
+        }
+        __syncthreads();   // this buffer is free for the copy of tile t + 2 gridDim
     }
 }
 
-cudaError_t launch_permute(int elem_bytes, const void* in, void* out, const PermDesc* d, int T,
-                           uint64_t ntiles, cudaStream_t s) {
-    const size_t smem = (size_t)elem_bytes << T;
-    if (elem_bytes == 8) {
-        static bool cfg = false;
-        if (!cfg) { cudaFuncSetAttribute(k_permute<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024); cfg = true; }
-        k_permute<float2><<<(unsigned)ntiles, 256, smem, s>>>((const float2*)in, (float2*)out, d);
-    } else {
-        static bool cfg = false;
-        if (!cfg) { cudaFuncSetAttribute(k_permute<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024); cfg = true; }
-        k_permute<double2><<<(unsigned)ntiles, 256, smem, s>>>((const double2*)in, (double2*)out, d);
+cudaError_t launch_permute(int elem_bytes, const void* in, void* out, const PermDesc& d, uint64_t ntiles,
+                           cudaStream_t s) {
+    const size_t smem = 2 * ((size_t)elem_bytes << d.T);
+    static int nsm[64] = {0}, per_sm[64][2] = {{0}};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    const int w = elem_bytes == 8 ? 0 : 1;
+    if (!per_sm[dev][w]) {
+        if (!nsm[dev]) {
+            e = cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return e;
+        }
+        const void* fn = w == 0 ? (const void*)k_permute<float2> : (const void*)k_permute<double2>;
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * (16 << 11));
+        if (e != cudaSuccess) return e;
+        int nb = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kPermThreads, 2 * (16 << 11));
+        if (e != cudaSuccess) return e;
+        per_sm[dev][w] = nb > 0 ? nb : 1;
     }
+    const uint64_t g = (uint64_t)nsm[dev] * (uint64_t)per_sm[dev][w];
+    const unsigned grid = (unsigned)(ntiles < g ? ntiles : g);
+    if (w == 0)
+        k_permute<float2><<<grid, kPermThreads, smem, s>>>((const float2*)in, (float2*)out, d, ntiles);
+    else
+        k_permute<double2><<<grid, kPermThreads, smem, s>>>((const double2*)in, (double2*)out, d, ntiles);
     return cudaGetLastError();
 }
 

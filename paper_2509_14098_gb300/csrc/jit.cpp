@@ -1290,7 +1290,9 @@ void stats(uint64_t* compiles, uint64_t* hits, double* compile_ms) {
 // into a kernel, expectation only.  Per tile a thread holds 16 amplitudes a_k (register
 // bits = tile bits 4..7 of the sweep's layout) and sums |a_k|^2 times the diagonal weight,
 // plus, for each X / Y term, Re(conj(a_k) f s_k p_k) with p_k the partner amplitude (in a
-// register, or in the tile staged in shared memory).  A Pauli string is Hermitian, so the
+// register, or in the tile staged in shared memory); terms whose X / Y qubits all sit on
+// the top 4 tile bits are evaluated from a second read of the tile with those bits as the
+// register bits.  A Pauli string is Hermitian, so the
 // two amplitudes of a register pair contribute complex-conjugate terms: one is
 // evaluated, twice.  Tiles are double-buffered with cp.async; FP32 per tile, compensated
 // FP32 across a thread's tiles, FP64 across threads.
@@ -1361,10 +1363,23 @@ std::string generate_pauli(const svk::PauliSweep& sw, const svk::PauliTerm* term
     for (int k = 0; k < K; ++k) body += fmt("const float2 %s = tb[te | %du];\n", amp(k).c_str(), (unsigned)k << L);
     body += "const u64 fix = base | tphys;\n";
     // diagonal: global-only terms give one weight per tile, mixed terms a signed sum
-    body += "float wc = 0.f;\n";
-    for (uint32_t i = d0; i < d1; ++i) {
-        const int zi = A.Q(tl[i].zmask), c = A.F(tl[i].fre32);
-        body += fmt("wc += (__popcll(base & a.q[%d]) & 1) ? -a.f[%d] : a.f[%d];\n", zi, c, c);
+    // (the global-only terms are shared by every thread of the tile: lane i of each warp
+    // evaluates terms i, i + 32, ..., then the warp sums them)
+    if (d1 > d0) {
+        int zq0 = -1, cf0 = -1;
+        for (uint32_t i = d0; i < d1; ++i) {
+            const int zi = A.Q(tl[i].zmask), c = A.F(tl[i].fre32);
+            if (i == d0) zq0 = zi, cf0 = c;
+        }
+        body += "float wc = 0.f;\n{\nconst u32 ln = tid & 31u;\n";
+        for (uint32_t c0 = 0; c0 < d1 - d0; c0 += 32) {
+            const uint32_t m = std::min<uint32_t>(32u, d1 - d0 - c0);
+            body += fmt("if (ln < %uu) {\nconst u32 j = %uu + ln;\nwc += (__popcll(base & a.q[%d + j]) & 1) ? -a.f[%d + j] : a.f[%d + j];\n}\n",
+                        m, c0, zq0, cf0, cf0);
+        }
+        body += "#pragma unroll\nfor (int o = 16; o > 0; o >>= 1) wc += __shfl_xor_sync(0xffffffffu, wc, o);\n}\n";
+    } else {
+        body += "float wc = 0.f;\n";
     }
     body += "float e = 0.f;\n";
     for (int k = 0; k < K; ++k)
@@ -1379,32 +1394,102 @@ std::string generate_pauli(const svk::PauliSweep& sw, const svk::PauliTerm* term
                         amp(k).c_str(), ((pt.smask >> k) & 1) ? "-" : "", amp(k).c_str(), amp(k).c_str());
         body += fmt("e = fmaf((__popcll(fix & a.q[%d]) & 1) ? -a.f[%d] : a.f[%d], m, e);\n}\n", zi, c, c);
     }
-    // X / Y terms
-    for (uint32_t i = d2; i < nterm; ++i) {
-        const svk::PauliTerm& pt = tl[i];
-        const uint32_t xthr = pt.xtile & ~regmask;
-        const bool real = (pt.flags & svk::PT_REAL) != 0, noz = (pt.flags & svk::PT_NOZ) != 0;
+    // X / Y terms.  A term whose X / Y qubits are all register bits of the first layout
+    // (tile bits L..L+R-1) pairs registers of that layout; one whose X / Y qubits are all
+    // on the top R tile bits pairs registers of a second layout, in which a thread holds
+    // the amplitudes along those bits (threads on tile bits 0..T-R-1, so the lanes still
+    // read consecutive amplitudes); any other term reads its partners from the tile.
+    const int RB0 = T - R;
+    const bool lb = RB0 >= L + R;
+    const uint32_t regmaskB = lb ? ((1u << R) - 1u) << RB0 : 0u;
+    uint64_t regphysB = 0;
+    for (int b = RB0; lb && b < T; ++b) regphysB |= sw.ptile[b];
+    auto in_b = [&](const svk::PauliTerm& pt) { return lb && pt.xtile != 0 && (pt.xtile & ~regmaskB) == 0; };
+    // a third layout for terms whose X / Y qubits are all among tile bits 0..L-1: a thread
+    // holds the 2^L amplitudes of one run (threads on tile bits L..T-1); lane l reads
+    // element j ^ (l mod 2^L) of its run into register j, so that the lanes of each load
+    // fall on distinct banks; a term's partner is then register j ^ x, and the lane's
+    // XOR enters only the Z sign (through the fixed-bit value, which includes it)
+    const bool lc = L == R && T - L == T - R;
+    auto in_c = [&](const svk::PauliTerm& pt) {
+        return lc && pt.xtile != 0 && (pt.xtile & ~((1u << L) - 1u)) == 0 && !in_b(pt);
+    };
+    // one term: Re(f sum_k conj(a_k) s_k p_k), with p_k a register of the same layout
+    // (xr: the term's X / Y bits among the layout's register bits) or a tile read
+    auto emit_xy = [&](const svk::PauliTerm& pt, const char* vn, const char* fixn, uint32_t xr, uint32_t sm, bool noz,
+                       uint32_t xthr) {
+        const bool real = (pt.flags & svk::PT_REAL) != 0;
         const int cr = A.F(pt.fre32), ci = real ? -1 : A.F(pt.fim32);
+        auto av = [&](int k) { return fmt("%s%d", vn, k); };
         body += "{\nfloat ar = 0.f, ai = 0.f;\n";
-        const uint32_t low = pt.xreg & (~pt.xreg + 1u);
+        const uint32_t low = xr & (~xr + 1u);
         if (xthr) body += fmt("const float2* const pb = tb + (te ^ %uu);\n", xthr);
         for (int k = 0; k < K; ++k) {
             if (!xthr && (k & (int)low)) continue;   // the pair's other amplitude: its conjugate term
-            const std::string p = xthr ? fmt("pb[%du]", (unsigned)((k ^ pt.xreg) << L)) : amp(k ^ pt.xreg);
-            const char* sg = ((pt.smask >> k) & 1) ? "-" : "";
+            const std::string p = xthr ? fmt("pb[%du]", (unsigned)((k ^ xr) << L)) : av(k ^ (int)xr);
+            const char* sg = ((sm >> k) & 1) ? "-" : "";
             if (xthr) body += fmt("{\nconst float2 p = %s;\n", p.c_str());
             const std::string pp = xthr ? std::string("p") : p;
-            body += fmt("ar = fmaf(%s%s.x, %s.x, fmaf(%s%s.y, %s.y, ar));\n", sg, amp(k).c_str(), pp.c_str(), sg, amp(k).c_str(),
+            body += fmt("ar = fmaf(%s%s.x, %s.x, fmaf(%s%s.y, %s.y, ar));\n", sg, av(k).c_str(), pp.c_str(), sg, av(k).c_str(),
                         pp.c_str());
             if (!real)
-                body += fmt("ai = fmaf(%s%s.x, %s.y, fmaf(%s%s.y, %s.x, ai));\n", sg, amp(k).c_str(), pp.c_str(),
-                            ((pt.smask >> k) & 1) ? "" : "-", amp(k).c_str(), pp.c_str());
+                body += fmt("ai = fmaf(%s%s.x, %s.y, fmaf(%s%s.y, %s.x, ai));\n", sg, av(k).c_str(), pp.c_str(),
+                            ((sm >> k) & 1) ? "" : "-", av(k).c_str(), pp.c_str());
             if (xthr) body += "}\n";
         }
         const std::string v = real ? fmt("a.f[%d] * ar", cr) : fmt("fmaf(a.f[%d], ar, -a.f[%d] * ai)", cr, ci);
         const float scale = xthr ? 1.f : 2.f;
         if (noz) body += fmt("e = fmaf(%.1ff, %s, e);\n", scale, v.c_str());
-        else body += fmt("e = fmaf((__popcll(fix & a.q[%d]) & 1) ? %.1ff : %.1ff, %s, e);\n", A.Q(pt.zmask), -scale, scale, v.c_str());
+        else body += fmt("e = fmaf((__popcll(%s & a.q[%d]) & 1) ? %.1ff : %.1ff, %s, e);\n", fixn, A.Q(pt.zmask), -scale, scale,
+                         v.c_str());
+        body += "}\n";
+    };
+    bool any_b = false, any_c = false;
+    for (uint32_t i = d2; i < nterm; ++i) {
+        const svk::PauliTerm& pt = tl[i];
+        if (in_b(pt)) {
+            any_b = true;
+            continue;
+        }
+        if (in_c(pt)) {
+            any_c = true;
+            continue;
+        }
+        emit_xy(pt, "x", "fix", pt.xreg, pt.smask, (pt.flags & svk::PT_NOZ) != 0, pt.xtile & ~regmask);
+    }
+    if (any_b) {
+        pre += fmt("u64 tphysb = 0;\n#pragma unroll\nfor (int b = 0; b < %d; ++b)\nif ((tid >> b) & 1u) tphysb |= a.q[%d + b];\n",
+                   RB0, QT);
+        body += "{\n";
+        for (int k = 0; k < K; ++k) body += fmt("const float2 y%d = tb[tid | %du];\n", k, (unsigned)k << RB0);
+        body += "const u64 fixb = base | tphysb;\n";
+        for (uint32_t i = d2; i < nterm; ++i) {
+            const svk::PauliTerm& pt = tl[i];
+            if (!in_b(pt)) continue;
+            const uint32_t zr = (tmask(pt.zmask) & regmaskB) >> RB0;
+            uint32_t sm = 0;
+            for (int k = 0; k < K; ++k)
+                if (__builtin_popcount((unsigned)k & zr) & 1) sm |= 1u << k;
+            emit_xy(pt, "y", "fixb", pt.xtile >> RB0, sm, (pt.zmask & ~regphysB) == 0, 0u);
+        }
+        body += "}\n";
+    }
+    if (any_c) {
+        pre += fmt("u64 tphysc = tid & %uu;\n#pragma unroll\nfor (int b = %d; b < %d; ++b)\nif ((tid >> (b - %d)) & 1u) tphysc |= a.q[%d + b];\n",
+                   (1u << L) - 1u, L, T, L, QT);
+        pre += fmt("const u32 tcx = (tid << %d) | (tid & %uu);\n", L, (1u << L) - 1u);
+        body += "{\n";
+        for (int k = 0; k < K; ++k) body += fmt("const float2 z%d = tb[tcx ^ %du];\n", k, k);
+        body += "const u64 fixc = base | tphysc;\n";
+        for (uint32_t i = d2; i < nterm; ++i) {
+            const svk::PauliTerm& pt = tl[i];
+            if (!in_c(pt)) continue;
+            const uint32_t zr = (uint32_t)(pt.zmask & ((1u << L) - 1u));
+            uint32_t sm = 0;
+            for (int k = 0; k < K; ++k)
+                if (__builtin_popcount((unsigned)k & zr) & 1) sm |= 1u << k;
+            emit_xy(pt, "z", "fixc", pt.xtile, sm, pt.zmask == 0, 0u);
+        }
         body += "}\n";
     }
     body += "{\nconst float y = e - ec, s2 = es + y;\nec = (s2 - es) - y;\nes = s2;\n}\n";

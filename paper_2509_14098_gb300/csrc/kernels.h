@@ -36,8 +36,9 @@ struct PermDesc {
     uint64_t pout[16];            // output value of output-tile bit c (ascending output positions)
     uint32_t sig[16];             // swizzled input element offset of output-tile bit c
 };
-cudaError_t launch_permute(int elem_bytes, const void* in, void* out, const PermDesc* d_desc, int T,
-                           uint64_t ntiles, cudaStream_t s);
+// d is passed by value (kernel parameter space); ntiles = 2^(n - d.T)
+cudaError_t launch_permute(int elem_bytes, const void* in, void* out, const PermDesc& d, uint64_t ntiles,
+                           cudaStream_t s);
 
 // Pauli-sum sweep.  A tile fixes the global bits; its T bits are laid out as
 //   tile bits [0, L)       the L lowest physical bits    (thread bits 0..L-1)

@@ -129,6 +129,41 @@ def test_permutation_sweep(sv, seed, dtype):
 
 
 @pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("owned", [False, True])
+def test_permutation_sweep_many_tiles(sv, dtype, owned):
+    """Widths at which every persistent CTA of the permutation sweep takes several tiles
+    (both tile buffers in use, a new global offset per tile): the bit reversal, then a
+    random permutation of the result, on a borrowed buffer (the result is copied back)
+    and on a handle that owns its state (the result buffer becomes the state)."""
+    import ctypes
+    from paper_2509_14098_gb300 import _native as N
+    n = 24 if dtype == 0 else 23
+    npdt = np.complex64 if dtype == 0 else np.complex128
+    psi0 = C.random_state(n, 11).astype(npdt)
+    rev = list(range(n))[::-1]
+    perm = [int(x) for x in np.random.default_rng(11).permutation(n)]
+    want = S.permute_qubits(S.permute_qubits(psi0, n, rev), n, perm)
+    out = np.empty_like(psi0)
+    if owned:
+        h = ctypes.c_void_p()
+        N.check(N.lib.sv_create(n, dtype, None, None, ctypes.byref(h)))
+        try:
+            N.check(N.lib.sv_set_state_host(h, psi0.ctypes.data_as(ctypes.c_void_p)))
+            for p in (rev, perm):
+                N.check(N.lib.sv_permute(h, (ctypes.c_uint32 * n)(*p)))
+            N.check(N.lib.sv_get_state_host(h, out.ctypes.data_as(ctypes.c_void_p)))
+        finally:
+            N.lib.sv_destroy(h)
+    else:
+        st = sv.StateVector(n, dtype)
+        st.set_host(psi0)
+        st.permute(rev)
+        st.permute(perm)
+        out = st.get_host()
+    assert np.array_equal(out, want)   # a pure data move: bit-exact
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
 def test_norm_and_expval(sv, dtype):
     n = 13
     psi = C.random_state(n, 7)
