@@ -55,8 +55,14 @@ typedef enum { SV_C64 = 0, SV_C128 = 1 } sv_dtype;
 
 /* Arithmetic used for stage sweeps.  SV_PREC_CUDACORE: complex FP32 (complex64
  * states) or FP64 (complex128 states) on the CUDA cores.  The split-precision
- * tensor-core modes apply stages fused into dense 2^k x 2^k unitaries as GEMMs. */
-typedef enum { SV_PREC_CUDACORE = 0, SV_PREC_TF32X3 = 1, SV_PREC_BF16X3 = 2 } sv_prec;
+ * tensor-core modes apply stages fused into dense 2^k x 2^k unitaries as GEMMs.
+ * The tensor cores' FP32 accumulation rounds toward zero, so every fused stage
+ * shrinks the state by about 1e-6 of its norm (nearly all of the split-precision
+ * error is this shrink); every stage is unitary, so a tensor-core run restores the
+ * input's norm at its end (an FP64 norm before and after, one scaling sweep).
+ * SV_PREC_NO_RENORM, OR-ed into a tensor-core mode, skips that step (to measure the
+ * raw split-precision error). */
+typedef enum { SV_PREC_CUDACORE = 0, SV_PREC_TF32X3 = 1, SV_PREC_BF16X3 = 2, SV_PREC_NO_RENORM = 0x100 } sv_prec;
 
 /* Gate kinds.  Matrices (Sec. 3.1): H, Pauli X/Y/Z, S = P(pi/2), SDG = P(-pi/2),
  * T = P(pi/4), TDG = P(-pi/4), RX/RY/RZ(t) = exp(-i t {X,Y,Z} / 2),
@@ -317,7 +323,8 @@ sv_status sv_pauli_compile(uint32_t n_qubits, sv_dtype dtype, const sv_observabl
  * of a library-owned handle or is copied back into a borrowed one; complex128
  * stages run in place and then one bit-permutation sweep.  params: host array of the circuit's n_params angles
  * (NULL if n_params == 0).  prec: SV_PREC_CUDACORE, or a tensor-core mode (needs a
- * plan from sv_partition_gemm; one tcgen05 GEMM kernel per partition, then the
+ * plan from sv_partition_gemm or sv_partition_hier; one tcgen05 GEMM kernel per
+ * partition, then the input's norm restored unless SV_PREC_NO_RENORM is set, then the
  * call synchronises to check the kernels' bounded waits, SV_ERR_TIMEOUT if one gave
  * up).  Async for SV_PREC_CUDACORE.
  * Errors: SV_ERR_ARG (width mismatch, null params), SV_ERR_UNSUPPORTED

@@ -10,10 +10,10 @@ import ctypes
 import numpy as np
 
 from . import _native as N
-from ._native import SvError, SV_C64, SV_C128, SV_PREC_CUDACORE, SV_PREC_TF32X3, SV_PREC_BF16X3
+from ._native import SvError, SV_C64, SV_C128, SV_PREC_CUDACORE, SV_PREC_TF32X3, SV_PREC_BF16X3, SV_PREC_NO_RENORM
 
 __all__ = ["Plan", "StateVector", "Batch", "SvError", "partition", "parse_qasm", "SV_C64", "SV_C128",
-           "SV_PREC_CUDACORE", "SV_PREC_TF32X3", "SV_PREC_BF16X3"]
+           "SV_PREC_CUDACORE", "SV_PREC_TF32X3", "SV_PREC_BF16X3", "SV_PREC_NO_RENORM"]
 
 _KIND_NAMES = {v: k for k, v in N.GATE_CODES.items()}
 _N_ANGLES = {"RX": 1, "RY": 1, "RZ": 1, "P": 1, "CP": 1, "U3": 3}

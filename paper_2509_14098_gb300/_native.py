@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(_HERE, "libsvgb300.so")
 SV_OK, SV_ERR_ARG, SV_ERR_OOM, SV_ERR_CUDA, SV_ERR_PARTITION, SV_ERR_UNSUPPORTED, SV_ERR_TIMEOUT = range(7)
 SV_C64, SV_C128 = 0, 1
 SV_PREC_CUDACORE, SV_PREC_TF32X3, SV_PREC_BF16X3 = 0, 1, 2
+SV_PREC_NO_RENORM = 0x100   # OR-ed into a tensor-core mode: keep the raw split-precision result
 STATUS_NAMES = {0: "SV_OK", 1: "SV_ERR_ARG", 2: "SV_ERR_OOM", 3: "SV_ERR_CUDA", 4: "SV_ERR_PARTITION",
                 5: "SV_ERR_UNSUPPORTED", 6: "SV_ERR_TIMEOUT"}
 

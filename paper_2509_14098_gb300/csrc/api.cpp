@@ -978,8 +978,35 @@ static sv_status run_forward(sv_handle h, const sv_plan* plan, const double* par
     return SV_OK;
 }
 
+// FP64 norm of the state into the handle's reduction slot `slot` (device double)
+static sv_status norm_to(sv_handle h, int slot) {
+    SV_CUDA(h->red.ensure((152 * 16 + 16) * sizeof(double)));
+    double* part = (double*)h->red.p + 16;
+    uint32_t nb = 0;
+    cudaEvent_t t0 = tick(h);
+    SV_CUDA(svk::launch_norm(h->eb, h->psi, 1ull << h->n, part, &nb, h->stream));
+    tock(h, t0, TK_OBS);
+    SV_CUDA(svk::launch_reduce_rows(part, nb, 1, (double*)h->red.p + slot, h->stream));
+    h->info.kernel_launches += 2;
+    h->info.hbm_bytes += (double)state_bytes(h);
+    return SV_OK;
+}
+
+// After tensor-core stages: scale the state back to the norm it had before them (the
+// accumulators' round-toward-zero shrinks every fused stage's output slightly; the
+// stages are unitary, so the exact result has the input's norm)
+static sv_status restore_norm(sv_handle h) {
+    sv_status s = norm_to(h, 3);
+    if (s) return s;
+    const double* r = (const double*)h->red.p;
+    SV_CUDA(svk::launch_scale_to_norm(h->eb, h->psi, 1ull << h->n, r + 2, r + 3, h->stream));
+    h->info.kernel_launches += 1;
+    h->info.hbm_bytes += 2.0 * (double)state_bytes(h);
+    return SV_OK;
+}
+
 // hierarchical tensor-core stages: one launch per run of sub-partitions of a stage
-static sv_status run_hier(sv_handle h, const sv_plan* plan, const double* params, int prec) {
+static sv_status run_hier(sv_handle h, const sv_plan* plan, const double* params, int prec, bool renorm) {
     const svh::Plan& P = plan->plan;
     svh::HierProgram hp;
     std::string err = svh::plan_hier(P, params, prec, &hp);
@@ -994,6 +1021,10 @@ static sv_status run_hier(sv_handle h, const sv_plan* plan, const double* params
     std::memcpy(h->gemm_host.data() + aoff, hp.ublob.data(), hp.ublob.size());
     SV_CUDA(cudaMemcpyAsync(h->gemm.p, h->gemm_host.data(), total, cudaMemcpyHostToDevice, h->stream));
     SV_CUDA(cudaMemsetAsync(h->status.p, 0, sizeof(int), h->stream));
+    if (renorm) {
+        sv_status s0 = norm_to(h, 2);
+        if (s0) return s0;
+    }
     for (size_t i = 0; i < hp.launches.size(); ++i) {
         cudaEvent_t t0 = tick(h);
         SV_CUDA(svk::launch_hier_stage(prec, h->psi, (const svk::HierStage*)h->gemm.p + i, hp.launches[i],
@@ -1009,6 +1040,10 @@ static sv_status run_hier(sv_handle h, const sv_plan* plan, const double* params
         sv_status s = do_permute(h, m.data());
         if (s) return s;
     }
+    if (renorm) {
+        sv_status s = restore_norm(h);
+        if (s) return s;
+    }
     int st = 0;
     SV_CUDA(cudaMemcpyAsync(&st, h->status.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     SV_CUDA(cudaStreamSynchronize(h->stream));
@@ -1016,7 +1051,7 @@ static sv_status run_hier(sv_handle h, const sv_plan* plan, const double* params
     return SV_OK;
 }
 
-static sv_status run_gemm(sv_handle h, const sv_plan* plan, const double* params, int prec) {
+static sv_status run_gemm(sv_handle h, const sv_plan* plan, const double* params, int prec, bool renorm) {
     const svh::Plan& P = plan->plan;
     svh::GemmProgram gp;
     std::string err = svh::plan_gemm(P, params, prec, &gp);
@@ -1033,6 +1068,10 @@ static sv_status run_gemm(sv_handle h, const sv_plan* plan, const double* params
     std::memcpy(h->gemm_host.data() + aoff, gp.ublob.data(), gp.ublob.size());
     SV_CUDA(cudaMemcpyAsync(h->gemm.p, h->gemm_host.data(), total, cudaMemcpyHostToDevice, h->stream));
     SV_CUDA(cudaMemsetAsync(h->status.p, 0, sizeof(int), h->stream));
+    if (renorm) {
+        sv_status s0 = norm_to(h, 2);
+        if (s0) return s0;
+    }
     for (size_t i = 0; i < gp.stages.size(); ++i) {
         cudaEvent_t t0 = tick(h);
         SV_CUDA(svk::launch_gemm_stage(prec, h->psi, (const svk::GemmStage*)h->gemm.p + i, gp.stages[i],
@@ -1046,6 +1085,10 @@ static sv_status run_gemm(sv_handle h, const sv_plan* plan, const double* params
         std::vector<uint32_t> m(P.n);
         for (int q = 0; q < P.n; ++q) m[q] = (uint32_t)P.final_map[q];
         sv_status s = do_permute(h, m.data());
+        if (s) return s;
+    }
+    if (renorm) {
+        sv_status s = restore_norm(h);
         if (s) return s;
     }
     int st = 0;
@@ -1104,12 +1147,14 @@ sv_status sv_run(sv_handle h, const sv_plan* plan, const double* params, sv_prec
     if (plan->plan.n != (int)h->n) return fail(SV_ERR_ARG, "plan width differs from the state");
     if (plan->plan.n_params > 0 && !params) return fail(SV_ERR_ARG, "params is NULL");
     h->info = sv_run_info{};
-    if (prec == SV_PREC_TF32X3 || prec == SV_PREC_BF16X3) {
+    const int mode = (int)prec & ~(int)SV_PREC_NO_RENORM;
+    const bool renorm = ((int)prec & (int)SV_PREC_NO_RENORM) == 0;
+    if (mode == SV_PREC_TF32X3 || mode == SV_PREC_BF16X3) {
         if (plan->plan.gemm_k == 0 && plan->plan.hier_k == 0)
             return fail(SV_ERR_UNSUPPORTED, "tensor-core precision needs a plan from sv_partition_gemm or sv_partition_hier");
         if (h->dt != SV_C64) return fail(SV_ERR_UNSUPPORTED, "tensor-core stages operate on complex64 states");
-        if (plan->plan.hier_k) return run_hier(h, plan, params, prec == SV_PREC_TF32X3 ? 1 : 2);
-        return run_gemm(h, plan, params, prec == SV_PREC_TF32X3 ? 1 : 2);
+        if (plan->plan.hier_k) return run_hier(h, plan, params, mode == SV_PREC_TF32X3 ? 1 : 2, renorm);
+        return run_gemm(h, plan, params, mode == SV_PREC_TF32X3 ? 1 : 2, renorm);
     }
     if (prec != SV_PREC_CUDACORE) return fail(SV_ERR_ARG, "bad precision");
     return run_forward(h, plan, params, true);

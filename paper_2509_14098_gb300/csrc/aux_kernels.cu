@@ -602,6 +602,51 @@ cudaError_t launch_norm(int elem_bytes, const void* psi, uint64_t n_amp, double*
     return cudaGetLastError();
 }
 
+// psi *= sqrt(norm_before / norm_after): the norm restoration after tensor-core stages
+template <typename C>
+__global__ void __launch_bounds__(256) k_scale_to_norm(C* __restrict__ psi, uint64_t n_amp,
+                                                       const double* __restrict__ nb, const double* __restrict__ na) {
+    const double b = *nb, a = *na;
+    if (!(b > 0.0) || !(a > 0.0)) return;
+    const double f = sqrt(b / a);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    if (sizeof(C) == 8) {
+        const float ff = (float)f;
+        float4* p = reinterpret_cast<float4*>(psi);
+        const uint64_t n4 = n_amp / 2;
+        for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+            float4 v = p[i];
+            v.x *= ff;
+            v.y *= ff;
+            v.z *= ff;
+            v.w *= ff;
+            p[i] = v;
+        }
+        if ((n_amp & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+            float2* q = reinterpret_cast<float2*>(psi) + (n_amp - 1);
+            q->x *= ff;
+            q->y *= ff;
+        }
+    } else {
+        double2* p = reinterpret_cast<double2*>(psi);
+        for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_amp; i += stride) {
+            double2 v = p[i];
+            v.x *= f;
+            v.y *= f;
+            p[i] = v;
+        }
+    }
+}
+
+cudaError_t launch_scale_to_norm(int elem_bytes, void* psi, uint64_t n_amp, const double* norm_before,
+                                 const double* norm_after, cudaStream_t s) {
+    const uint64_t want = (n_amp + 2047) / 2048;
+    const uint32_t nb = (uint32_t)(want < 152ull * 16 ? (want ? want : 1) : 152ull * 16);
+    if (elem_bytes == 8) k_scale_to_norm<float2><<<nb, 256, 0, s>>>((float2*)psi, n_amp, norm_before, norm_after);
+    else k_scale_to_norm<double2><<<nb, 256, 0, s>>>((double2*)psi, n_amp, norm_before, norm_after);
+    return cudaGetLastError();
+}
+
 // out[r] = sum_i in[i * rows + r], one block per row, strided fixed-order sums and a
 // fixed tree: the result does not depend on timing.
 __global__ void __launch_bounds__(256) k_reduce_rows(const double* __restrict__ in, uint64_t n,

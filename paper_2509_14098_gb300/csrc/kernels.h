@@ -87,6 +87,9 @@ cudaError_t launch_norm(int elem_bytes, const void* psi, uint64_t n_amp, double*
 // out[r] = sum_{i < n} in[i * stride + r] for r < rows, fixed order (one block per row).
 cudaError_t launch_reduce_rows(const double* in, uint64_t n, uint32_t rows, double* out,
                                cudaStream_t s);
+// psi *= sqrt(*norm_before / *norm_after) (device doubles; unchanged if either is 0)
+cudaError_t launch_scale_to_norm(int elem_bytes, void* psi, uint64_t n_amp, const double* norm_before,
+                                 const double* norm_after, cudaStream_t s);
 // state set to |0...0>
 cudaError_t launch_zero_state(int elem_bytes, void* psi, uint64_t n_amp, cudaStream_t s);
 

@@ -12,9 +12,12 @@ worst case per element), which the unitary carries unchanged into the output; th
 of the fixed unitary is a perturbation of the same relative size per entry, measured
 inside u for these dense unitaries (a 5-qubit BF16x3 GEMM: 4.4e-6).  `gemm_eps` is the
 sum of the two terms; the state bound sums it over the GEMMs (`derived_bound`,
-`hier_bound`).  At 26 and 32 qubits (60-97 stages) the measured error is 5e-5 to 1e-4:
-the target's 2e-5 on the state is missed there, and the
-tests hold the derived bound instead of widening the target.
+`hier_bound`).  At 26 and 32 qubits (60-97 stages) the raw error (SV_PREC_NO_RENORM) is
+5e-5 to 1e-4, almost all of it a shrink of the norm: the tensor cores' accumulation
+rounds toward zero.  Every stage is unitary, so a tensor-core run restores the input's
+norm at its end (the default); what remains is the error orthogonal to the exact state,
+which TF32x3 holds to the target's 2e-5 at 26 qubits and BF16x3 (whose 2^-16 split of
+the state is the larger term) does not.  The raw runs are held to the derived bound.
 """
 import numpy as np
 import pytest
@@ -167,20 +170,33 @@ def test_brick26_vs_oracle(sv, brick26, brick26_c128, k, prec):
     n = circ.n_qubits
     plan = sv.Plan(circ, k, gemm=True)
     st = sv.StateVector(n)
-    st.set_host(psi0)
-    st.run(plan, None, prec)
-    got = st.get_host().astype(np.complex128)
-    bound = derived_bound(plan, prec)
-    err = float(np.linalg.norm(got - brick26_c128))
     idx = np.array(gold["indices"])
     amp = np.array([complex(a, b) for a, b in gold["amplitudes"]])
-    samp = float(np.max(np.abs(got[idx] - amp)))
-    zerr = float(np.max(np.abs(_z_expectations(sv, st, n) - np.array(gold["z_expectations"]))))
+    n0 = float(np.vdot(psi0.astype(np.complex128), psi0.astype(np.complex128)).real)
+    res = {}
+    for mode in ("raw", "restored"):
+        st.set_host(psi0)
+        st.run(plan, None, prec | (sv.SV_PREC_NO_RENORM if mode == "raw" else 0))
+        got = st.get_host().astype(np.complex128)
+        res[mode] = (float(np.linalg.norm(got - brick26_c128)), float(np.max(np.abs(got[idx] - amp))),
+                     float(np.max(np.abs(_z_expectations(sv, st, n) - np.array(gold["z_expectations"])))),
+                     float(np.vdot(got, got).real) - n0)
     st.close()
-    print(f"brick26 k={k} prec={prec} stages={len(plan.stages())} err_vs_c128={err:.3e} "
-          f"max_sample_err={samp:.3e} max_Z_err={zerr:.3e} bound={bound:.3e} target=2e-5")
+    bound = derived_bound(plan, prec)
+    for mode, (err, samp, zerr, dn) in res.items():
+        print(f"brick26 k={k} prec={prec} {mode} stages={len(plan.stages())} err_vs_c128={err:.3e} "
+              f"max_sample_err={samp:.3e} max_Z_err={zerr:.3e} norm2_change={dn:.2e} bound={bound:.3e} target=2e-5")
+    err, samp, zerr, dn = res["raw"]
     assert err <= bound, (err, bound)
     assert samp <= bound and zerr <= 2 * bound
+    assert dn < 0   # the raw result has lost norm
+    err, samp, zerr, dn = res["restored"]
+    assert abs(dn) <= 1e-6 * n0
+    assert err <= res["raw"][0]
+    if prec == 1:   # TF32x3 meets the target once the norm is restored
+        assert err <= 2e-5 and samp <= 2e-5 and zerr <= 4e-5, (err, samp, zerr)
+    else:
+        assert err <= bound and samp <= bound and zerr <= 2 * bound
 
 
 @pytest.mark.parametrize("k", [5, 6, 7])
