@@ -127,6 +127,14 @@ bool tma_runs(const svk::Stage& st, int n, int nv, std::vector<Run>* dims) {
     return ok && want;
 }
 
+// An uncontrolled real 2x2 of the form c [[1, 1], [1, -1]] (the Hadamard): a forward
+// stage applies it as the butterfly (x0 + x1, x0 - x1) and multiplies the product of
+// the factors c into every amplitude once, at the end of the stage
+bool h_like(const svk::DevOp<float>& o) {
+    return o.type == svk::OP_UR && !(o.flags & svk::F_BIND) && o.ctrl_fix == 0 && o.ctrl_reg == 0 && o.m[0] != 0.f &&
+           o.m[2] == o.m[0] && o.m[4] == o.m[0] && o.m[6] == -o.m[0];
+}
+
 class Gen {
   public:
     Gen(const StageView& v, Built* out) : V(v), st(*v.st), B(out) {}
@@ -142,6 +150,8 @@ class Gen {
     bool ttab = false;        // per-(slot, thread) thread-bit angle table in shared memory
     bool cbank = false;       // per-op constants read from the parameter bank (else shared memory)
     bool tma = false;         // tiles staged by TMA (128-byte swizzle) instead of cp.async (software swizzle)
+    bool hdefer = false;      // Hadamard-like ops as butterflies, their factor applied once per stage
+    double hscale = 1.0;      // product of the deferred factors
     int NS = 2;               // TMA ring slots (set in run())
     uint32_t swz(uint32_t e) const { return tma ? (e ^ (((e >> 4) & 7u) << 1)) : svk::swizzle8(e); }
     std::vector<std::vector<int>> tbo;   // per group: tile bit of each thread bit
@@ -261,6 +271,10 @@ std::string Gen::dense(const svk::DevOp<float>& o, int gi) {
                 std::swap(perm[k], perm[k | bj]);   // a relabel of registers: no instruction
             }
         }
+    } else if (o.type == svk::OP_UR && hdefer && h_like(o)) {
+        hscale *= (double)o.m[0];
+        for (int k = 0; k < K; ++k)
+            if (selected(k)) r += fmt("svj_hb(%s, %s);\n", amp(0, k).c_str(), amp(0, k | bj).c_str());
     } else if (o.type == svk::OP_UR) {
         const int m0 = A.F(o.m[0]), m2 = A.F(o.m[2]), m4 = A.F(o.m[4]), m6 = A.F(o.m[6]);
         if (o.flags & svk::F_BIND) binds.push_back({m0, svk::OP_UR, o.u, (int)o.term_off});
@@ -426,6 +440,8 @@ std::string Gen::run() {
     if (R < 1 || R > 5 || TR < 0 || TR > 9 || T > svk::kMaxT) return "jit: unsupported tile shape";
     if (st.tile_pos[0] != 0) return "jit: the tile must hold physical bit 0";
     BM = V.batched;
+    // (not with lambda or gradients in the same kernel: those read the amplitudes mid-stage)
+    hdefer = NV == 1 && !BM;
     ZI = V.zero_init;
     if (!BM)
         for (uint32_t i = 0; i < st.n_ops; ++i)
@@ -737,6 +753,11 @@ std::string Gen::run() {
         zgen = -1;
         for (uint32_t oi = 0; oi < G.n_ops; ++oi) gcode += op(V.ops[G.op_off + oi], g);
         gcode += reduce_pending();
+        if (g == ng - 1 && hscale != 1.0) {   // the deferred Hadamard factors, once
+            const int fi = A.F((float)hscale);
+            for (int k = 0; k < K; ++k)
+                gcode += fmt("%s = __fmul2_rn(make_float2(S.f[%d], S.f[%d]), %s);\n", amp(0, k).c_str(), fi, fi, amp(0, k).c_str());
+        }
         for (int v = 0; v < NV; ++v) {
             if (pairs) {
                 for (int k = 0; k < K; k += 2)
@@ -1011,6 +1032,7 @@ std::string structure_key(const StageView& v) {
         const svk::DevOp<float>& o = v.ops[i];
         put(o.type | (uint64_t)o.j << 8 | (uint64_t)o.u << 16 | (uint64_t)o.flags << 24 | (uint64_t)(o.ctrl_fix != 0) << 32);
         put(o.ctrl_reg);
+        put(h_like(o) ? 1 : 0);
         put(o.slot);
         put(o.n_terms);
         if (o.flags & (svk::F_TERMS | svk::F_TW))

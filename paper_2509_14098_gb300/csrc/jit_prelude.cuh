@@ -32,6 +32,14 @@ SVJ_DI void svj_ur(float2& x0, float2& x1, float m0, float m2, float m4, float m
     x1 = y1;
 }
 
+// Hadamard butterfly without its factor: (x0, x1) -> (x0 + x1, x0 - x1) (packed FP32x2)
+SVJ_DI void svj_hb(float2& x0, float2& x1) {
+    const float2 y0 = __ffma2_rn(make_float2(1.f, 1.f), x1, x0);
+    const float2 y1 = __ffma2_rn(make_float2(-1.f, -1.f), x1, x0);
+    x0 = y0;
+    x1 = y1;
+}
+
 // complex 2x2 on a pair; m = row-major (re, im) pairs
 SVJ_DI void svj_u(float2& x0, float2& x1, float m0, float m1, float m2, float m3, float m4, float m5,
                   float m6, float m7) {
