@@ -196,7 +196,8 @@ sv_status sv_timing_read(sv_handle h, sv_timing* out, int reset);
  * L is the width of the shared-memory tile in qubits.  sv_partition reserves the
  * min(4, L - 1, n) lowest physical qubits in every partition: a tile must contain them
  * so that each HBM access is a contiguous run of >= 128 bytes.  The plan is
- * deterministic, library-owned, independent of any handle and of the dtype.
+ * deterministic, library-owned, independent of any handle and of the dtype.  A
+ * circuit with no gates has no partitions (running it leaves the state unchanged).
  * Errors: SV_ERR_ARG (bad circuit: qubit out of range, unknown kind, bad param
  * slot; L < 1 or > 14), SV_ERR_PARTITION (a gate's qubits cannot be made local). */
 sv_status sv_partition(const sv_circuit* circuit, uint32_t L, sv_plan** out);
@@ -384,10 +385,12 @@ sv_status sv_norm_noalloc(const void* dev_state, uint32_t n_qubits, sv_dtype dty
  * forward circuit from the current state, forms lambda = O psi, then un-applies
  * the partitions in reverse to psi and lambda together while accumulating
  * dE/dtheta_p = 2 Re <lambda| dU_p/dtheta psi> for every parameter (RX, RY, RZ
- * parameters supported).  On return the handle holds psi(theta) (forward result).
- * expval_out (host, may be NULL) receives E; grad_out (host, n_params) the
- * gradient.  Synchronises.  Errors: SV_ERR_UNSUPPORTED for parameters on other
- * gate kinds. */
+ * parameters supported).  On return the handle holds the backward pass's
+ * reconstruction of the input state (the circuit un-applied: the input up to
+ * rounding).  expval_out (host, may be NULL) receives E; grad_out (host, n_params)
+ * the gradient.  Synchronises.  Errors: SV_ERR_UNSUPPORTED for parameters on other
+ * gate kinds, and for partitions whose psi and lambda tiles together exceed shared
+ * memory (L = 14 for complex64, L >= 13 for complex128). */
 sv_status sv_grad(sv_handle h, const sv_plan* plan, const double* params, const sv_observable* obs,
                   double* expval_out, double* grad_out);
 

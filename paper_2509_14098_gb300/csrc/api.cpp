@@ -708,7 +708,6 @@ static sv_status build_plan(const sv_circuit* c, uint32_t L, uint32_t n_fixed, s
     if (!c || (c->n_gates && !c->gates)) return fail(SV_ERR_ARG, "null circuit");
     if (c->n_qubits < 1 || c->n_qubits > (uint32_t)svk::kMaxQ) return fail(SV_ERR_ARG, "n_qubits out of range");
     if (L < 1 || L > (uint32_t)svk::kMaxT) return fail(SV_ERR_ARG, "L must be in [1, 14]");
-    if (c->n_gates == 0) return fail(SV_ERR_ARG, "empty circuit");
     if (c->n_gates > 32768) return fail(SV_ERR_ARG, "more than 32768 gates");
     std::vector<svh::GateRec> gates;
     std::string gerr = svh::gates_from_circuit(c, &gates);

@@ -392,6 +392,8 @@ std::string Lowerer::stage(int s) {
     for (int b = 0; b < n; ++b)
         if (!((tile >> b) & 1)) st.glob_pos[ng++] = (uint8_t)b;
     int R = std::min(rmax_, T);
+    // at most 2^9 threads per tile: a 14-qubit complex64 forward tile takes 5 register bits
+    if (T - R > 9 && eb_ == 8 && !bwd_) R = std::min(5, T);
     st.T = (uint32_t)T;
     st.n_glob = (uint32_t)ng;
     for (int b = 0; b < T; ++b) {
@@ -476,7 +478,7 @@ std::string Lowerer::run() {
     out_->slot_param.clear();
     out_->groups.reserve(4096);
     const int S = (int)P_.top.local.size();
-    if (S == 0) return "empty plan";
+    // S == 0: an empty circuit, whose program has no stages (the identity)
     for (int k = 0; k < S; ++k) {
         int s = bwd_ ? S - 1 - k : k;
         std::string err = stage(s);

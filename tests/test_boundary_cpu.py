@@ -56,7 +56,8 @@ def _native_partition(sv, c, L, nf):
 
 
 CASES = [(C.ghz(3), 2, 0), (C.ghz(9), 3, 0), (C.qft(8), 3, 0), (C.qft(10), 5, 4),
-         (C.brickwork(10, 6, 1), 4, 2), (C.hea(7, 3), 6, 4), (C.qft_roundtrip(12), 6, 4)]
+         (C.brickwork(10, 6, 1), 4, 2), (C.hea(7, 3), 6, 4), (C.qft_roundtrip(12), 6, 4),
+         (C.Circuit(5, []), 3, 0)]   # the empty circuit: no stages
 
 
 @pytest.mark.parametrize("c,L,nf", CASES)

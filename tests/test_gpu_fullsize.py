@@ -2,6 +2,8 @@
 times), where the oracle cannot hold the whole state:
 
 * QFT30 then inverse QFT (960 gates, L = 11) is the identity: ||psi_out - psi_in||_2 <= 2e-5.
+* QFT34 then inverse QFT on the largest state that fits (2^34 complex64, 137 GB): sampled
+  amplitudes return to their inputs and the norm is kept.
 * QFT30 alone: sampled output amplitudes against the oracle's definition of the DFT
   amplitude (computed one by one in FP64), and the whole vector against cuFFT.
   Per sample the bound is 2e-5 relative: the target's 2e-5 on the unit-norm vector
@@ -54,6 +56,36 @@ def test_qft30_roundtrip_identity(sv):
     assert err <= 2e-5, err
     assert st.run_info()["permutation_sweeps"] == 0
     assert abs(st.norm() - 1.0) <= 1e-5
+
+
+def test_qft34_roundtrip_largest_state(sv):
+    """The largest complex64 state that fits one GB300 with room to spare (2^34
+    amplitudes, 137 GB; the roundtrip's relabels cancel, so no second state buffer):
+    the QFT roundtrip returns 4096 sampled amplitudes to their inputs, within 1e-4 of
+    the root-mean-square amplitude (the roundtrip's vector error is about 3e-6 of the
+    norm; a misplaced amplitude would be off by O(1)), and keeps the norm."""
+    import torch
+    n = 34
+    free, _ = torch.cuda.mem_get_info()
+    if free < (1 << n) * 8 + (8 << 30):
+        pytest.skip("needs 2^34 complex64 amplitudes of free device memory")
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    psi = torch.randn(1 << n, dtype=torch.complex64, device="cuda", generator=g)
+    st = sv.StateVector(n, tensor=psi)
+    nrm = st.norm()
+    idx = torch.randint(0, 1 << n, (4096,), device="cuda", generator=g)
+    before = psi[idx].clone()
+    st.run(sv.Plan(C.qft_roundtrip(n), 11))
+    torch.cuda.synchronize()
+    rms = (nrm / (1 << n)) ** 0.5
+    err = float((psi[idx] - before).abs().max().item())
+    assert err <= 1e-4 * rms, err
+    assert abs(st.norm() / nrm - 1.0) <= 1e-5
+    assert st.run_info()["permutation_sweeps"] == 0
+    st.close()
+    del psi, before
+    torch.cuda.empty_cache()
 
 
 def test_qft30_sampled_outputs(sv):

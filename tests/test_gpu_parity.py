@@ -189,6 +189,36 @@ def test_tiny_states(sv, n):
     assert abs(st.expval(obs) - O.expval(got, obs)) <= 1e-6 * max(1, abs(O.expval(got, obs)))
 
 
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_degenerate_circuits(sv, dtype):
+    """The method's degenerate cases: an empty circuit leaves the state bit-exact; a
+    circuit of diagonal gates only (every gate exempt, one stage with no dense op); a
+    circuit of SWAPs only (pure relabels: the state moves by the final qubit map only,
+    bit-exact); a budget L >= n (the whole state is one tile)."""
+    n = 14
+    psi0 = C.random_state(n, 21)
+    npdt = np.complex64 if dtype == 0 else np.complex128
+    tol = TOL[dtype]
+    got, _, _ = run_gpu(sv, C.Circuit(n, []), 11, psi0, dtype)
+    assert np.array_equal(got, psi0.astype(npdt).astype(np.complex128))
+    rng = np.random.default_rng(21)
+    diag = C.Circuit(n, [C.Gate(k, tuple(int(q) for q in rng.choice(n, 2 if k in ("CZ", "CP") else 1, replace=False)), -1,
+                                (float(rng.uniform(0, 2 * np.pi)),) if k in ("RZ", "P", "CP") else ())
+                         for k in map(str, rng.choice(["Z", "S", "T", "SDG", "TDG", "RZ", "P", "CZ", "CP"], 60))])
+    got, _, _ = run_gpu(sv, diag, 11, psi0, dtype)
+    assert np.linalg.norm(got - S.simulate(diag, None, psi0)) <= tol
+    swaps = C.Circuit(n, [C.Gate("SWAP", tuple(int(q) for q in rng.choice(n, 2, replace=False))) for _ in range(9)])
+    got, st, _ = run_gpu(sv, swaps, 11, psi0, dtype)
+    assert np.array_equal(got, S.simulate(swaps, None, psi0.astype(npdt).astype(np.complex128)))
+    assert st.run_info()["stage_sweeps"] + st.run_info()["permutation_sweeps"] <= 2
+    n1 = 14 if dtype == 0 else 13   # the widest tile of the dtype (128 KB / 128 KB)
+    c = C.random_circuit(n1, 120, 5)
+    psi1 = C.random_state(n1, 22)
+    got, st, _ = run_gpu(sv, c, n1, psi1, dtype)
+    assert np.linalg.norm(got - S.simulate(c, None, psi1)) <= tol
+    assert st.run_info()["stage_sweeps"] == 1
+
+
 @pytest.fixture(scope="module")
 def hea12_reference():
     """The differentiation workload at oracle size (12 qubits, 10 layers, 240
