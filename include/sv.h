@@ -337,6 +337,17 @@ sv_status sv_run(sv_handle h, const sv_plan* plan, const double* params, sv_prec
  * this sweep).  phys_of_qubit: host array of n entries, a permutation. */
 sv_status sv_permute(sv_handle h, const uint32_t* phys_of_qubit);
 
+/* The tile sv_permute uses for phys_of_qubit on an n_qubits state of dtype, computed on
+ * the host (no GPU, no handle; an introspection call with no counterpart in the paper):
+ * *tile_bits = the tile's width T (12 for complex64, 11 for complex128, n if smaller),
+ * *tile_mask = its input physical bits (the lowest 4, the inputs of output bits 0..3,
+ * then alternately widening the contiguous input and output runs), *in_run = the number
+ * of lowest input bits it holds contiguously (a read is a run of 2^in_run amplitudes),
+ * *out_run = the same for the output bits.  Errors: SV_ERR_ARG (null pointer, bad width
+ * or dtype, not a permutation). */
+sv_status sv_permute_plan_info(uint32_t n_qubits, sv_dtype dtype, const uint32_t* phys_of_qubit, uint32_t* tile_bits,
+                               uint64_t* tile_mask, uint32_t* in_run, uint32_t* out_run);
+
 /* <psi|O|psi> for a Pauli sum (Sec. 4.2's observable, evaluated by Pauli sweeps:
  * one read of psi per group of X/Y-carrying terms whose X/Y qubits fit one tile of 13
  * (complex64) or 12 (complex128) qubits together with qubits 0..3; the diagonal terms

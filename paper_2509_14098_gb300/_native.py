@@ -103,6 +103,8 @@ _SIGS = {
     "sv_plan_centrality": ([_vp, ctypes.POINTER(_u32), ctypes.POINTER(_u64), ctypes.POINTER(_u32)], ctypes.c_int),
     "sv_plan_destroy": ([_vp], ctypes.c_int),
     "sv_plan_compile": ([_vp, _dp, _u32, ctypes.POINTER(_u32)], ctypes.c_int),
+    "sv_permute_plan_info": ([_u32, ctypes.c_int, ctypes.POINTER(_u32), ctypes.POINTER(_u32), ctypes.POINTER(ctypes.c_uint64),
+                              ctypes.POINTER(_u32), ctypes.POINTER(_u32)], ctypes.c_int),
     "sv_pauli_compile": ([_u32, ctypes.c_int, ctypes.POINTER(sv_observable), ctypes.POINTER(_u32)], ctypes.c_int),
     "sv_jit_stats": ([ctypes.POINTER(_u64), ctypes.POINTER(_u64), _dp], ctypes.c_int),
     "sv_qasm_parse": ([ctypes.c_char_p, ctypes.POINTER(sv_gate), _u32, ctypes.POINTER(_u32), ctypes.POINTER(_u32)],

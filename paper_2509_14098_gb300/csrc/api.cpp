@@ -219,31 +219,17 @@ static sv_status jflag_check(sv_handle h) {
 // ---------------------------------------------------------------------------
 // permutation sweep: new[y] = old[x], bit phys_of_qubit[q] of x = bit q of y
 // ---------------------------------------------------------------------------
-static sv_status do_permute(sv_handle h, const uint32_t* phys_of_qubit) {
-    const int n = (int)h->n;
-    int dst[64];
-    {
-        uint64_t seen = 0;
-        for (int q = 0; q < n; ++q) {
-            uint32_t p = phys_of_qubit[q];
-            if (p >= (uint32_t)n || ((seen >> p) & 1)) return fail(SV_ERR_ARG, "not a permutation");
-            seen |= 1ull << p;
-            dst[p] = q;
-        }
-    }
-    bool ident = true;
-    for (int p = 0; p < n; ++p)
-        if (dst[p] != p) ident = false;
-    if (ident) return SV_OK;
-    // tile: the input's 4 lowest bits and the input bits that land on output bits 0..3,
-    // then alternately the next input bit above the contiguous input run and the input
-    // bit that lands just above the contiguous output run, so that both the reads and
-    // the writes are runs of at least 512 bytes (2^12 complex64 / 2^11 complex128)
+// Tile of the permutation sweep (input physical bits): the input's 4 lowest bits and the
+// input bits that land on output bits 0..3, then alternately the next input bit above
+// the contiguous input run and the input bit that lands just above the contiguous output
+// run, so that both the reads and the writes are runs of at least 512 bytes (2^12
+// complex64 / 2^11 complex128).  dst[p] = the output bit of input bit p.
+static uint64_t perm_tile(int n, int eb, const uint32_t* phys_of_qubit, const int* dst, int* T) {
     const int c = std::min(4, n);
     uint64_t B = (1ull << c) - 1;
     for (int p = 0; p < n; ++p)
         if (dst[p] < c) B |= 1ull << p;
-    const int Tp = std::min(n, h->eb == 8 ? 12 : 11);
+    const int Tp = std::min(n, eb == 8 ? 12 : 11);
     for (int turn = 0, ri = 0, ro = 0; __builtin_popcountll(B) < Tp; turn ^= 1) {
         while (ri < n && ((B >> ri) & 1)) ++ri;
         while (ro < n && ((B >> phys_of_qubit[ro]) & 1)) ++ro;
@@ -251,6 +237,32 @@ static sv_status do_permute(sv_handle h, const uint32_t* phys_of_qubit) {
         else if (ro < n) B |= 1ull << phys_of_qubit[ro];
         else if (ri < n) B |= 1ull << ri;
     }
+    *T = Tp;
+    return B;
+}
+
+// dst[p] from phys_of_qubit (false: not a permutation of 0..n-1)
+static bool perm_dst(int n, const uint32_t* phys_of_qubit, int* dst) {
+    uint64_t seen = 0;
+    for (int q = 0; q < n; ++q) {
+        const uint32_t p = phys_of_qubit[q];
+        if (p >= (uint32_t)n || ((seen >> p) & 1)) return false;
+        seen |= 1ull << p;
+        dst[p] = q;
+    }
+    return true;
+}
+
+static sv_status do_permute(sv_handle h, const uint32_t* phys_of_qubit) {
+    const int n = (int)h->n;
+    int dst[64];
+    if (!perm_dst(n, phys_of_qubit, dst)) return fail(SV_ERR_ARG, "not a permutation");
+    bool ident = true;
+    for (int p = 0; p < n; ++p)
+        if (dst[p] != p) ident = false;
+    if (ident) return SV_OK;
+    int Tp = 0;
+    const uint64_t B = perm_tile(n, h->eb, phys_of_qubit, dst, &Tp);
     svk::PermDesc d;
     std::memset(&d, 0, sizeof(d));
     d.T = (uint32_t)Tp;
@@ -1191,6 +1203,26 @@ sv_status sv_expval(sv_handle h, const sv_observable* obs, double* out) {
     SV_CUDA(cudaMemcpyAsync(out, h->red.p, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     SV_CUDA(cudaStreamSynchronize(h->stream));
     return jflag_check(h);
+}
+
+sv_status sv_permute_plan_info(uint32_t n_qubits, sv_dtype dtype, const uint32_t* phys_of_qubit, uint32_t* tile_bits,
+                               uint64_t* tile_mask, uint32_t* in_run, uint32_t* out_run) {
+    if (!phys_of_qubit || !tile_bits || !tile_mask || !in_run || !out_run) return fail(SV_ERR_ARG, "null argument");
+    if (n_qubits < 1 || n_qubits > (uint32_t)svk::kMaxQ) return fail(SV_ERR_ARG, "n_qubits out of range");
+    if (dtype != SV_C64 && dtype != SV_C128) return fail(SV_ERR_ARG, "bad dtype");
+    const int n = (int)n_qubits;
+    int dst[64];
+    if (!perm_dst(n, phys_of_qubit, dst)) return fail(SV_ERR_ARG, "not a permutation");
+    int T = 0;
+    const uint64_t B = perm_tile(n, dtype == SV_C64 ? 8 : 16, phys_of_qubit, dst, &T);
+    uint32_t ri = 0, ro = 0;
+    while ((int)ri < n && ((B >> ri) & 1)) ++ri;
+    while ((int)ro < n && ((B >> phys_of_qubit[ro]) & 1)) ++ro;
+    *tile_bits = (uint32_t)T;
+    *tile_mask = B;
+    *in_run = ri;
+    *out_run = ro;
+    return SV_OK;
 }
 
 sv_status sv_pauli_plan_info(uint32_t n_qubits, sv_dtype dtype, const sv_observable* obs, uint32_t* n_sweeps,
