@@ -96,6 +96,9 @@ __global__ void __launch_bounds__(kPermThreads, 3) k_permute(const C* __restrict
 cudaError_t launch_permute(int elem_bytes, const void* in, void* out, const PermDesc& d, uint64_t ntiles,
                            cudaStream_t s) {
     const size_t smem = 2 * ((size_t)elem_bytes << d.T);
+    // one lane per global bit in the warp OR-reduction (tiles of 11 or 12 bits and at most
+    // 40 qubits leave at most 29), and a tile of at most kPermChunks 16-byte chunks per thread
+    if (d.n_glob > 32 || ((size_t)elem_bytes << d.T) > (size_t)16 * kPermThreads * kPermChunks) return cudaErrorInvalidValue;
     static int nsm[64] = {0}, per_sm[64][2] = {{0}};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
